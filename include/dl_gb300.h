@@ -1,0 +1,170 @@
+/*
+ * dl_gb300.h -- C ABI of the GB300 (sm_103a) dictionary-learning library.
+ *
+ * The library implements one dictionary-learning (DL) iteration of
+ * Irofti & Dumitrescu, "Overcomplete Dictionary Learning with Jacobi Atom
+ * Updates" (arXiv 1509.05054): OMP sparse coding of every signal (Algorithm 1,
+ * step 1; Batch-OMP Cholesky form of the OMP-Box tool cited in Section 4)
+ * followed by the Jacobi atom update in its AK-SVD form with full parallelism,
+ * PAK-SVD with group size n (Section 3, Eq. 3 and Eq. 5, Algorithm 2 with
+ * step 4 replaced by Eq. 5).
+ *
+ * Problem statement (Section 1, Eq. 1): signals Y (p x m), dictionary D
+ * (p x n) with unit-norm columns, sparsity s; find D and an s-sparse X
+ * (n x m, at most s nonzeros per column) minimising ||Y - D X||_F.
+ *
+ * Layouts (all single precision unless stated):
+ *   Y       p x m, column-major: signal i occupies Y[i*p .. i*p+p).
+ *   D       p x n, column-major: atom j occupies D[j*p .. j*p+p).
+ *   X       n x m compressed sparse column (CSC): colptr[m+1] int64 with
+ *           colptr[0] = 0, rowidx[] int32 atom indices, val[] float
+ *           coefficients; column i holds entries colptr[i] .. colptr[i+1]-1,
+ *           at most s of them, atom indices strictly ascending.  The caller
+ *           sizes rowidx/val for s*m entries.
+ *
+ * Memory: every array argument is owned by the caller.  Either all array
+ * arguments of one call are device pointers (cudaMalloc, or torch tensors on
+ * the context's GPU), or all are host pointers (pageable or pinned); in the
+ * host case the call stages them through device buffers owned by the context
+ * and copies results back before returning.  `rmse` outputs are always host
+ * memory.  The context owns only its workspace (Gram matrix, correlations,
+ * per-signal slots, partial sums, staging buffers).
+ *
+ * Streams: work is enqueued on the context's stream (set by dl_init or
+ * dl_set_stream) and is asynchronous for device pointers unless a host `rmse`
+ * array is requested, in which case the call synchronises the stream before
+ * returning.  Calls on one context must not overlap from several host
+ * threads.
+ *
+ * Errors: every entry point returns DL_OK (0) or a negative status.  Argument
+ * errors (DL_EINVAL) are detected before anything is enqueued and leave all
+ * outputs untouched.  DL_ECUDA reports a CUDA runtime error.  DL_ENUMERIC is
+ * reported at the next synchronisation when a kernel met a non-finite input
+ * (NaN/Inf in Y or D).  dl_strerror() gives a one-line description.
+ */
+#ifndef DL_GB300_H
+#define DL_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dl_ctx dl_ctx;
+
+/* status codes */
+#define DL_OK 0
+#define DL_EINVAL (-1)
+#define DL_ECUDA (-2)
+#define DL_ENUMERIC (-3)
+#define DL_ETIMEOUT (-4)
+#define DL_ENOMEM (-5)
+#define DL_ENOTIMPL (-6)
+
+/* arithmetic of the correlation D^T Y and Gram D^T D products */
+#define DL_FP32 0 /* FP32-accurate (split-TF32 tensor cores, FP32 accumulation) */
+#define DL_BF16 1 /* BF16 operands, FP32 accumulation */
+#define DL_FP8 2  /* E4M3 operands with per-atom / per-signal scales */
+
+/* compiled limits */
+#define DL_MAX_P 128
+#define DL_MAX_N 1024
+#define DL_MAX_S 16
+
+/*
+ * dl_init -- create a context for problems with signal length p, n atoms, up
+ * to m_max signals and sparsity up to s_max (Section 1, Eq. 1).
+ *   out        receives the new context (unchanged on error).
+ *   p          1 <= p <= DL_MAX_P.
+ *   n          1 <= n <= DL_MAX_N.
+ *   m_max      1 <= m_max; workspace is sized for m_max signals
+ *              (about m_max * (4n + 8 s_max + 16) bytes plus O(n^2 + 152 n p)).
+ *   s_max      1 <= s_max <= min(p, n, DL_MAX_S).
+ *   precision  DL_FP32 (DL_BF16 / DL_FP8 return DL_ENOTIMPL when not built).
+ *   stream     a cudaStream_t (NULL = the legacy default stream).
+ * The context binds to the CUDA device current at the call.
+ * Returns DL_OK, DL_EINVAL, DL_ENOMEM or DL_ECUDA.
+ */
+int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision, void* stream);
+
+/* dl_set_stream -- enqueue subsequent work of ctx on `stream` (cudaStream_t). */
+int dl_set_stream(dl_ctx* ctx, void* stream);
+
+/* dl_destroy -- free the context's workspace; NULL is accepted. */
+int dl_destroy(dl_ctx* ctx);
+
+/* dl_strerror -- static one-line description of a status code. */
+const char* dl_strerror(int status);
+
+/*
+ * omp_code -- sparse coding stage (Algorithm 1, step 1): for every signal y_i
+ * (column i of Y), greedy OMP selects at most s atoms of D and the
+ * least-squares coefficients on them.  Batch-OMP form: alpha0 = D^T y,
+ * G = D^T D; at each of s steps the atom with the largest |alpha_j| among the
+ * unselected ones is added (lowest index on ties), the Cholesky factor of
+ * G[I,I] grows by one row, and alpha is the correlation of the new residual.
+ * A column stops early (fewer than s entries) when max|alpha| is 0, when the
+ * new Cholesky pivot is below 1e-6 (numerically dependent atom), or when the
+ * residual energy is below 1e-6 ||y||^2.
+ *   Y       p x m signals;  m <= m_max of the context.
+ *   D       p x n dictionary (unit-norm columns expected; other columns are
+ *           accepted and selection then uses the raw correlations d_j^T r).
+ *   s       1 <= s <= s_max.
+ *   colptr, rowidx, val   X output in CSC form (see the layout notes above).
+ * Returns DL_OK, DL_EINVAL, DL_ECUDA or DL_ENUMERIC.
+ */
+int omp_code(dl_ctx* ctx, const float* Y, int64_t m, const float* D, int s, int64_t* colptr,
+             int32_t* rowidx, float* val);
+
+/*
+ * jau_update -- atom-update stage of one DL iteration, Jacobi form with full
+ * parallelism (PAK-SVD with group size n; Section 3, Eq. 3 and Eq. 5): with
+ * E = Y - D X formed once from the input D and X, every atom j used by some
+ * signal becomes
+ *     d_j' = F x^T / ||F x^T||,  F = E_{I_j} + d_j x_{j,I_j}
+ *          ~ E_{I_j} x_{j,I_j}^T + ||x_{j,I_j}||^2 d_j,
+ * and its row of X becomes x_{j,I_j}' = F^T d_j' = E_{I_j}^T d_j' +
+ * (d_j^T d_j') x_{j,I_j}.  Atoms no signal uses (or whose F x^T is zero) are
+ * left unchanged.  The support of X is not changed.
+ *   Y       p x m signals.
+ *   D       p x n dictionary, updated in place.
+ *   colptr, rowidx   X support (CSC, read only; at most s_max per column).
+ *   val     X coefficients, updated in place.
+ *   rmse2   NULL, or host double[2] receiving ||Y - D X||_F / ||Y||_F before
+ *           and after the update (the call then synchronises).
+ * Returns DL_OK, DL_EINVAL, DL_ECUDA or DL_ENUMERIC.
+ */
+int jau_update(dl_ctx* ctx, const float* Y, int64_t m, float* D, const int64_t* colptr,
+               const int32_t* rowidx, float* val, double* rmse2);
+
+/*
+ * dl_iterate -- `iters` full DL iterations (Algorithm 1 with group size n):
+ * omp_code with the current D, then jau_update.  D is updated in place; X
+ * (CSC) holds the representation of the last iteration after its atom update.
+ *   rmse    NULL, or host double[2*iters]: rmse[2k] = ||Y - D X||_F/||Y||_F
+ *           right after sparse coding of iteration k, rmse[2k+1] the same at
+ *           the end of iteration k (updated D and X, as Section 4.2 computes
+ *           the error at the end of a PAK-SVD iteration).
+ * Returns DL_OK, DL_EINVAL, DL_ECUDA or DL_ENUMERIC.
+ */
+int dl_iterate(dl_ctx* ctx, const float* Y, int64_t m, float* D, int s, int iters,
+               int64_t* colptr, int32_t* rowidx, float* val, double* rmse);
+
+/*
+ * dl_sync -- wait for the context's stream and report a pending device-side
+ * error (DL_ENUMERIC for non-finite inputs met by a kernel) or DL_OK.
+ */
+int dl_sync(dl_ctx* ctx);
+
+/*
+ * dl_kernel_launches -- number of kernels the library enqueued on this
+ * context since it was created (graph replays count each kernel they hold).
+ */
+int64_t dl_kernel_launches(dl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DL_GB300_H */
