@@ -163,6 +163,25 @@ int dl_sync(dl_ctx* ctx);
  */
 int64_t dl_kernel_launches(dl_ctx* ctx);
 
+/*
+ * dl_set_profiling -- when on != 0, dl_iterate records CUDA events on the
+ * context's stream around each phase of every iteration (also inside the
+ * replayed CUDA graph) and synchronises after each iteration to accumulate the
+ * per-phase durations.  Turning it on or off resets the accumulated times.
+ * Returns DL_OK or DL_EINVAL / DL_ECUDA.
+ */
+int dl_set_profiling(dl_ctx* ctx, int on);
+
+/*
+ * dl_phase_times -- average duration in milliseconds, per profiled iteration,
+ * of the phases 0 Gram D^T D, 1 correlations D^T Y, 2 OMP, 3 colptr scan,
+ * 4 error accumulation U = E X^T (+ fixed-order reduction), 5 atom update,
+ * 6 row update + RMSE partials + CSC write, 7 RMSE finalisation + D copy.
+ * Writes min(max_phases, 8) values to ms (host) and returns 8, the number of
+ * phases, or DL_EINVAL.
+ */
+int dl_phase_times(dl_ctx* ctx, double* ms, int max_phases);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,488 @@
+// C ABI of the library (include/dl_gb300.h): argument validation, workspace,
+// host staging, and the per-iteration launch sequence (captured once into a
+// CUDA graph and replayed).
+#include "../../include/dl_gb300.h"
+#include "dl_internal.cuh"
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+struct dl_ctx {
+  int dev = 0;
+  int p = 0, n = 0, s_max = 0, precision = 0;
+  int64_t m_max = 0;
+  cudaStream_t st = nullptr;
+  int64_t lda = 0;  // row stride of the correlation matrix A0 (floats)
+  // workspace
+  float* G = nullptr;
+  float* A0 = nullptr;
+  int32_t* sidx = nullptr;
+  float* sval = nullptr;
+  int32_t* scnt = nullptr;
+  int64_t* bsum = nullptr;
+  int* err = nullptr;
+  int* iter = nullptr;
+  double* rmse = nullptr;
+  int rmse_cap = 0;  // iterations
+  dlk::JauWork jw{};
+  // host staging (lazily allocated)
+  float* hY = nullptr;
+  float* hD = nullptr;
+  int64_t* hcolptr = nullptr;
+  int32_t* hrowidx = nullptr;
+  float* hval = nullptr;
+  // graph cache for one DL iteration
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t gkey_m = -1;
+  int gkey_s = -1;
+  int gkey_seen = 0;
+  int64_t launches = 0;
+  // optional per-phase timing with CUDA events recorded on the context's stream
+  bool prof = false;
+  cudaEvent_t ev[9] = {};
+  double phase_ms[8] = {};
+  int64_t phase_count = 0;
+};
+
+namespace {
+
+constexpr int kKernelsOmp = 3;       // gram, correlations, omp
+constexpr int kKernelsScan = 2;      // colptr scan
+constexpr int kKernelsJau = 5;       // accumulate, reduce, atoms, rows, finalize
+
+void free_ctx(dl_ctx* c) {
+  if (!c) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->dev);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
+  void* ptrs[] = {c->G, c->A0, c->sidx, c->sval, c->scnt, c->bsum, c->err, c->iter, c->rmse,
+                  c->jw.Upart, c->jw.U, c->jw.epart_a, c->jw.epart_b, c->jw.Dn, c->jw.C,
+                  c->hY, c->hD, c->hcolptr, c->hrowidx, c->hval};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  cudaSetDevice(prev);
+  delete c;
+}
+
+template <typename T>
+bool dalloc(T** out, size_t count) {
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)out, sizeof(T) * count) == cudaSuccess;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DL_OK;
+  if (e == cudaErrorMemoryAllocation) return DL_ENOMEM;
+  return DL_ECUDA;
+}
+
+#define DL_CHECK(expr)                   \
+  do {                                   \
+    cudaError_t e_ = (expr);             \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+struct DevGuard {
+  int prev = 0;
+  explicit DevGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DevGuard() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// 1 = device (or managed) memory, 0 = host memory, -1 = null
+int ptr_kind(const void* p) {
+  if (!p) return -1;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+
+// Read and clear the device error word; returns a status.
+int take_device_error(dl_ctx* c) {
+  int h = 0;
+  DL_CHECK(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  DL_CHECK(cudaStreamSynchronize(c->st));
+  if (h) DL_CHECK(cudaMemsetAsync(c->err, 0, sizeof(int), c->st));
+  if (h & dlk::ERR_CSC) return DL_EINVAL;
+  if (h & dlk::ERR_NONFINITE) return DL_ENUMERIC;
+  if (h & dlk::ERR_TIMEOUT) return DL_ETIMEOUT;
+  return DL_OK;
+}
+
+int ensure_rmse(dl_ctx* c, int iters) {
+  if (iters <= c->rmse_cap) return DL_OK;
+  DL_CHECK(cudaStreamSynchronize(c->st));
+  if (c->rmse) cudaFree(c->rmse);
+  c->rmse = nullptr;
+  c->rmse_cap = 0;
+  int cap = iters < 64 ? 64 : iters;
+  if (!dalloc(&c->rmse, (size_t)2 * cap)) return DL_ENOMEM;
+  c->rmse_cap = cap;
+  return DL_OK;
+}
+
+int ensure_staging(dl_ctx* c) {
+  if (c->hY) return DL_OK;
+  const size_t m = (size_t)c->m_max;
+  if (!dalloc(&c->hY, m * c->p) || !dalloc(&c->hD, (size_t)c->n * c->p) ||
+      !dalloc(&c->hcolptr, m + 1) || !dalloc(&c->hrowidx, m * c->s_max) ||
+      !dalloc(&c->hval, m * c->s_max))
+    return DL_ENOMEM;
+  return DL_OK;
+}
+
+// Phase boundaries for optional timing: 0 gram | 1 correlations | 2 omp | 3 colptr scan |
+// 4 accumulate+reduce | 5 atoms | 6 rows | 7 finalize+copy | 8
+void mark(dl_ctx* c, int k) {
+  if (c->prof) cudaEventRecordWithFlags(c->ev[k], c->st, cudaEventRecordExternal);
+}
+
+// ---- enqueue helpers (no synchronisation) --------------------------------------
+cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
+  mark(c, 0);
+  cudaError_t e = dlk::gemm_nt_simt(D, c->n, D, c->n, c->p, c->G, c->n, c->st);
+  if (e != cudaSuccess) return e;
+  mark(c, 1);
+  e = dlk::gemm_nt_simt(Y, m, D, c->n, c->p, c->A0, c->lda, c->st);
+  if (e != cudaSuccess) return e;
+  mark(c, 2);
+  e = dlk::omp_batch(c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval, c->scnt, c->err,
+                     c->st);
+  mark(c, 3);
+  return e;
+}
+
+cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const int64_t* colptr,
+                    int32_t* rowidx_out, float* val_out) {
+  mark(c, 4);
+  cudaError_t e = dlk::jau_accumulate(Y, c->p, m, D, c->n, s, c->sidx, c->sval, c->scnt, c->jw,
+                                      c->err, c->st);
+  if (e != cudaSuccess) return e;
+  mark(c, 5);
+  e = dlk::jau_atoms(D, c->p, c->n, c->jw, c->st);
+  if (e != cudaSuccess) return e;
+  mark(c, 6);
+  e = dlk::jau_rows(Y, c->p, m, D, c->n, s, c->sidx, c->sval, c->scnt, c->jw, colptr, rowidx_out,
+                    val_out, c->st);
+  if (e != cudaSuccess) return e;
+  mark(c, 7);
+  e = dlk::jau_finalize(c->jw, c->rmse, c->iter, c->st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(D, c->jw.Dn, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyDeviceToDevice,
+                      c->st);
+  mark(c, 8);
+  return e;
+}
+
+cudaError_t enq_iteration(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int64_t* colptr,
+                          int32_t* rowidx, float* val) {
+  cudaError_t e = enq_omp(c, Y, m, D, s);
+  if (e != cudaSuccess) return e;
+  e = dlk::counts_to_colptr(c->scnt, m, c->bsum, colptr, c->st);
+  if (e != cudaSuccess) return e;
+  return enq_jau(c, Y, m, D, s, colptr, rowidx, val);
+}
+
+int check_common(dl_ctx* c, int64_t m) {
+  if (!c) return DL_EINVAL;
+  if (m < 0 || m > c->m_max) return DL_EINVAL;
+  return DL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dl_strerror(int status) {
+  switch (status) {
+    case DL_OK: return "success";
+    case DL_EINVAL: return "invalid argument (sizes, pointers, or CSC content)";
+    case DL_ECUDA: return "CUDA runtime error";
+    case DL_ENUMERIC: return "non-finite value met in the inputs";
+    case DL_ETIMEOUT: return "a bounded device-side wait timed out";
+    case DL_ENOMEM: return "device memory allocation failed";
+    case DL_ENOTIMPL: return "not implemented in this build";
+    default: return "unknown status";
+  }
+}
+
+int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision, void* stream) {
+  if (!out) return DL_EINVAL;
+  if (p < 1 || p > DL_MAX_P || n < 1 || n > DL_MAX_N || m_max < 1 || s_max < 1 ||
+      s_max > DL_MAX_S || s_max > p || s_max > n)
+    return DL_EINVAL;
+  if (precision != DL_FP32) {
+    if (precision == DL_BF16 || precision == DL_FP8) return DL_ENOTIMPL;
+    return DL_EINVAL;
+  }
+  dl_ctx* c = new dl_ctx();
+  cudaGetDevice(&c->dev);
+  c->p = p;
+  c->n = n;
+  c->m_max = m_max;
+  c->s_max = s_max;
+  c->precision = precision;
+  c->st = (cudaStream_t)stream;
+  c->lda = ((int64_t)n + 31) / 32 * 32;
+  const size_t mm = (size_t)m_max;
+  c->jw.nb_accum = dlk::jau_accum_blocks(p, n);
+  c->jw.nb_row = dlk::jau_row_blocks();
+  const size_t ulen = (size_t)n * p + n;
+  const size_t nslices = dlk::jau_accum_smem(p, n) > 0 ? (size_t)c->jw.nb_accum : 1;
+  bool ok = dalloc(&c->G, (size_t)n * n) && dalloc(&c->A0, mm * c->lda) &&
+            dalloc(&c->sidx, mm * s_max) && dalloc(&c->sval, mm * s_max) &&
+            dalloc(&c->scnt, mm) && dalloc(&c->bsum, (size_t)dlk::scan_blocks(m_max) + 1) &&
+            dalloc(&c->err, 1) && dalloc(&c->iter, 1) && dalloc(&c->jw.Upart, nslices * ulen) &&
+            dalloc(&c->jw.U, ulen) && dalloc(&c->jw.epart_a, (size_t)2 * c->jw.nb_accum) &&
+            dalloc(&c->jw.epart_b, (size_t)c->jw.nb_row) && dalloc(&c->jw.Dn, (size_t)n * p) &&
+            dalloc(&c->jw.C, (size_t)n);
+  if (!ok) {
+    cudaGetLastError();
+    free_ctx(c);
+    return DL_ENOMEM;
+  }
+  if (ensure_rmse(c, 64) != DL_OK || cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->iter, 0, sizeof(int)) != cudaSuccess) {
+    free_ctx(c);
+    return DL_ECUDA;
+  }
+  *out = c;
+  return DL_OK;
+}
+
+int dl_set_stream(dl_ctx* c, void* stream) {
+  if (!c) return DL_EINVAL;
+  if ((cudaStream_t)stream != c->st) {
+    c->st = (cudaStream_t)stream;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gkey_seen = 0;
+  }
+  return DL_OK;
+}
+
+int dl_destroy(dl_ctx* c) {
+  free_ctx(c);
+  return DL_OK;
+}
+
+int dl_sync(dl_ctx* c) {
+  if (!c) return DL_EINVAL;
+  DevGuard g(c->dev);
+  return take_device_error(c);
+}
+
+int64_t dl_kernel_launches(dl_ctx* c) { return c ? c->launches : 0; }
+
+int dl_set_profiling(dl_ctx* c, int on) {
+  if (!c) return DL_EINVAL;
+  DevGuard g(c->dev);
+  const bool want = on != 0;
+  if (want && !c->ev[0])
+    for (cudaEvent_t& e : c->ev) DL_CHECK(cudaEventCreate(&e));
+  if (want != c->prof) {
+    c->prof = want;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gkey_seen = 0;
+  }
+  for (double& x : c->phase_ms) x = 0.0;
+  c->phase_count = 0;
+  return DL_OK;
+}
+
+int dl_phase_times(dl_ctx* c, double* ms, int max_phases) {
+  if (!c || !ms || max_phases < 0) return DL_EINVAL;
+  const int k = max_phases < 8 ? max_phases : 8;
+  for (int q = 0; q < k; ++q) ms[q] = c->phase_count ? c->phase_ms[q] / c->phase_count : 0.0;
+  return 8;
+}
+
+int omp_code(dl_ctx* c, const float* Y, int64_t m, const float* D, int s, int64_t* colptr,
+             int32_t* rowidx, float* val) {
+  int rc = check_common(c, m);
+  if (rc) return rc;
+  if (s < 1 || s > c->s_max || !Y || !D || !colptr || !rowidx || !val) return DL_EINVAL;
+  const int kind = ptr_kind(Y);
+  if (ptr_kind(D) != kind || ptr_kind(colptr) != kind || ptr_kind(rowidx) != kind ||
+      ptr_kind(val) != kind)
+    return DL_EINVAL;
+  DevGuard g(c->dev);
+  const float *dY = Y, *dD = D;
+  int64_t* dcp = colptr;
+  int32_t* dri = rowidx;
+  float* dv = val;
+  if (kind == 0) {
+    if ((rc = ensure_staging(c))) return rc;
+    DL_CHECK(cudaMemcpyAsync(c->hY, Y, sizeof(float) * (size_t)m * c->p, cudaMemcpyHostToDevice, c->st));
+    DL_CHECK(cudaMemcpyAsync(c->hD, D, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyHostToDevice, c->st));
+    dY = c->hY;
+    dD = c->hD;
+    dcp = c->hcolptr;
+    dri = c->hrowidx;
+    dv = c->hval;
+  }
+  DL_CHECK(enq_omp(c, dY, m, dD, s));
+  DL_CHECK(dlk::counts_to_colptr(c->scnt, m, c->bsum, dcp, c->st));
+  DL_CHECK(dlk::slots_to_csc(c->sidx, c->sval, c->scnt, m, s, dcp, dri, dv, c->st));
+  c->launches += kKernelsOmp + kKernelsScan + 1;
+  if (kind == 0) {
+    DL_CHECK(cudaMemcpyAsync(colptr, dcp, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyDeviceToHost, c->st));
+    DL_CHECK(cudaStreamSynchronize(c->st));
+    const int64_t nnz = colptr[m];
+    DL_CHECK(cudaMemcpyAsync(rowidx, dri, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost, c->st));
+    DL_CHECK(cudaMemcpyAsync(val, dv, sizeof(float) * (size_t)nnz, cudaMemcpyDeviceToHost, c->st));
+    return take_device_error(c);
+  }
+  return DL_OK;
+}
+
+int jau_update(dl_ctx* c, const float* Y, int64_t m, float* D, const int64_t* colptr,
+               const int32_t* rowidx, float* val, double* rmse2) {
+  int rc = check_common(c, m);
+  if (rc) return rc;
+  if (!Y || !D || !colptr || !rowidx || !val) return DL_EINVAL;
+  const int kind = ptr_kind(Y);
+  if (ptr_kind(D) != kind || ptr_kind(colptr) != kind || ptr_kind(rowidx) != kind ||
+      ptr_kind(val) != kind)
+    return DL_EINVAL;
+  DevGuard g(c->dev);
+  const int s = c->s_max;
+  const float* dY = Y;
+  float* dD = D;
+  const int64_t* dcp = colptr;
+  const int32_t* dri = rowidx;
+  float* dv = val;
+  int64_t nnz = 0;
+  if (kind == 0) {
+    nnz = colptr[m];
+    if (nnz < 0 || nnz > m * (int64_t)s || colptr[0] != 0) return DL_EINVAL;
+    if ((rc = ensure_staging(c))) return rc;
+    DL_CHECK(cudaMemcpyAsync(c->hY, Y, sizeof(float) * (size_t)m * c->p, cudaMemcpyHostToDevice, c->st));
+    DL_CHECK(cudaMemcpyAsync(c->hD, D, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyHostToDevice, c->st));
+    DL_CHECK(cudaMemcpyAsync(c->hcolptr, colptr, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyHostToDevice, c->st));
+    DL_CHECK(cudaMemcpyAsync(c->hrowidx, rowidx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, c->st));
+    DL_CHECK(cudaMemcpyAsync(c->hval, val, sizeof(float) * (size_t)nnz, cudaMemcpyHostToDevice, c->st));
+    dY = c->hY;
+    dD = c->hD;
+    dcp = c->hcolptr;
+    dri = c->hrowidx;
+    dv = c->hval;
+  }
+  DL_CHECK(cudaMemsetAsync(c->iter, 0, sizeof(int), c->st));
+  DL_CHECK(dlk::csc_to_slots(dcp, dri, dv, m, c->n, s, c->sidx, c->sval, c->scnt, c->err, c->st));
+  DL_CHECK(enq_jau(c, dY, m, dD, s, dcp, nullptr, dv));
+  c->launches += 1 + kKernelsJau;
+  if (kind == 0) {
+    DL_CHECK(cudaMemcpyAsync(D, dD, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyDeviceToHost, c->st));
+    DL_CHECK(cudaMemcpyAsync(val, dv, sizeof(float) * (size_t)nnz, cudaMemcpyDeviceToHost, c->st));
+  }
+  if (rmse2) DL_CHECK(cudaMemcpyAsync(rmse2, c->rmse, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->st));
+  if (kind == 0 || rmse2) return take_device_error(c);
+  return DL_OK;
+}
+
+int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters, int64_t* colptr,
+               int32_t* rowidx, float* val, double* rmse) {
+  int rc = check_common(c, m);
+  if (rc) return rc;
+  if (s < 1 || s > c->s_max || iters < 0 || !Y || !D || !colptr || !rowidx || !val)
+    return DL_EINVAL;
+  const int kind = ptr_kind(Y);
+  if (ptr_kind(D) != kind || ptr_kind(colptr) != kind || ptr_kind(rowidx) != kind ||
+      ptr_kind(val) != kind)
+    return DL_EINVAL;
+  if (iters == 0) return DL_OK;
+  DevGuard g(c->dev);
+  if ((rc = ensure_rmse(c, iters))) return rc;
+  const float* dY = Y;
+  float* dD = D;
+  int64_t* dcp = colptr;
+  int32_t* dri = rowidx;
+  float* dv = val;
+  if (kind == 0) {
+    if ((rc = ensure_staging(c))) return rc;
+    DL_CHECK(cudaMemcpyAsync(c->hY, Y, sizeof(float) * (size_t)m * c->p, cudaMemcpyHostToDevice, c->st));
+    DL_CHECK(cudaMemcpyAsync(c->hD, D, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyHostToDevice, c->st));
+    dY = c->hY;
+    dD = c->hD;
+    dcp = c->hcolptr;
+    dri = c->hrowidx;
+    dv = c->hval;
+  }
+  DL_CHECK(cudaMemsetAsync(c->iter, 0, sizeof(int), c->st));
+  const void* key[5] = {dY, dD, dcp, dri, dv};
+  const bool same = c->gkey_m == m && c->gkey_s == s && memcmp(key, c->gkey, sizeof(key)) == 0;
+  if (!same) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    memcpy(c->gkey, key, sizeof(key));
+    c->gkey_m = m;
+    c->gkey_s = s;
+    c->gkey_seen = 0;
+  }
+  const bool can_graph = c->st != nullptr && m > 0;
+  for (int it = 0; it < iters; ++it) {
+    if (can_graph && c->gkey_seen >= 1 && !c->gexec) {
+      cudaGraph_t graph = nullptr;
+      DL_CHECK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enq_iteration(c, dY, m, dD, s, dcp, dri, dv);
+      cudaError_t e2 = cudaStreamEndCapture(c->st, &graph);
+      if (e != cudaSuccess) return cuda_status(e);
+      if (e2 != cudaSuccess) return cuda_status(e2);
+      e = cudaGraphInstantiate(&c->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_status(e);
+      }
+    }
+    if (c->gexec) {
+      DL_CHECK(cudaGraphLaunch(c->gexec, c->st));
+    } else {
+      DL_CHECK(enq_iteration(c, dY, m, dD, s, dcp, dri, dv));
+      c->gkey_seen++;
+    }
+    c->launches += kKernelsOmp + kKernelsScan + kKernelsJau;
+    if (c->prof) {
+      DL_CHECK(cudaStreamSynchronize(c->st));
+      for (int k = 0; k < 8; ++k) {
+        float ms = 0.f;
+        DL_CHECK(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+        c->phase_ms[k] += ms;
+      }
+      c->phase_count++;
+    }
+  }
+  if (kind == 0) {
+    DL_CHECK(cudaMemcpyAsync(D, dD, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyDeviceToHost, c->st));
+    DL_CHECK(cudaMemcpyAsync(colptr, dcp, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyDeviceToHost, c->st));
+    DL_CHECK(cudaStreamSynchronize(c->st));
+    const int64_t nnz = colptr[m];
+    DL_CHECK(cudaMemcpyAsync(rowidx, dri, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost, c->st));
+    DL_CHECK(cudaMemcpyAsync(val, dv, sizeof(float) * (size_t)nnz, cudaMemcpyDeviceToHost, c->st));
+  }
+  if (rmse)
+    DL_CHECK(cudaMemcpyAsync(rmse, c->rmse, sizeof(double) * 2 * (size_t)iters,
+                             cudaMemcpyDeviceToHost, c->st));
+  if (kind == 0 || rmse) return take_device_error(c);
+  return DL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the public C ABI (include/dl_gb300.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dlk {
+
+// Device-side error word bits (read back by the host at synchronisation).
+enum : int {
+  ERR_NONFINITE = 1,  // NaN/Inf met in Y or D
+  ERR_CSC = 2,        // caller CSC column with > s_max entries or atom index out of range
+  ERR_TIMEOUT = 4,    // a bounded device wait gave up
+};
+
+constexpr float kPivotMin = 1e-6f;     // Cholesky pivot delta below this: dependent atom, stop
+constexpr float kResidRel = 1e-6f;     // residual energy below this * ||y||^2: stop
+
+// ---- correlations and Gram --------------------------------------------------
+// C[i*ldc + j] = sum_r A[i*p + r] * B[j*p + r]  for i < rows_a, j < rows_b (FP32, CUDA cores)
+cudaError_t gemm_nt_simt(const float* A, int64_t rows_a, const float* B, int rows_b, int p, float* C,
+                         int64_t ldc, cudaStream_t st);
+
+// ---- OMP ----------------------------------------------------------------------
+// Batch-OMP of m signals from their correlations A0 (row i = D^T y_i, stride lda) and G = D^T D.
+// Writes s slots per signal (atoms ascending, unused slots idx = -1) and the count.
+cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
+                      int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
+                      cudaStream_t st);
+bool omp_supported(int n, int s);
+
+// ---- JAU / PAK-SVD (group size n) ---------------------------------------------
+struct JauWork {
+  float* Upart;     // [nb_accum][n*p + n] per-CTA partial U = E X^T and r = row energies
+  float* U;         // [n*p + n] reduced
+  double* epart_a;  // [nb_accum][2]  (||E||^2, ||Y||^2) partials
+  double* epart_b;  // [nb_row]       ||Y - D'X'||^2 partials
+  float* Dn;        // [n*p] updated atoms
+  float* C;         // [n]   d_j^T d_j'
+  int nb_accum;
+  int nb_row;
+};
+int jau_accum_blocks(int p, int n);
+int jau_row_blocks();
+size_t jau_accum_smem(int p, int n);
+
+cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int n, int s,
+                           const int32_t* idx, const float* val, const int32_t* cnt,
+                           const JauWork& w, int* err, cudaStream_t st);
+cudaError_t jau_atoms(const float* D, int p, int n, const JauWork& w, cudaStream_t st);
+// x' = E^T d' + c x per slot; writes slots (val) and, when csc_val != nullptr, the CSC arrays.
+cudaError_t jau_rows(const float* Y, int p, int64_t m, const float* D, int n, int s,
+                     const int32_t* idx, float* val, const int32_t* cnt, const JauWork& w,
+                     const int64_t* colptr, int32_t* csc_rowidx, float* csc_val, cudaStream_t st);
+// rmse_out[2*(*iter)] / [2*(*iter)+1] from the partials, then ++*iter (device counter).
+cudaError_t jau_finalize(const JauWork& w, double* rmse_out, int* iter, cudaStream_t st);
+
+// ---- CSC <-> slots --------------------------------------------------------------
+int64_t scan_blocks(int64_t m);
+cudaError_t counts_to_colptr(const int32_t* cnt, int64_t m, int64_t* bsum, int64_t* colptr,
+                             cudaStream_t st);
+cudaError_t slots_to_csc(const int32_t* idx, const float* val, const int32_t* cnt, int64_t m,
+                         int s, const int64_t* colptr, int32_t* rowidx, float* cval,
+                         cudaStream_t st);
+cudaError_t csc_to_slots(const int64_t* colptr, const int32_t* rowidx, const float* cval,
+                         int64_t m, int n, int s, int32_t* idx, float* val, int32_t* cnt,
+                         int* err, cudaStream_t st);
+
+int num_sms();
+
+}  // namespace dlk

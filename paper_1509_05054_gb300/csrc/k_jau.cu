@@ -1,0 +1,470 @@
+// Jacobi atom update in the AK-SVD form with full parallelism (PAK-SVD,
+// group size n; Section 3, Eq. 3 and Eq. 5; Algorithm 2 with step 4 replaced
+// by Eq. 5).  With E = Y - D X formed once:
+//   F_j x_j^T = E_{I_j} x_{j,I_j}^T + ||x_{j,I_j}||^2 d_j  =  U_j + r_j d_j
+//   d_j'      = (U_j + r_j d_j) / ||U_j + r_j d_j||
+//   x_{j,i}'  = F^T d_j' = e_i^T d_j' + (d_j^T d_j') x_{j,i}      for i in I_j
+// U = E X^T (p x n) and r_j = ||x_j||^2 are accumulated signal by signal (the
+// support sets I_j are never materialised), then every atom is updated by one
+// warp, then every signal recomputes its error and its coefficients.
+//
+// Passes over the signals stream Y, the slots and D with 32-lane-coalesced
+// loads; per-CTA partial sums are reduced in a fixed order.
+#include "dl_internal.cuh"
+
+#include <math.h>
+
+namespace dlk {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int ACC_THREADS = 512;
+constexpr int ROW_THREADS = 256;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Block-wide sum of a double; result valid on thread 0.
+__device__ double block_sum_d(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum_d(v);
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < nw; ++q) r += scratch[q];
+  return r;
+}
+
+// Pass A: e_i = y_i - D x_i; U[:, j] += x_{j,i} e_i; r_j += x_{j,i}^2;
+// partial ||E||^2 and ||Y||^2.  PL = rows per lane (p <= 32*PL).
+template <int PL, bool SMEM>
+__global__ void __launch_bounds__(ACC_THREADS) accum_kernel(
+    const float* __restrict__ Y, int p, int64_t m, const float* __restrict__ D, int n, int s,
+    const int32_t* __restrict__ idx, const float* __restrict__ val, const int32_t* __restrict__ cnt,
+    float* __restrict__ Upart, double* __restrict__ epart, int* __restrict__ err) {
+  extern __shared__ float sh[];
+  __shared__ double red[ACC_THREADS / 32];
+  const int lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  const int np = n * p;
+  float* U = SMEM ? sh : Upart;  // atom-major: U[j*p + r]; then r_j at U[np + j]
+  if (SMEM) {
+    for (int q = threadIdx.x; q < np + n; q += blockDim.x) U[q] = 0.f;
+    __syncthreads();
+  }
+  float ee = 0.f, yy = 0.f;
+  const int64_t gw = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5);
+  const int64_t stride = (int64_t)gridDim.x * nw;
+  for (int64_t i = gw; i < m; i += stride) {
+    float e[PL];
+#pragma unroll
+    for (int u = 0; u < PL; ++u) {
+      const int r = lane + 32 * u;
+      e[u] = (r < p) ? Y[i * p + r] : 0.f;
+      yy = fmaf(e[u], e[u], yy);
+    }
+    const int c = cnt[i];
+    const int myj = (lane < c) ? idx[i * s + lane] : 0;
+    const float myx = (lane < c) ? val[i * s + lane] : 0.f;
+    for (int t = 0; t < c; ++t) {
+      const int j = __shfl_sync(FULL, myj, t);
+      const float x = __shfl_sync(FULL, myx, t);
+#pragma unroll
+      for (int u = 0; u < PL; ++u) {
+        const int r = lane + 32 * u;
+        if (r < p) e[u] = fmaf(-x, __ldg(D + (size_t)j * p + r), e[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PL; ++u) ee = fmaf(e[u], e[u], ee);
+    for (int t = 0; t < c; ++t) {
+      const int j = __shfl_sync(FULL, myj, t);
+      const float x = __shfl_sync(FULL, myx, t);
+#pragma unroll
+      for (int u = 0; u < PL; ++u) {
+        const int r = lane + 32 * u;
+        if (r < p) atomicAdd(&U[(size_t)j * p + r], x * e[u]);
+      }
+      if (lane == 0) atomicAdd(&U[np + j], x * x);
+    }
+  }
+  if (!isfinite(ee) || !isfinite(yy)) atomicOr(err, ERR_NONFINITE);
+  if (SMEM) {
+    __syncthreads();
+    float* out = Upart + (size_t)blockIdx.x * (np + n);
+    for (int q = threadIdx.x; q < np + n; q += blockDim.x) out[q] = U[q];
+  }
+  const double see = block_sum_d((double)ee, red);
+  const double syy = block_sum_d((double)yy, red);
+  if (threadIdx.x == 0) {
+    epart[2 * blockIdx.x] = see;
+    epart[2 * blockIdx.x + 1] = syy;
+  }
+}
+
+// U[q] = sum over partial slices in slice order (deterministic).
+__global__ void reduce_kernel(const float* __restrict__ Upart, int nslices, int len,
+                              float* __restrict__ U) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= len) return;
+  float acc = 0.f;
+  for (int b = 0; b < nslices; ++b) acc += Upart[(size_t)b * len + q];
+  U[q] = acc;
+}
+
+// One warp per atom: v = U_j + r_j d_j; d' = v/||v|| (d kept if v = 0); c = d^T d'.
+template <int PL>
+__global__ void atoms_kernel(const float* __restrict__ D, int p, int n, const float* __restrict__ U,
+                             float* __restrict__ Dn, float* __restrict__ C) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= n) return;
+  const float rj = U[(size_t)n * p + j];
+  float d[PL], v[PL];
+  float vv = 0.f;
+#pragma unroll
+  for (int u = 0; u < PL; ++u) {
+    const int r = lane + 32 * u;
+    d[u] = (r < p) ? D[(size_t)j * p + r] : 0.f;
+    v[u] = (r < p) ? fmaf(rj, d[u], U[(size_t)j * p + r]) : 0.f;
+    vv = fmaf(v[u], v[u], vv);
+  }
+  vv = warp_sum(vv);
+  if (vv > 0.f) {
+    const float inv = 1.0f / sqrtf(vv);
+    float c = 0.f;
+#pragma unroll
+    for (int u = 0; u < PL; ++u) {
+      const int r = lane + 32 * u;
+      v[u] *= inv;
+      c = fmaf(d[u], v[u], c);
+      if (r < p) Dn[(size_t)j * p + r] = v[u];
+    }
+    c = warp_sum(c);
+    if (lane == 0) C[j] = c;
+  } else {
+#pragma unroll
+    for (int u = 0; u < PL; ++u) {
+      const int r = lane + 32 * u;
+      if (r < p) Dn[(size_t)j * p + r] = d[u];
+    }
+    if (lane == 0) C[j] = 1.f;
+  }
+}
+
+// Pass B: per signal, e = y - D x (old atoms), x_t' = e.d'_{j_t} + c_{j_t} x_t,
+// then ||y - D' x'||^2.  Writes the slots and, optionally, the CSC arrays.
+template <int PL>
+__global__ void __launch_bounds__(ROW_THREADS) rows_kernel(
+    const float* __restrict__ Y, int p, int64_t m, const float* __restrict__ D,
+    const float* __restrict__ Dn, const float* __restrict__ C, int s,
+    const int32_t* __restrict__ idx, float* __restrict__ val, const int32_t* __restrict__ cnt,
+    const int64_t* __restrict__ colptr, int32_t* __restrict__ csc_rowidx,
+    float* __restrict__ csc_val, double* __restrict__ epart) {
+  __shared__ double red[ROW_THREADS / 32];
+  const int lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  float e2 = 0.f;
+  const int64_t gw = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5);
+  const int64_t stride = (int64_t)gridDim.x * nw;
+  for (int64_t i = gw; i < m; i += stride) {
+    float y[PL], e[PL];
+#pragma unroll
+    for (int u = 0; u < PL; ++u) {
+      const int r = lane + 32 * u;
+      y[u] = (r < p) ? Y[i * p + r] : 0.f;
+      e[u] = y[u];
+    }
+    const int c = cnt[i];
+    const int myj = (lane < c) ? idx[i * s + lane] : 0;
+    const float myx = (lane < c) ? val[i * s + lane] : 0.f;
+    for (int t = 0; t < c; ++t) {
+      const int j = __shfl_sync(FULL, myj, t);
+      const float x = __shfl_sync(FULL, myx, t);
+#pragma unroll
+      for (int u = 0; u < PL; ++u) {
+        const int r = lane + 32 * u;
+        if (r < p) e[u] = fmaf(-x, __ldg(D + (size_t)j * p + r), e[u]);
+      }
+    }
+    float newx = 0.f;  // lane t: x_t'
+    for (int t = 0; t < c; ++t) {
+      const int j = __shfl_sync(FULL, myj, t);
+      const float x = __shfl_sync(FULL, myx, t);
+      float dot = 0.f;
+#pragma unroll
+      for (int u = 0; u < PL; ++u) {
+        const int r = lane + 32 * u;
+        if (r < p) dot = fmaf(e[u], __ldg(Dn + (size_t)j * p + r), dot);
+      }
+      dot = warp_sum(dot);
+      const float xn = fmaf(__ldg(C + j), x, dot);
+      if (lane == t) newx = xn;
+      // residual with the updated atoms: y - D' x'
+#pragma unroll
+      for (int u = 0; u < PL; ++u) {
+        const int r = lane + 32 * u;
+        if (r < p) y[u] = fmaf(-xn, __ldg(Dn + (size_t)j * p + r), y[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PL; ++u) e2 = fmaf(y[u], y[u], e2);
+    if (lane < c) {
+      val[i * s + lane] = newx;
+      if (csc_val) {
+        const int64_t o = colptr[i] + lane;
+        if (csc_rowidx) csc_rowidx[o] = myj;
+        csc_val[o] = newx;
+      }
+    }
+  }
+  const double se = block_sum_d((double)e2, red);
+  if (threadIdx.x == 0) epart[blockIdx.x] = se;
+}
+
+__global__ void finalize_kernel(const double* __restrict__ epa, int na, const double* __restrict__ epb,
+                                int nb, double* __restrict__ rmse, int* __restrict__ iter) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double ee = 0.0, yy = 0.0, e2 = 0.0;
+  for (int b = 0; b < na; ++b) {
+    ee += epa[2 * b];
+    yy += epa[2 * b + 1];
+  }
+  for (int b = 0; b < nb; ++b) e2 += epb[b];
+  const int it = *iter;
+  rmse[2 * it] = yy > 0.0 ? sqrt(ee / yy) : 0.0;
+  rmse[2 * it + 1] = yy > 0.0 ? sqrt(e2 / yy) : 0.0;
+  *iter = it + 1;
+}
+
+// ---- CSC helpers ------------------------------------------------------------------
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_PER_THREAD = 4;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_PER_THREAD;
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_sum_kernel(const int32_t* __restrict__ cnt,
+                                                                 int64_t m, int64_t* __restrict__ bsum) {
+  __shared__ double red[SCAN_THREADS / 32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_PER_THREAD;
+  int64_t loc = 0;
+#pragma unroll
+  for (int u = 0; u < SCAN_PER_THREAD; ++u)
+    if (base + u < m) loc += cnt[base + u];
+  const double tot = block_sum_d((double)loc, red);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = (int64_t)tot;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_write_kernel(const int32_t* __restrict__ cnt,
+                                                                   int64_t m,
+                                                                   const int64_t* __restrict__ bsum,
+                                                                   int64_t* __restrict__ colptr) {
+  __shared__ int64_t wsum[SCAN_THREADS / 32];
+  __shared__ int64_t boff;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    int64_t o = 0;
+    for (unsigned b = 0; b < blockIdx.x; ++b) o += bsum[b];
+    boff = o;
+  }
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_PER_THREAD;
+  int64_t v[SCAN_PER_THREAD];
+  int64_t loc = 0;
+#pragma unroll
+  for (int u = 0; u < SCAN_PER_THREAD; ++u) {
+    v[u] = (base + u < m) ? cnt[base + u] : 0;
+    loc += v[u];
+  }
+  // inclusive warp scan of loc
+  int64_t inc = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t nb = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += nb;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int64_t x = (lane < SCAN_THREADS / 32) ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t nb = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += nb;
+    }
+    if (lane < SCAN_THREADS / 32) wsum[lane] = x;  // inclusive over warps
+  }
+  __syncthreads();
+  int64_t run = boff + (w > 0 ? wsum[w - 1] : 0) + (inc - loc);
+#pragma unroll
+  for (int u = 0; u < SCAN_PER_THREAD; ++u) {
+    if (base + u < m) colptr[base + u] = run;
+    run += v[u];
+    if (base + u == m - 1) colptr[m] = run;
+  }
+}
+
+__global__ void slots_to_csc_kernel(const int32_t* __restrict__ idx, const float* __restrict__ val,
+                                    const int32_t* __restrict__ cnt, int64_t m, int s,
+                                    const int64_t* __restrict__ colptr, int32_t* __restrict__ rowidx,
+                                    float* __restrict__ cval) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= m * s) return;
+  const int64_t i = g / s;
+  const int t = (int)(g - i * s);
+  if (t < cnt[i]) {
+    rowidx[colptr[i] + t] = idx[g];
+    cval[colptr[i] + t] = val[g];
+  }
+}
+
+__global__ void csc_to_slots_kernel(const int64_t* __restrict__ colptr,
+                                    const int32_t* __restrict__ rowidx, const float* __restrict__ cval,
+                                    int64_t m, int n, int s, int32_t* __restrict__ idx,
+                                    float* __restrict__ val, int32_t* __restrict__ cnt,
+                                    int* __restrict__ err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t a = colptr[i], b = colptr[i + 1];
+  int c = (int)(b - a);
+  bool ok = (b >= a) && (c <= s) && (a >= 0) && (b <= m * (int64_t)s);
+  for (int t = 0; ok && t < c; ++t) {
+    const int j = rowidx[a + t];
+    if (j < 0 || j >= n || (t > 0 && j <= rowidx[a + t - 1])) ok = false;
+  }
+  if (!ok) {
+    atomicOr(err, ERR_CSC);
+    c = 0;
+  }
+  for (int t = 0; t < s; ++t) {
+    idx[i * s + t] = (t < c) ? rowidx[a + t] : -1;
+    val[i * s + t] = (t < c) ? cval[a + t] : 0.f;
+  }
+  cnt[i] = c;
+}
+
+template <int PL>
+cudaError_t accum_t(const float* Y, int p, int64_t m, const float* D, int n, int s,
+                    const int32_t* idx, const float* val, const int32_t* cnt, const JauWork& w,
+                    int* err, cudaStream_t st) {
+  const size_t smem = jau_accum_smem(p, n);
+  if (smem > 0) {
+    cudaFuncSetAttribute(accum_kernel<PL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    accum_kernel<PL, true><<<w.nb_accum, ACC_THREADS, smem, st>>>(Y, p, m, D, n, s, idx, val, cnt,
+                                                                  w.Upart, w.epart_a, err);
+  } else {
+    cudaMemsetAsync(w.Upart, 0, sizeof(float) * ((size_t)n * p + n), st);
+    accum_kernel<PL, false><<<w.nb_accum, ACC_THREADS, 0, st>>>(Y, p, m, D, n, s, idx, val, cnt,
+                                                                w.Upart, w.epart_a, err);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int len = n * p + n;
+  const int nslices = smem > 0 ? w.nb_accum : 1;
+  reduce_kernel<<<(len + 255) / 256, 256, 0, st>>>(w.Upart, nslices, len, w.U);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int num_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+size_t jau_accum_smem(int p, int n) {
+  const size_t bytes = sizeof(float) * ((size_t)n * p + n);
+  return bytes <= 200u * 1024u ? bytes : 0;
+}
+int jau_accum_blocks(int p, int n) { return jau_accum_smem(p, n) > 0 ? num_sms() : 4 * num_sms(); }
+int jau_row_blocks() { return 4 * num_sms(); }
+
+cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int n, int s,
+                           const int32_t* idx, const float* val, const int32_t* cnt,
+                           const JauWork& w, int* err, cudaStream_t st) {
+  if (p <= 32) return accum_t<1>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
+  if (p <= 64) return accum_t<2>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
+  if (p <= 96) return accum_t<3>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
+  return accum_t<4>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
+}
+
+cudaError_t jau_atoms(const float* D, int p, int n, const JauWork& w, cudaStream_t st) {
+  const int blocks = (n + 7) / 8;
+  if (p <= 32) atoms_kernel<1><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C);
+  else if (p <= 64) atoms_kernel<2><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C);
+  else if (p <= 96) atoms_kernel<3><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C);
+  else atoms_kernel<4><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C);
+  return cudaGetLastError();
+}
+
+cudaError_t jau_rows(const float* Y, int p, int64_t m, const float* D, int n, int s,
+                     const int32_t* idx, float* val, const int32_t* cnt, const JauWork& w,
+                     const int64_t* colptr, int32_t* csc_rowidx, float* csc_val, cudaStream_t st) {
+  (void)n;
+  const int nb = w.nb_row;
+#define DL_ROWS(PL)                                                                              \
+  rows_kernel<PL><<<nb, ROW_THREADS, 0, st>>>(Y, p, m, D, w.Dn, w.C, s, idx, val, cnt, colptr, \
+                                              csc_rowidx, csc_val, w.epart_b)
+  if (p <= 32) DL_ROWS(1);
+  else if (p <= 64) DL_ROWS(2);
+  else if (p <= 96) DL_ROWS(3);
+  else DL_ROWS(4);
+#undef DL_ROWS
+  return cudaGetLastError();
+}
+
+cudaError_t jau_finalize(const JauWork& w, double* rmse_out, int* iter, cudaStream_t st) {
+  finalize_kernel<<<1, 32, 0, st>>>(w.epart_a, w.nb_accum, w.epart_b, w.nb_row, rmse_out, iter);
+  return cudaGetLastError();
+}
+
+int64_t scan_blocks(int64_t m) { return (m + SCAN_CHUNK - 1) / SCAN_CHUNK; }
+
+cudaError_t counts_to_colptr(const int32_t* cnt, int64_t m, int64_t* bsum, int64_t* colptr,
+                             cudaStream_t st) {
+  if (m <= 0) {
+    cudaMemsetAsync(colptr, 0, sizeof(int64_t), st);
+    return cudaGetLastError();
+  }
+  const unsigned nb = (unsigned)scan_blocks(m);
+  scan_sum_kernel<<<nb, SCAN_THREADS, 0, st>>>(cnt, m, bsum);
+  scan_write_kernel<<<nb, SCAN_THREADS, 0, st>>>(cnt, m, bsum, colptr);
+  return cudaGetLastError();
+}
+
+cudaError_t slots_to_csc(const int32_t* idx, const float* val, const int32_t* cnt, int64_t m,
+                         int s, const int64_t* colptr, int32_t* rowidx, float* cval,
+                         cudaStream_t st) {
+  const int64_t tot = m * s;
+  if (tot <= 0) return cudaSuccess;
+  slots_to_csc_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(idx, val, cnt, m, s, colptr,
+                                                                     rowidx, cval);
+  return cudaGetLastError();
+}
+
+cudaError_t csc_to_slots(const int64_t* colptr, const int32_t* rowidx, const float* cval,
+                         int64_t m, int n, int s, int32_t* idx, float* val, int32_t* cnt,
+                         int* err, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  csc_to_slots_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(colptr, rowidx, cval, m, n, s,
+                                                                   idx, val, cnt, err);
+  return cudaGetLastError();
+}
+
+}  // namespace dlk

@@ -1,0 +1,282 @@
+// Batch-OMP sparse coding, one warp per signal (Algorithm 1 step 1; the OMP-Box
+// tool named in Section 4 implements the Cholesky "Batch-OMP" of [RZE08]).
+//
+// Per signal y with correlations alpha0 = D^T y and Gram G = D^T D, step k:
+//   sel   = argmax_{j not selected} |alpha_j|        (lowest index on ties)
+//   w     = L^{-1} G[I, sel],  delta = G[sel,sel] - w.w,  L gets row (w, sqrt(delta))
+//   z_k   = alpha[sel] / L_kk        (coefficient of y on the new orthonormal direction)
+//   phi_k = (G[:, sel] - sum_{q<k} w_q phi_q) / L_kk    (= D^T q_k)
+//   alpha = alpha - z_k phi_k                             (= D^T r_k)
+// and at the end x_I = L^{-T} z.  This is the Gram-Schmidt (progressive
+// Cholesky) form of Batch-OMP: alpha is updated with one new vector per step
+// instead of being recomputed as alpha0 - G[:,I] gamma, which needs the same
+// n*k multiply-adds but no triangular solve per step.  Both give the same
+// alpha in exact arithmetic.
+//
+// Lane l of the warp holds alpha[32t + l], t < NT = ceil(n/32), in registers,
+// and the phi vectors either in registers (small n*s) or in shared memory.
+// Selected atoms are masked by setting their alpha to NaN, which fmaxf and the
+// equality test of the argmax both ignore.
+#include "dl_internal.cuh"
+
+#include <math.h>
+
+namespace dlk {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+template <int NT, int SMAX, bool SMEM_PHI>
+__global__ void __launch_bounds__(256) omp_warp_kernel(
+    const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
+    const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
+    float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err) {
+  extern __shared__ float smem_phi[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (i >= m) return;
+
+  constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
+  float phi_r[SMEM_PHI ? 1 : NPHI][SMEM_PHI ? 1 : NT];
+  float* phi_s = SMEM_PHI ? smem_phi + (size_t)wib * NPHI * NT * 32 : nullptr;
+#define PHI(q, t) (*(SMEM_PHI ? &phi_s[((q) * NT + (t)) * 32 + lane] : &phi_r[SMEM_PHI ? 0 : (q)][SMEM_PHI ? 0 : (t)]))
+
+  // ||y||^2 for the residual stop rule and the non-finite check
+  float yy = 0.f;
+  for (int r = lane; r < p; r += 32) {
+    const float v = Y[i * p + r];
+    yy = fmaf(v, v, yy);
+  }
+  yy = warp_sum(yy);
+
+  float alpha[NT];
+  const float qnan = __int_as_float(0x7fc00000);
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int j = 32 * t + lane;
+    alpha[t] = (j < n) ? A0[i * lda + j] : qnan;
+  }
+
+  bool bad_in = false;
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+    if (32 * t + lane < n && !isfinite(alpha[t])) bad_in = true;
+  const bool finite_in = isfinite(yy) && !__any_sync(FULL, bad_in);
+
+  float Lrow[SMAX];  // lane j: row j of L
+  float Lcol[SMAX];  // lane j: Lcol[q] = L[q][j] for q > j
+  float wv[SMAX];    // current w, broadcast to all lanes
+  int Iv[SMAX];      // selected atoms, broadcast to all lanes
+#pragma unroll
+  for (int q = 0; q < SMAX; ++q) {
+    Lrow[q] = 0.f;
+    Lcol[q] = 0.f;
+    wv[q] = 0.f;
+    Iv[q] = 0;
+  }
+  float invLdiag = 0.f;  // lane j: 1 / L_jj
+  float myz = 0.f;       // lane j: z_j
+  int myI = -1;          // lane j: I_j
+  float rr = yy;
+  int k = 0;
+  if (!finite_in && lane == 0) atomicOr(err, ERR_NONFINITE);
+
+#pragma unroll
+  for (int step = 0; step < SMAX; ++step) {
+    if (step >= s || !finite_in) break;
+    // ---- argmax |alpha| over unselected atoms, lowest index on ties
+    float mloc = 0.f;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) mloc = fmaxf(mloc, fabsf(alpha[t]));
+    const float mval = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mloc)));
+    if (!(mval > 0.f) || !isfinite(mval)) {
+      if (!isfinite(mval) && lane == 0) atomicOr(err, ERR_NONFINITE);
+      break;
+    }
+    unsigned key = 0xffffffffu;
+#pragma unroll
+    for (int t = NT - 1; t >= 0; --t)
+      if (fabsf(alpha[t]) == mval) key = (unsigned)(32 * t + lane);
+    const int sel = (int)__reduce_min_sync(FULL, key);
+    const int tsel = sel >> 5, lsel = sel & 31;
+    const float* __restrict__ Gr = G + (size_t)sel * n;  // row sel == column sel (G symmetric)
+
+    // issue the Gram row loads early (needed for phi unless this is the last step)
+    const bool need_phi = (step + 1 < s) && (step + 1 < SMAX);
+    if (need_phi) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const int j = 32 * t + lane;
+        PHI(step < NPHI ? step : 0, t) = (j < n) ? __ldg(Gr + j) : 0.f;
+      }
+    }
+    const float gI = (lane < step) ? __ldg(Gr + myI) : 0.f;  // lane q: G[I_q, sel]
+    const float gss = __ldg(Gr + sel);
+
+    // ---- Cholesky row append: forward substitution L w = G[I, sel]
+    float acc = 0.f, wsq = 0.f;
+#pragma unroll
+    for (int q = 0; q < SMAX - 1; ++q) {
+      if (q >= step) break;
+      const float wl = (gI - acc) * invLdiag;  // valid on lane q
+      const float wq = __shfl_sync(FULL, wl, q);
+      acc = fmaf(Lrow[q], wq, acc);
+      wsq = fmaf(wq, wq, wsq);
+      wv[q] = wq;
+    }
+    const float delta = gss - wsq;
+    if (!(delta > kPivotMin)) {
+      if (!isfinite(delta) && lane == 0) atomicOr(err, ERR_NONFINITE);
+      break;
+    }
+    const float Lkk = sqrtf(delta);
+    const float invL = 1.0f / Lkk;
+
+    // z_k = alpha[sel] / L_kk
+    float amine = 0.f;
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+      if (t == tsel) amine = alpha[t];
+    const float zk = __shfl_sync(FULL, amine, lsel) * invL;
+
+    // record row `step` of L (lane step) and column entries (lanes q < step)
+    if (lane == step) {
+#pragma unroll
+      for (int q = 0; q < SMAX; ++q)
+        if (q < step) Lrow[q] = wv[q];
+      Lrow[step] = Lkk;
+      invLdiag = invL;
+      myz = zk;
+      myI = sel;
+    }
+#pragma unroll
+    for (int q = 0; q < SMAX; ++q)
+      if (q < step && lane == q) Lcol[step] = wv[q];
+    Iv[step] = sel;
+    rr = fmaf(-zk, zk, rr);
+    k = step + 1;
+
+    // mask the selected atom
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+      if (t == tsel && lane == lsel) alpha[t] = qnan;
+
+    // ---- phi_k and alpha update
+    if (need_phi) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        float g = PHI(step < NPHI ? step : 0, t);
+#pragma unroll
+        for (int q = 0; q < SMAX - 1; ++q) {
+          if (q >= step) break;
+          g = fmaf(-wv[q], PHI(q, t), g);
+        }
+        g *= invL;
+        PHI(step < NPHI ? step : 0, t) = g;
+        alpha[t] = fmaf(-zk, g, alpha[t]);
+      }
+    }
+    if (rr <= kResidRel * yy) break;
+  }
+#undef PHI
+
+  // ---- back substitution L^T gamma = z
+  float gam = 0.f, acc2 = 0.f;
+#pragma unroll
+  for (int q = SMAX - 1; q >= 0; --q) {
+    if (q < k) {
+      const float gl = (myz - acc2) * invLdiag;  // valid on lane q
+      const float gq = __shfl_sync(FULL, gl, q);
+      if (lane == q) gam = gq;
+      acc2 = fmaf(Lcol[q], gq, acc2);
+    }
+  }
+
+  // ---- write the support in ascending atom order
+  const int64_t base = i * s;
+  if (lane < k) {
+    int rank = 0;
+#pragma unroll
+    for (int q = 0; q < SMAX; ++q)
+      if (q < k && Iv[q] < myI) ++rank;
+    oidx[base + rank] = myI;
+    oval[base + rank] = gam;
+  } else if (lane < s) {
+    oidx[base + lane] = -1;
+    oval[base + lane] = 0.f;
+  }
+  if (lane == 0) ocnt[i] = k;
+}
+
+template <int NT, int SMAX, bool SMEM>
+cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
+                     int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
+                     cudaStream_t st) {
+  int warps = 8;
+  size_t smem = 0;
+  if (SMEM) {
+    const size_t per_warp = (size_t)(SMAX - 1) * NT * 32 * sizeof(float);
+    warps = (int)((200u * 1024u) / per_warp);
+    if (warps > 8) warps = 8;
+    if (warps < 1) warps = 1;
+    smem = per_warp * warps;
+    cudaFuncSetAttribute(omp_warp_kernel<NT, SMAX, SMEM>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  const int64_t blocks = (m + warps - 1) / warps;
+  omp_warp_kernel<NT, SMAX, SMEM><<<(unsigned)blocks, warps * 32, smem, st>>>(
+      A0, lda, G, n, Y, p, m, s, idx, val, cnt, err);
+  return cudaGetLastError();
+}
+
+// register budget: alpha + phi must stay well inside 255 registers
+template <int NT, int SMAX>
+constexpr bool fits_regs() {
+  return NT * (SMAX - 1) <= 128;
+}
+
+template <int NT, int SMAX>
+cudaError_t pick_store(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
+                       int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
+                       cudaStream_t st) {
+  if constexpr (fits_regs<NT, SMAX>())
+    return launch_t<NT, SMAX, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  else
+    return launch_t<NT, SMAX, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+}
+
+template <int NT>
+cudaError_t pick_s(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
+                   int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
+                   cudaStream_t st) {
+  if (s <= 4) return pick_store<NT, 4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  if (s <= 8) return pick_store<NT, 8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  if (s <= 12) return pick_store<NT, 12>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  return pick_store<NT, 16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+}
+
+}  // namespace
+
+bool omp_supported(int n, int s) { return n >= 1 && n <= 1024 && s >= 1 && s <= 16; }
+
+cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
+                      int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
+                      cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  const int nt = (n + 31) / 32;
+  if (nt <= 1) return pick_s<1>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  if (nt <= 2) return pick_s<2>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  if (nt <= 4) return pick_s<4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  if (nt <= 8) return pick_s<8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  if (nt <= 16) return pick_s<16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  return pick_s<32>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+}
+
+}  // namespace dlk

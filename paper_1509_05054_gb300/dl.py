@@ -1,0 +1,185 @@
+"""Thin Python binding of the C ABI in ``include/dl_gb300.h``.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libdl_gb300.so``.  The functions keep the C names
+(``dl_init``, ``omp_code``, ``jau_update``, ``dl_iterate``, ...) and accept
+either torch tensors (device or host) or raw integer pointers.  There is no
+CPU fallback: if the library is missing, loading raises.
+
+Layouts follow the C header: ``Y`` is an ``(m, p)`` float32 tensor (row i is
+signal i, i.e. the column-major ``p x m`` matrix), ``D`` is ``(n, p)``
+(row j is atom j), ``X`` is CSC (``colptr`` int64 ``m+1``, ``rowidx`` int32,
+``val`` float32, capacity ``s*m``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdl_gb300.so")
+
+DL_OK, DL_EINVAL, DL_ECUDA, DL_ENUMERIC, DL_ETIMEOUT, DL_ENOMEM, DL_ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
+DL_FP32, DL_BF16, DL_FP8 = 0, 1, 2
+
+_lib = None
+_lock = threading.Lock()
+
+
+class DLError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {dl_strerror(status)} (status {status})")
+
+
+def load(build_if_missing: bool = True):
+    """Load ``libdl_gb300.so`` (building it with nvcc first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH}")
+            from . import build as _build
+            _build.build()
+        lib = ctypes.CDLL(LIB_PATH)
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        lib.dl_init.argtypes = [ctypes.POINTER(P), i32, i32, i64, i32, i32, P]
+        lib.dl_set_stream.argtypes = [P, P]
+        lib.dl_destroy.argtypes = [P]
+        lib.dl_strerror.argtypes = [i32]
+        lib.dl_strerror.restype = ctypes.c_char_p
+        lib.omp_code.argtypes = [P, P, i64, P, i32, P, P, P]
+        lib.jau_update.argtypes = [P, P, i64, P, P, P, P, P]
+        lib.dl_iterate.argtypes = [P, P, i64, P, i32, i32, P, P, P, P]
+        lib.dl_sync.argtypes = [P]
+        lib.dl_kernel_launches.argtypes = [P]
+        lib.dl_kernel_launches.restype = i64
+        lib.dl_set_profiling.argtypes = [P, i32]
+        lib.dl_phase_times.argtypes = [P, P, i32]
+        for name in ("dl_init", "dl_set_stream", "dl_destroy", "omp_code", "jau_update", "dl_iterate",
+                     "dl_sync", "dl_set_profiling", "dl_phase_times"):
+            getattr(lib, name).restype = i32
+        _lib = lib
+        return lib
+
+
+def _ptr(x):
+    """Pointer of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "arrays must be contiguous"
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        assert x.flags["C_CONTIGUOUS"], "arrays must be contiguous"
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _check(rc: int, where: str):
+    if rc != DL_OK:
+        raise DLError(rc, where)
+
+
+def dl_strerror(status: int) -> str:
+    return load().dl_strerror(int(status)).decode()
+
+
+def dl_init(p: int, n: int, m_max: int, s_max: int, precision: int = DL_FP32, stream=None) -> int:
+    ctx = ctypes.c_void_p()
+    _check(load().dl_init(ctypes.byref(ctx), p, n, m_max, s_max, precision, _stream_ptr(stream)),
+           "dl_init")
+    return ctx.value
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def dl_set_stream(ctx: int, stream) -> None:
+    _check(load().dl_set_stream(ctx, _stream_ptr(stream)), "dl_set_stream")
+
+
+def dl_destroy(ctx: int) -> None:
+    load().dl_destroy(ctx)
+
+
+def dl_sync(ctx: int) -> None:
+    _check(load().dl_sync(ctx), "dl_sync")
+
+
+def dl_kernel_launches(ctx: int) -> int:
+    return int(load().dl_kernel_launches(ctx))
+
+
+PHASES = ("gram", "correlations", "omp", "colptr_scan", "accumulate", "atoms", "rows", "finalize")
+
+
+def dl_set_profiling(ctx: int, on: bool) -> None:
+    _check(load().dl_set_profiling(ctx, 1 if on else 0), "dl_set_profiling")
+
+
+def dl_phase_times(ctx: int) -> dict:
+    import numpy as np
+    out = np.zeros(8)
+    rc = load().dl_phase_times(ctx, out.ctypes.data, 8)
+    if rc < 0:
+        raise DLError(rc, "dl_phase_times")
+    return dict(zip(PHASES, out.tolist()))
+
+
+def omp_code(ctx: int, Y, m: int, D, s: int, colptr, rowidx, val) -> None:
+    _check(load().omp_code(ctx, _ptr(Y), m, _ptr(D), s, _ptr(colptr), _ptr(rowidx), _ptr(val)),
+           "omp_code")
+
+
+def jau_update(ctx: int, Y, m: int, D, colptr, rowidx, val, rmse2=None) -> None:
+    _check(load().jau_update(ctx, _ptr(Y), m, _ptr(D), _ptr(colptr), _ptr(rowidx), _ptr(val),
+                             _ptr(rmse2)), "jau_update")
+
+
+def dl_iterate(ctx: int, Y, m: int, D, s: int, iters: int, colptr, rowidx, val, rmse=None) -> None:
+    _check(load().dl_iterate(ctx, _ptr(Y), m, _ptr(D), s, iters, _ptr(colptr), _ptr(rowidx),
+                             _ptr(val), _ptr(rmse)), "dl_iterate")
+
+
+class Context:
+    """Owns one ``dl_ctx`` and the CSC output tensors for convenience."""
+
+    def __init__(self, p: int, n: int, m_max: int, s_max: int, precision: int = DL_FP32,
+                 device=None, stream=None):
+        import torch
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        with torch.cuda.device(self.device):
+            if stream is None:
+                stream = torch.cuda.current_stream(self.device)
+            self.ctx = dl_init(p, n, m_max, s_max, precision, stream)
+        self.p, self.n, self.m_max, self.s_max = p, n, m_max, s_max
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            dl_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_csc(self, m: int, s: int, device=None):
+        import torch
+        dev = self.device if device is None else device
+        colptr = torch.zeros(m + 1, dtype=torch.int64, device=dev)
+        rowidx = torch.zeros(max(1, m * s), dtype=torch.int32, device=dev)
+        val = torch.zeros(max(1, m * s), dtype=torch.float32, device=dev)
+        return colptr, rowidx, val

@@ -1,0 +1,320 @@
+"""GPU path vs the FP64 oracle, through the C ABI, on seeded synthetic inputs.
+
+Tolerances (FP32 path):
+  * supports identical on >= 99.9% of the signals, every mismatch a near-tie
+    of the top two |correlations| (relative gap < 1e-5 in the oracle's run);
+  * relative RMSE ||Y - D X||_F / ||Y||_F within 1e-4 of the oracle's;
+  * atoms updated from an identical X within 1e-5;
+  * coefficients (identical supports) within 5e-4 absolute on unit-variance
+    patches: FP32 correlations carry ~1e-6 relative error, amplified by the
+    conditioning of the s x s support Gram.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1509_05054_gb300 import synth
+
+from _common import assert_support_parity, csc_to_slots
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dl():
+    from paper_1509_05054_gb300 import build as _b
+    _b.build()
+    from paper_1509_05054_gb300 import dl as _dl
+    _dl.load()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return _dl
+
+
+def _gpu_omp(dl, Y, D, s, ctx=None):
+    m, p = Y.shape
+    n = D.shape[0]
+    own = ctx is None
+    if own:
+        ctx = dl.dl_init(p, n, max(1, m), s, dl.DL_FP32, torch.cuda.current_stream())
+    Yd = torch.from_numpy(np.ascontiguousarray(Y, np.float32)).cuda()
+    Dd = torch.from_numpy(np.ascontiguousarray(D, np.float32)).cuda()
+    colptr = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+    rowidx = torch.zeros(max(1, m * s), dtype=torch.int32, device="cuda")
+    val = torch.zeros(max(1, m * s), dtype=torch.float32, device="cuda")
+    dl.omp_code(ctx, Yd, m, Dd, s, colptr, rowidx, val)
+    dl.dl_sync(ctx)
+    if own:
+        dl.dl_destroy(ctx)
+    return csc_to_slots(colptr.cpu().numpy(), rowidx.cpu().numpy(), val.cpu().numpy(), s)
+
+
+SHAPES = [
+    # (workload, m, s) -- small enough for the oracle in seconds, several tiles + ragged tail
+    ("tiny", 1000, 3),
+    ("patch_n256", 5003, 6),
+    ("patch_n512", 3001, 8),
+]
+
+
+@pytest.mark.parametrize("name,m,s", SHAPES)
+def test_omp_code_matches_oracle(dl, name, m, s):
+    Y, D, spec = synth.workload_inputs(name, m=m)
+    idx_g, val_g, cnt_g = _gpu_omp(dl, Y, D, s)
+    idx_o, val_o, cnt_o, gaps = oracle.omp(Y.astype(np.float64), D.astype(np.float64), s,
+                                           return_gaps=True)
+    same = assert_support_parity(idx_g, cnt_g, idx_o, cnt_o, gaps)
+    np.testing.assert_allclose(val_g[same], val_o[same], rtol=0, atol=5e-4)
+    # CSC validity: ascending atoms, at most s per column
+    for i in range(0, m, max(1, m // 200)):
+        c = cnt_g[i]
+        assert c <= s and np.all(np.diff(idx_g[i, :c]) > 0)
+    rho_g = oracle.rmse(Y, D, idx_g, val_g, cnt_g)
+    rho_o = oracle.rmse(Y, D, idx_o, val_o, cnt_o)
+    assert abs(rho_g - rho_o) <= 1e-4
+
+
+def test_omp_s1_is_argmax(dl):
+    Y, D, _ = synth.workload_inputs("patch_n256", m=4000)
+    idx_g, val_g, cnt_g = _gpu_omp(dl, Y, D, 1)
+    C = Y.astype(np.float64) @ D.astype(np.float64).T
+    top2 = np.sort(np.abs(C), axis=1)[:, -2:]
+    clear = (top2[:, 1] - top2[:, 0]) / top2[:, 1] >= 1e-5
+    np.testing.assert_array_equal(idx_g[clear, 0], np.argmax(np.abs(C), axis=1)[clear])
+    np.testing.assert_allclose(val_g[:, 0], C[np.arange(4000), idx_g[:, 0]], rtol=1e-5, atol=1e-5)
+
+
+def _to_csc_tensors(idx, val, cnt, s):
+    m = len(cnt)
+    colptr = np.zeros(m + 1, np.int64)
+    colptr[1:] = np.cumsum(cnt)
+    mask = idx >= 0
+    rowidx = idx[mask].astype(np.int32)
+    vals = val[mask].astype(np.float32)
+    cap = max(1, m * s)
+    r = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    v = torch.zeros(cap, dtype=torch.float32, device="cuda")
+    r[: len(rowidx)] = torch.from_numpy(rowidx).cuda()
+    v[: len(vals)] = torch.from_numpy(vals).cuda()
+    return torch.from_numpy(colptr).cuda(), r, v
+
+
+@pytest.mark.parametrize("name,m,s", SHAPES)
+def test_jau_update_matches_oracle_from_identical_x(dl, name, m, s):
+    """Atoms from an identical X within 1e-5; rows and RMSE pair close (Eq. 3, 5)."""
+    Y, D, spec = synth.workload_inputs(name, m=m)
+    Y64, D64 = Y.astype(np.float64), D.astype(np.float64)
+    idx, val, cnt = oracle.omp(Y64, D64, s)
+    val32 = val.astype(np.float32).astype(np.float64)      # the GPU sees FP32 coefficients
+    D1_o, val1_o, _ = oracle.jau(Y64, D64, idx, val32, cnt)
+    rho_before = oracle.rmse(Y64, D64, idx, val32, cnt)
+    rho_after = oracle.rmse(Y64, D1_o, idx, val1_o, cnt)
+
+    p, n = D.shape[1], D.shape[0]
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    Yd = torch.from_numpy(Y).cuda()
+    Dd = torch.from_numpy(D.copy()).cuda()
+    colptr, rowidx, v = _to_csc_tensors(idx, val, cnt, s)
+    rm = np.zeros(2)
+    dl.jau_update(ctx, Yd, m, Dd, colptr, rowidx, v, rm)
+    dl.dl_destroy(ctx)
+    D1_g = Dd.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(D1_g, D1_o, rtol=0, atol=1e-5)
+    _, val1_g, _ = csc_to_slots(colptr.cpu().numpy(), rowidx.cpu().numpy(), v.cpu().numpy(), s)
+    np.testing.assert_allclose(val1_g, val1_o, rtol=0, atol=2e-4)
+    assert abs(rm[0] - rho_before) <= 1e-5
+    assert abs(rm[1] - rho_after) <= 1e-4
+
+
+def test_dl_iterate_teacher_forced(dl):
+    """Each GPU iteration vs the oracle started from the GPU's own D^(k) (the JAU
+    trajectory is erratic, so free-running FP32 and FP64 runs may part ways)."""
+    name, m, s, iters = "patch_n256", 6007, 6, 4
+    Y, D, _ = synth.workload_inputs(name, m=m)
+    Y64 = Y.astype(np.float64)
+    p, n = D.shape[1], D.shape[0]
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    Yd = torch.from_numpy(Y).cuda()
+    Dd = torch.from_numpy(D.copy()).cuda()
+    colptr, rowidx, val = (torch.zeros(m + 1, dtype=torch.int64, device="cuda"),
+                           torch.zeros(m * s, dtype=torch.int32, device="cuda"),
+                           torch.zeros(m * s, dtype=torch.float32, device="cuda"))
+    for k in range(iters):
+        Dk = Dd.cpu().numpy().astype(np.float64)
+        rm = np.zeros(2)
+        dl.dl_iterate(ctx, Yd, m, Dd, s, 1, colptr, rowidx, val, rm)
+        idx_o, val_o, cnt_o, gaps = oracle.omp(Y64, Dk, s, return_gaps=True)
+        rho_omp = oracle.rmse(Y64, Dk, idx_o, val_o, cnt_o)
+        D1_o, val1_o, _ = oracle.jau(Y64, Dk, idx_o, val_o, cnt_o)
+        rho_jau = oracle.rmse(Y64, D1_o, idx_o, val1_o, cnt_o)
+        assert abs(rm[0] - rho_omp) <= 1e-4, (k, rm, rho_omp)
+        assert abs(rm[1] - rho_jau) <= 1e-4, (k, rm, rho_jau)
+        idx_g, val_g, cnt_g = csc_to_slots(colptr.cpu().numpy(), rowidx.cpu().numpy(),
+                                           val.cpu().numpy(), s)
+        assert_support_parity(idx_g, cnt_g, idx_o, cnt_o, gaps)
+        # the end-of-iteration error of the returned D and X matches the reported one
+        rho_end = oracle.rmse(Y64, Dd.cpu().numpy().astype(np.float64), idx_g, val_g, cnt_g)
+        assert abs(rho_end - rm[1]) <= 1e-5
+        assert rm[1] <= rm[0] + 1e-6
+    dl.dl_destroy(ctx)
+
+
+def test_full_size_sampled_parity(dl):
+    """The throughput shape (p=64, n=512, s=8, m=1e5) in the launch configuration
+    the benchmark uses (dl_iterate, graph replay): one iteration, the RMSE pair
+    against the oracle on all signals, and supports on a sample of 4000."""
+    Y, D, spec = synth.workload_inputs("patch_n512")
+    m, s = spec["m"], spec["s"]
+    p, n = D.shape[1], D.shape[0]
+    Y64, D64 = Y.astype(np.float64), D.astype(np.float64)
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    Yd = torch.from_numpy(Y).cuda()
+    Dd = torch.from_numpy(D.copy()).cuda()
+    colptr = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+    rowidx = torch.zeros(m * s, dtype=torch.int32, device="cuda")
+    val = torch.zeros(m * s, dtype=torch.float32, device="cuda")
+    rm = np.zeros(2)
+    dl.dl_iterate(ctx, Yd, m, Dd, s, 1, colptr, rowidx, val, rm)
+    idx_o, val_o, cnt_o = oracle.omp(Y64, D64, s)
+    rho_omp = oracle.rmse(Y64, D64, idx_o, val_o, cnt_o)
+    assert abs(rm[0] - rho_omp) <= 1e-4
+    sample = np.random.default_rng(0).choice(m, 4000, replace=False)
+    # supports come from a fresh omp_code with the same D (dl_iterate already changed D)
+    Dd2 = torch.from_numpy(D.copy()).cuda()
+    ctx2 = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    dl.omp_code(ctx2, Yd, m, Dd2, s, colptr, rowidx, val)
+    dl.dl_sync(ctx2)
+    idx_g, val_g, cnt_g = csc_to_slots(colptr.cpu().numpy(), rowidx.cpu().numpy(),
+                                       val.cpu().numpy(), s)
+    _, _, _, gaps = oracle.omp(Y64[sample], D64, s, return_gaps=True)
+    assert_support_parity(idx_g[sample], cnt_g[sample], idx_o[sample], cnt_o[sample], gaps)
+    dl.dl_destroy(ctx)
+    dl.dl_destroy(ctx2)
+
+
+def test_edge_cases(dl):
+    """Zero signal, exactly sparse signal (early stop), m = 1, n not a multiple of 32,
+    s = p, empty problem."""
+    g = np.random.default_rng(5)
+    p, n = 20, 50
+    D = synth.random_dictionary(p, n, seed=9).astype(np.float32)
+    Y = g.standard_normal((7, p)).astype(np.float32)
+    Y[0] = 0.0
+    Y[1] = 2.0 * D[3] - 1.5 * D[17]
+    for s in (1, 3, p):
+        idx_g, val_g, cnt_g = _gpu_omp(dl, Y, D, s)
+        idx_o, val_o, cnt_o, gaps = oracle.omp(Y.astype(np.float64), D.astype(np.float64), s,
+                                               return_gaps=True)
+        assert cnt_g[0] == 0 and np.all(idx_g[0] == -1)
+        assert set(idx_g[1, :cnt_g[1]]) >= {3, 17}
+        assert oracle.rmse(Y[1:2], D, idx_g[1:2], val_g[1:2], cnt_g[1:2]) < 1e-3
+        if s < p:
+            assert_support_parity(idx_g[2:], cnt_g[2:], idx_o[2:], cnt_o[2:], gaps[2:], frac=0.99)
+    idx_g, val_g, cnt_g = _gpu_omp(dl, Y[2:3], D, 3)
+    idx_o, val_o, cnt_o = oracle.omp(Y[2:3].astype(np.float64), D.astype(np.float64), 3)
+    np.testing.assert_array_equal(idx_g, idx_o)
+    # empty problem
+    ctx = dl.dl_init(p, n, 10, 3, dl.DL_FP32, torch.cuda.current_stream())
+    colptr = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+    r = torch.zeros(1, dtype=torch.int32, device="cuda")
+    v = torch.zeros(1, dtype=torch.float32, device="cuda")
+    Yd = torch.zeros(p, device="cuda")
+    Dd = torch.from_numpy(D).cuda()
+    dl.omp_code(ctx, Yd, 0, Dd, 3, colptr, r, v)
+    dl.dl_sync(ctx)
+    assert int(colptr[0]) == 0
+    dl.dl_destroy(ctx)
+
+
+def test_invalid_arguments_and_nonfinite(dl):
+    p, n, m, s = 16, 32, 100, 3
+    with pytest.raises(dl.DLError) as e:
+        dl.dl_init(p, n, m, p + 1, dl.DL_FP32, None)
+    assert e.value.status == dl.DL_EINVAL
+    with pytest.raises(dl.DLError):
+        dl.dl_init(0, n, m, s, dl.DL_FP32, None)
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    Y, D, _ = synth.workload_inputs("tiny", m=m)
+    Yd, Dd = torch.from_numpy(Y).cuda(), torch.from_numpy(D).cuda()
+    colptr, rowidx, val = (torch.zeros(m + 1, dtype=torch.int64, device="cuda"),
+                           torch.zeros(m * s, dtype=torch.int32, device="cuda"),
+                           torch.zeros(m * s, dtype=torch.float32, device="cuda"))
+    with pytest.raises(dl.DLError) as e:
+        dl.omp_code(ctx, Yd, m + 1, Dd, s, colptr, rowidx, val)      # m > m_max
+    assert e.value.status == dl.DL_EINVAL
+    with pytest.raises(dl.DLError) as e:
+        dl.omp_code(ctx, Yd, m, Dd, s + 1, colptr, rowidx, val)      # s > s_max
+    assert e.value.status == dl.DL_EINVAL
+    with pytest.raises(dl.DLError) as e:                              # mixed host/device
+        dl.omp_code(ctx, Yd, m, D, s, colptr, rowidx, val)
+    assert e.value.status == dl.DL_EINVAL
+    Ybad = Yd.clone()
+    Ybad[5, 3] = float("nan")
+    dl.omp_code(ctx, Ybad, m, Dd, s, colptr, rowidx, val)
+    with pytest.raises(dl.DLError) as e:
+        dl.dl_sync(ctx)
+    assert e.value.status == dl.DL_ENUMERIC
+    dl.dl_sync(ctx)  # error word was cleared
+    # corrupt CSC into jau_update: atom index out of range
+    dl.omp_code(ctx, Yd, m, Dd, s, colptr, rowidx, val)
+    rowidx[0] = n + 5
+    with pytest.raises(dl.DLError) as e:
+        dl.jau_update(ctx, Yd, m, Dd, colptr, rowidx, val, np.zeros(2))
+    assert e.value.status == dl.DL_EINVAL
+    dl.dl_destroy(ctx)
+
+
+def test_host_pointer_path_matches_device_path(dl):
+    """All-host arguments are staged by the library and give the device path's result."""
+    name, m, s = "patch_n256", 3000, 6
+    Y, D, _ = synth.workload_inputs(name, m=m)
+    p, n = D.shape[1], D.shape[0]
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    Dh = D.copy()
+    cp_h = np.zeros(m + 1, np.int64)
+    ri_h = np.zeros(m * s, np.int32)
+    v_h = np.zeros(m * s, np.float32)
+    rm_h = np.zeros(4)
+    dl.dl_iterate(ctx, Y, m, Dh, s, 2, cp_h, ri_h, v_h, rm_h)
+    Yd, Dd = torch.from_numpy(Y).cuda(), torch.from_numpy(D.copy()).cuda()
+    cp, ri, v = (torch.zeros(m + 1, dtype=torch.int64, device="cuda"),
+                 torch.zeros(m * s, dtype=torch.int32, device="cuda"),
+                 torch.zeros(m * s, dtype=torch.float32, device="cuda"))
+    rm_d = np.zeros(4)
+    dl.dl_iterate(ctx, Yd, m, Dd, s, 2, cp, ri, v, rm_d)
+    dl.dl_destroy(ctx)
+    np.testing.assert_allclose(rm_h, rm_d, rtol=0, atol=1e-6)
+    np.testing.assert_array_equal(cp_h, cp.cpu().numpy())
+    np.testing.assert_allclose(Dh, Dd.cpu().numpy(), rtol=0, atol=1e-5)
+
+
+def test_multi_iteration_graph_replay_matches_single_calls(dl):
+    """dl_iterate(iters=3) (graph-captured after the first iteration) equals three
+    dl_iterate(iters=1) calls to within rounding; the RMSE array has 2*iters entries."""
+    name, m, s = "patch_n256", 4000, 6
+    Y, D, _ = synth.workload_inputs(name, m=m)
+    p, n = D.shape[1], D.shape[0]
+    st = torch.cuda.Stream()
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, st)
+    Yd = torch.from_numpy(Y).cuda()
+    outs = []
+    for mode in ("one", "three"):
+        Dd = torch.from_numpy(D.copy()).cuda()
+        cp, ri, v = (torch.zeros(m + 1, dtype=torch.int64, device="cuda"),
+                     torch.zeros(m * s, dtype=torch.int32, device="cuda"),
+                     torch.zeros(m * s, dtype=torch.float32, device="cuda"))
+        torch.cuda.synchronize()
+        if mode == "one":
+            rm = np.zeros(6)
+            for k in range(3):
+                r2 = np.zeros(2)
+                dl.dl_iterate(ctx, Yd, m, Dd, s, 1, cp, ri, v, r2)
+                rm[2 * k: 2 * k + 2] = r2
+        else:
+            rm = np.zeros(6)
+            dl.dl_iterate(ctx, Yd, m, Dd, s, 3, cp, ri, v, rm)
+        outs.append((rm, Dd.cpu().numpy()))
+    dl.dl_destroy(ctx)
+    np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=0, atol=1e-5)
+    assert np.all(outs[1][0][1::2] <= outs[1][0][0::2] + 1e-6)
