@@ -149,8 +149,15 @@ int ensure_staging(dl_ctx* c) {
 
 // Phase boundaries for optional timing: 0 gram | 1 correlations | 2 omp | 3 colptr scan |
 // 4 accumulate+reduce | 5 atoms | 6 rows | 7 finalize+copy | 8
+// Inside stream capture the record becomes an external event node of the graph.
 void mark(dl_ctx* c, int k) {
-  if (c->prof) cudaEventRecordWithFlags(c->ev[k], c->st, cudaEventRecordExternal);
+  if (!c->prof) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c->st, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(c->ev[k], c->st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(c->ev[k], c->st);
 }
 
 // ---- enqueue helpers (no synchronisation) --------------------------------------
