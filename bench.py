@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE)
+    ap.add_argument("--m", type=int, default=None,
+                    help="override the number of signals (profiling of smaller cases)")
     return ap.parse_args()
 
 
@@ -183,7 +185,7 @@ def run_ours(args):
             pg.barrier(device_ids=[local_rank])
         torch.cuda.synchronize()
 
-    Y, D, spec = synth.workload_inputs(args.workload)
+    Y, D, spec = synth.workload_inputs(args.workload, m=args.m)
     m, p, n, s = spec["m"], spec["p"], spec["n"], spec["s"]
     st = torch.cuda.Stream()
     ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, st)

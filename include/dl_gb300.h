@@ -152,6 +152,29 @@ int dl_iterate(dl_ctx* ctx, const float* Y, int64_t m, float* D, int s, int iter
                int64_t* colptr, int32_t* rowidx, float* val, double* rmse);
 
 /*
+ * dl_gram -- G = D^T D (n x n, row-major, device), the Gram matrix Batch-OMP
+ * works from (the OMP-Box tool of Section 4).  D and G are device pointers.
+ * Asynchronous.  Returns DL_OK, DL_EINVAL or DL_ECUDA.
+ */
+int dl_gram(dl_ctx* ctx, const float* D, float* G);
+
+/*
+ * dl_correlate -- A = Y^T D: A[i*n + j] = d_j^T y_i (m x n, row-major,
+ * device), the correlations alpha0 = D^T y_i OMP starts from (Algorithm 1,
+ * step 1).  Y, D, A are device pointers; m <= m_max.  Asynchronous.
+ * Returns DL_OK, DL_EINVAL or DL_ECUDA.
+ */
+int dl_correlate(dl_ctx* ctx, const float* Y, int64_t m, const float* D, float* A);
+
+/*
+ * dl_uses_tensor_cores -- 1 if this context's shape (p % 4 == 0, p <= 64,
+ * n <= 512) takes the split-TF32 tcgen05 path for D^T Y and D^T D, 0 if it
+ * takes the FP32 CUDA-core path.  The environment variable
+ * DL_FORCE_SIMT_GEMM forces the CUDA-core path.
+ */
+int dl_uses_tensor_cores(dl_ctx* ctx);
+
+/*
  * dl_sync -- wait for the context's stream and report a pending device-side
  * error (DL_ENUMERIC for non-finite inputs met by a kernel) or DL_OK.
  */

@@ -19,6 +19,9 @@ struct dl_ctx {
   // workspace
   float* G = nullptr;
   float* A0 = nullptr;
+  float* Dhi = nullptr;  // TF32 head / tail of D for the tensor-core correlations
+  float* Dlo = nullptr;
+  int use_tc = -1;       // -1 unknown, 0 CUDA-core path, 1 tcgen05 path
   int32_t* sidx = nullptr;
   float* sval = nullptr;
   int32_t* scnt = nullptr;
@@ -50,7 +53,7 @@ struct dl_ctx {
 
 namespace {
 
-constexpr int kKernelsOmp = 3;       // gram, correlations, omp
+constexpr int kKernelsOmp = 4;       // split, gram, correlations, omp
 constexpr int kKernelsScan = 2;      // colptr scan
 constexpr int kKernelsJau = 5;       // accumulate, reduce, atoms, rows, finalize
 
@@ -62,7 +65,7 @@ void free_ctx(dl_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
-  void* ptrs[] = {c->G, c->A0, c->sidx, c->sval, c->scnt, c->bsum, c->err, c->iter, c->rmse,
+  void* ptrs[] = {c->G, c->A0, c->Dhi, c->Dlo, c->sidx, c->sval, c->scnt, c->bsum, c->err, c->iter, c->rmse,
                   c->jw.Upart, c->jw.U, c->jw.epart_a, c->jw.epart_b, c->jw.Dn, c->jw.C,
                   c->hY, c->hD, c->hcolptr, c->hrowidx, c->hval};
   for (void* q : ptrs)
@@ -161,12 +164,33 @@ void mark(dl_ctx* c, int k) {
 }
 
 // ---- enqueue helpers (no synchronisation) --------------------------------------
+// The tensor-core path needs p % 4 == 0, p <= 64, n <= 512 and 16-byte aligned operands;
+// other shapes use the FP32 CUDA-core GEMM.
+bool tc_ok(dl_ctx* c, const float* Y, const float* D) {
+  if (getenv("DL_FORCE_SIMT_GEMM")) return false;
+  return dlk::corr_tc_supported(Y, c->p, c->n, c->lda) &&
+         dlk::corr_tc_supported(D, c->p, c->n, c->n);
+}
+
+cudaError_t enq_gram(dl_ctx* c, const float* D, bool tc) {
+  if (!tc) return dlk::gemm_nt_simt(D, c->n, D, c->n, c->p, c->G, c->n, c->st);
+  cudaError_t e = dlk::split_tf32(D, (int64_t)c->n * c->p, c->Dhi, c->Dlo, c->st);
+  if (e != cudaSuccess) return e;
+  return dlk::corr_tf32x3(D, c->n, c->Dhi, c->Dlo, c->n, c->p, c->G, c->n, c->err, c->st);
+}
+
+cudaError_t enq_corr(dl_ctx* c, const float* Y, int64_t m, const float* D, bool tc) {
+  if (!tc) return dlk::gemm_nt_simt(Y, m, D, c->n, c->p, c->A0, c->lda, c->st);
+  return dlk::corr_tf32x3(Y, m, c->Dhi, c->Dlo, c->n, c->p, c->A0, c->lda, c->err, c->st);
+}
+
 cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
+  const bool tc = tc_ok(c, Y, D);
   mark(c, 0);
-  cudaError_t e = dlk::gemm_nt_simt(D, c->n, D, c->n, c->p, c->G, c->n, c->st);
+  cudaError_t e = enq_gram(c, D, tc);
   if (e != cudaSuccess) return e;
   mark(c, 1);
-  e = dlk::gemm_nt_simt(Y, m, D, c->n, c->p, c->A0, c->lda, c->st);
+  e = enq_corr(c, Y, m, D, tc);
   if (e != cudaSuccess) return e;
   mark(c, 2);
   e = dlk::omp_batch(c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval, c->scnt, c->err,
@@ -258,7 +282,8 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
             dalloc(&c->err, 1) && dalloc(&c->iter, 1) && dalloc(&c->jw.Upart, nslices * ulen) &&
             dalloc(&c->jw.U, ulen) && dalloc(&c->jw.epart_a, (size_t)2 * c->jw.nb_accum) &&
             dalloc(&c->jw.epart_b, (size_t)c->jw.nb_row) && dalloc(&c->jw.Dn, (size_t)n * p) &&
-            dalloc(&c->jw.C, (size_t)n);
+            dalloc(&c->jw.C, (size_t)n) && dalloc(&c->Dhi, (size_t)n * p) &&
+            dalloc(&c->Dlo, (size_t)n * p);
   if (!ok) {
     cudaGetLastError();
     free_ctx(c);
@@ -319,6 +344,36 @@ int dl_phase_times(dl_ctx* c, double* ms, int max_phases) {
   const int k = max_phases < 8 ? max_phases : 8;
   for (int q = 0; q < k; ++q) ms[q] = c->phase_count ? c->phase_ms[q] / c->phase_count : 0.0;
   return 8;
+}
+
+int dl_gram(dl_ctx* c, const float* D, float* G) {
+  if (!c || !D || !G || ptr_kind(D) != 1 || ptr_kind(G) != 1) return DL_EINVAL;
+  DevGuard g(c->dev);
+  const bool tc = tc_ok(c, D, D);
+  DL_CHECK(enq_gram(c, D, tc));
+  DL_CHECK(cudaMemcpyAsync(G, c->G, sizeof(float) * (size_t)c->n * c->n, cudaMemcpyDeviceToDevice, c->st));
+  c->launches += tc ? 2 : 1;
+  return DL_OK;
+}
+
+int dl_correlate(dl_ctx* c, const float* Y, int64_t m, const float* D, float* A) {
+  int rc = check_common(c, m);
+  if (rc) return rc;
+  if (!Y || !D || !A || ptr_kind(Y) != 1 || ptr_kind(D) != 1 || ptr_kind(A) != 1) return DL_EINVAL;
+  DevGuard g(c->dev);
+  const bool tc = tc_ok(c, Y, D);
+  if (tc) DL_CHECK(dlk::split_tf32(D, (int64_t)c->n * c->p, c->Dhi, c->Dlo, c->st));
+  DL_CHECK(enq_corr(c, Y, m, D, tc));
+  if (m > 0)
+    DL_CHECK(cudaMemcpy2DAsync(A, sizeof(float) * c->n, c->A0, sizeof(float) * c->lda,
+                               sizeof(float) * c->n, (size_t)m, cudaMemcpyDeviceToDevice, c->st));
+  c->launches += tc ? 2 : 1;
+  return DL_OK;
+}
+
+int dl_uses_tensor_cores(dl_ctx* c) {
+  if (!c) return DL_EINVAL;
+  return dlk::corr_tc_supported(nullptr, c->p, c->n, c->lda) ? 1 : 0;
 }
 
 int omp_code(dl_ctx* c, const float* Y, int64_t m, const float* D, int s, int64_t* colptr,

@@ -22,6 +22,13 @@ constexpr float kResidRel = 1e-6f;     // residual energy below this * ||y||^2: 
 cudaError_t gemm_nt_simt(const float* A, int64_t rows_a, const float* B, int rows_b, int p, float* C,
                          int64_t ldc, cudaStream_t st);
 
+// FP32-accurate C = A B^T on tcgen05 tensor cores (split TF32, see k_corr_tc.cu).
+// B is given pre-split (B = Bhi + Blo).  Requires corr_tc_supported().
+bool corr_tc_supported(const float* A, int p, int n, int64_t ldc);
+cudaError_t split_tf32(const float* B, int64_t count, float* hi, float* lo, cudaStream_t st);
+cudaError_t corr_tf32x3(const float* A, int64_t rows_a, const float* Bhi, const float* Blo, int n,
+                        int p, float* C, int64_t ldc, int* err, cudaStream_t st);
+
 // ---- OMP ----------------------------------------------------------------------
 // Batch-OMP of m signals from their correlations A0 (row i = D^T y_i, stride lda) and G = D^T D.
 // Writes s slots per signal (atoms ascending, unused slots idx = -1) and the count.

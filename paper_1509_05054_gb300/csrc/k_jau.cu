@@ -233,19 +233,27 @@ __global__ void __launch_bounds__(ROW_THREADS) rows_kernel(
   if (threadIdx.x == 0) epart[blockIdx.x] = se;
 }
 
-__global__ void finalize_kernel(const double* __restrict__ epa, int na, const double* __restrict__ epb,
-                                int nb, double* __restrict__ rmse, int* __restrict__ iter) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One block: strided partial sums in a fixed order, then a fixed-order tree.
+constexpr int FIN_THREADS = 256;
+__global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(
+    const double* __restrict__ epa, int na, const double* __restrict__ epb, int nb,
+    double* __restrict__ rmse, int* __restrict__ iter) {
+  __shared__ double red[FIN_THREADS / 32];
   double ee = 0.0, yy = 0.0, e2 = 0.0;
-  for (int b = 0; b < na; ++b) {
+  for (int b = threadIdx.x; b < na; b += FIN_THREADS) {
     ee += epa[2 * b];
     yy += epa[2 * b + 1];
   }
-  for (int b = 0; b < nb; ++b) e2 += epb[b];
-  const int it = *iter;
-  rmse[2 * it] = yy > 0.0 ? sqrt(ee / yy) : 0.0;
-  rmse[2 * it + 1] = yy > 0.0 ? sqrt(e2 / yy) : 0.0;
-  *iter = it + 1;
+  for (int b = threadIdx.x; b < nb; b += FIN_THREADS) e2 += epb[b];
+  ee = block_sum_d(ee, red);
+  yy = block_sum_d(yy, red);
+  e2 = block_sum_d(e2, red);
+  if (threadIdx.x == 0) {
+    const int it = *iter;
+    rmse[2 * it] = yy > 0.0 ? sqrt(ee / yy) : 0.0;
+    rmse[2 * it + 1] = yy > 0.0 ? sqrt(e2 / yy) : 0.0;
+    *iter = it + 1;
+  }
 }
 
 // ---- CSC helpers ------------------------------------------------------------------
@@ -430,7 +438,7 @@ cudaError_t jau_rows(const float* Y, int p, int64_t m, const float* D, int n, in
 }
 
 cudaError_t jau_finalize(const JauWork& w, double* rmse_out, int* iter, cudaStream_t st) {
-  finalize_kernel<<<1, 32, 0, st>>>(w.epart_a, w.nb_accum, w.epart_b, w.nb_row, rmse_out, iter);
+  finalize_kernel<<<1, FIN_THREADS, 0, st>>>(w.epart_a, w.nb_accum, w.epart_b, w.nb_row, rmse_out, iter);
   return cudaGetLastError();
 }
 

@@ -58,9 +58,13 @@ def load(build_if_missing: bool = True):
         lib.dl_kernel_launches.argtypes = [P]
         lib.dl_kernel_launches.restype = i64
         lib.dl_set_profiling.argtypes = [P, i32]
+        lib.dl_gram.argtypes = [P, P, P]
+        lib.dl_correlate.argtypes = [P, P, i64, P, P]
+        lib.dl_uses_tensor_cores.argtypes = [P]
         lib.dl_phase_times.argtypes = [P, P, i32]
         for name in ("dl_init", "dl_set_stream", "dl_destroy", "omp_code", "jau_update", "dl_iterate",
-                     "dl_sync", "dl_set_profiling", "dl_phase_times"):
+                     "dl_sync", "dl_set_profiling", "dl_phase_times", "dl_gram", "dl_correlate",
+                     "dl_uses_tensor_cores"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -135,6 +139,21 @@ def dl_phase_times(ctx: int) -> dict:
     if rc < 0:
         raise DLError(rc, "dl_phase_times")
     return dict(zip(PHASES, out.tolist()))
+
+
+def dl_gram(ctx: int, D, G) -> None:
+    _check(load().dl_gram(ctx, _ptr(D), _ptr(G)), "dl_gram")
+
+
+def dl_correlate(ctx: int, Y, m: int, D, A) -> None:
+    _check(load().dl_correlate(ctx, _ptr(Y), m, _ptr(D), _ptr(A)), "dl_correlate")
+
+
+def dl_uses_tensor_cores(ctx: int) -> int:
+    rc = load().dl_uses_tensor_cores(ctx)
+    if rc < 0:
+        raise DLError(rc, "dl_uses_tensor_cores")
+    return rc
 
 
 def omp_code(ctx: int, Y, m: int, D, s: int, colptr, rowidx, val) -> None:
