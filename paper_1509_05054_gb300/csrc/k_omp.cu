@@ -25,6 +25,7 @@ namespace dlk {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int OMP_THREADS = 128;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -32,18 +33,43 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Bits of the argmax key that carry the element index t within a lane.
+template <int NT>
+constexpr int tbits() {
+  return NT <= 1 ? 0 : NT <= 2 ? 1 : NT <= 4 ? 2 : NT <= 8 ? 3 : NT <= 16 ? 4 : 5;
+}
+
+// alpha[T] of the calling lane: read the value and mask the element (NaN).
+// Executed by one lane only, so the indexed branch costs a few instructions
+// instead of a select over all NT registers on every lane.
+template <int NT, int T>
+__device__ __forceinline__ void take_case(float (&alpha)[NT], int tsel, float& out, float qnan) {
+  if constexpr (T < NT) {
+    if (tsel == T) {
+      out = alpha[T];
+      alpha[T] = qnan;
+    }
+    take_case<NT, T + 1>(alpha, tsel, out, qnan);
+  }
+}
+
 template <int NT, int SMAX, bool SMEM_PHI>
-__global__ void __launch_bounds__(256) omp_warp_kernel(
+__global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
     const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
     float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err) {
   extern __shared__ float smem_phi[];
+  __shared__ float Lsh[OMP_THREADS / 32][SMAX][SMAX];  // per warp: L[j][q]
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   if (i >= m) return;
+  float(&L)[SMAX][SMAX] = Lsh[wib];
 
   constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
+  constexpr int TB = tbits<NT>();
+  constexpr unsigned TMASK = (1u << TB) - 1u;
+  constexpr unsigned VMASK = 0x7FFFFFFFu & ~TMASK;
   float phi_r[SMEM_PHI ? 1 : NPHI][SMEM_PHI ? 1 : NT];
   float* phi_s = SMEM_PHI ? smem_phi + (size_t)wib * NPHI * NT * 32 : nullptr;
 #define PHI(q, t) (*(SMEM_PHI ? &phi_s[((q) * NT + (t)) * 32 + lane] : &phi_r[SMEM_PHI ? 0 : (q)][SMEM_PHI ? 0 : (t)]))
@@ -63,49 +89,39 @@ __global__ void __launch_bounds__(256) omp_warp_kernel(
     const int j = 32 * t + lane;
     alpha[t] = (j < n) ? A0[i * lda + j] : qnan;
   }
-
   bool bad_in = false;
 #pragma unroll
   for (int t = 0; t < NT; ++t)
     if (32 * t + lane < n && !isfinite(alpha[t])) bad_in = true;
   const bool finite_in = isfinite(yy) && !__any_sync(FULL, bad_in);
+  if (!finite_in && lane == 0) atomicOr(err, ERR_NONFINITE);
 
-  float Lrow[SMAX];  // lane j: row j of L
-  float Lcol[SMAX];  // lane j: Lcol[q] = L[q][j] for q > j
-  float wv[SMAX];    // current w, broadcast to all lanes
-  int Iv[SMAX];      // selected atoms, broadcast to all lanes
+  float wv[SMAX];  // current w, broadcast to all lanes
 #pragma unroll
-  for (int q = 0; q < SMAX; ++q) {
-    Lrow[q] = 0.f;
-    Lcol[q] = 0.f;
-    wv[q] = 0.f;
-    Iv[q] = 0;
-  }
+  for (int q = 0; q < SMAX; ++q) wv[q] = 0.f;
   float invLdiag = 0.f;  // lane j: 1 / L_jj
   float myz = 0.f;       // lane j: z_j
   int myI = -1;          // lane j: I_j
   float rr = yy;
   int k = 0;
-  if (!finite_in && lane == 0) atomicOr(err, ERR_NONFINITE);
 
 #pragma unroll
   for (int step = 0; step < SMAX; ++step) {
     if (step >= s || !finite_in) break;
-    // ---- argmax |alpha| over unselected atoms, lowest index on ties
-    float mloc = 0.f;
+    // ---- argmax |alpha| over unselected atoms.  Key = |alpha| with the low TB
+    // mantissa bits replaced by (NT-1-t): one float max gives the largest value and,
+    // among values equal to 2^-(23-TB) relative, the lowest t; masked (NaN) entries
+    // are ignored by fmaxf.  Across lanes the lowest lane wins.
+    float kmax = 0.f;
 #pragma unroll
-    for (int t = 0; t < NT; ++t) mloc = fmaxf(mloc, fabsf(alpha[t]));
-    const float mval = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mloc)));
-    if (!(mval > 0.f) || !isfinite(mval)) {
-      if (!isfinite(mval) && lane == 0) atomicOr(err, ERR_NONFINITE);
-      break;
-    }
-    unsigned key = 0xffffffffu;
-#pragma unroll
-    for (int t = NT - 1; t >= 0; --t)
-      if (fabsf(alpha[t]) == mval) key = (unsigned)(32 * t + lane);
-    const int sel = (int)__reduce_min_sync(FULL, key);
-    const int tsel = sel >> 5, lsel = sel & 31;
+    for (int t = 0; t < NT; ++t)
+      kmax = fmaxf(kmax, __uint_as_float((__float_as_uint(alpha[t]) & VMASK) | (unsigned)(NT - 1 - t)));
+    const unsigned kbits = __reduce_max_sync(FULL, __float_as_uint(kmax));
+    if ((kbits & VMASK) == 0u) break;  // max |alpha| = 0
+    const unsigned ball = __ballot_sync(FULL, __float_as_uint(kmax) == kbits);
+    const int lsel = __ffs(ball) - 1;
+    const int tsel = NT - 1 - (int)(kbits & TMASK);
+    const int sel = 32 * tsel + lsel;
     const float* __restrict__ Gr = G + (size_t)sel * n;  // row sel == column sel (G symmetric)
 
     // issue the Gram row loads early (needed for phi unless this is the last step)
@@ -120,6 +136,11 @@ __global__ void __launch_bounds__(256) omp_warp_kernel(
     const float gI = (lane < step) ? __ldg(Gr + myI) : 0.f;  // lane q: G[I_q, sel]
     const float gss = __ldg(Gr + sel);
 
+    // the selected alpha (exact, signed) and its masking, on the owning lane only
+    float amine = 0.f;
+    if (lane == lsel) take_case<NT, 0>(alpha, tsel, amine, qnan);
+    const float asel = __shfl_sync(FULL, amine, lsel);
+
     // ---- Cholesky row append: forward substitution L w = G[I, sel]
     float acc = 0.f, wsq = 0.f;
 #pragma unroll
@@ -127,7 +148,8 @@ __global__ void __launch_bounds__(256) omp_warp_kernel(
       if (q >= step) break;
       const float wl = (gI - acc) * invLdiag;  // valid on lane q
       const float wq = __shfl_sync(FULL, wl, q);
-      acc = fmaf(Lrow[q], wq, acc);
+      if (lane > q && lane < step) acc = fmaf(L[lane][q], wq, acc);
+      if (lane == q) L[step][q] = wq;
       wsq = fmaf(wq, wq, wsq);
       wv[q] = wq;
     }
@@ -138,35 +160,14 @@ __global__ void __launch_bounds__(256) omp_warp_kernel(
     }
     const float Lkk = sqrtf(delta);
     const float invL = 1.0f / Lkk;
-
-    // z_k = alpha[sel] / L_kk
-    float amine = 0.f;
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-      if (t == tsel) amine = alpha[t];
-    const float zk = __shfl_sync(FULL, amine, lsel) * invL;
-
-    // record row `step` of L (lane step) and column entries (lanes q < step)
+    const float zk = asel * invL;  // coefficient on the new orthonormal direction
     if (lane == step) {
-#pragma unroll
-      for (int q = 0; q < SMAX; ++q)
-        if (q < step) Lrow[q] = wv[q];
-      Lrow[step] = Lkk;
       invLdiag = invL;
       myz = zk;
       myI = sel;
     }
-#pragma unroll
-    for (int q = 0; q < SMAX; ++q)
-      if (q < step && lane == q) Lcol[step] = wv[q];
-    Iv[step] = sel;
     rr = fmaf(-zk, zk, rr);
     k = step + 1;
-
-    // mask the selected atom
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-      if (t == tsel && lane == lsel) alpha[t] = qnan;
 
     // ---- phi_k and alpha update
     if (need_phi) {
@@ -183,9 +184,11 @@ __global__ void __launch_bounds__(256) omp_warp_kernel(
         alpha[t] = fmaf(-zk, g, alpha[t]);
       }
     }
+    __syncwarp();  // row `step` of L (written by lanes q < step) is read next step
     if (rr <= kResidRel * yy) break;
   }
 #undef PHI
+  __syncwarp();
 
   // ---- back substitution L^T gamma = z
   float gam = 0.f, acc2 = 0.f;
@@ -195,17 +198,21 @@ __global__ void __launch_bounds__(256) omp_warp_kernel(
       const float gl = (myz - acc2) * invLdiag;  // valid on lane q
       const float gq = __shfl_sync(FULL, gl, q);
       if (lane == q) gam = gq;
-      acc2 = fmaf(Lcol[q], gq, acc2);
+      if (lane < q) acc2 = fmaf(L[q][lane], gq, acc2);
     }
   }
 
   // ---- write the support in ascending atom order
+  int rank = 0;
+#pragma unroll
+  for (int q = 0; q < SMAX; ++q) {
+    if (q < k) {
+      const int Iq = __shfl_sync(FULL, myI, q);
+      rank += (Iq < myI) ? 1 : 0;
+    }
+  }
   const int64_t base = i * s;
   if (lane < k) {
-    int rank = 0;
-#pragma unroll
-    for (int q = 0; q < SMAX; ++q)
-      if (q < k && Iv[q] < myI) ++rank;
     oidx[base + rank] = myI;
     oval[base + rank] = gam;
   } else if (lane < s) {
@@ -219,12 +226,12 @@ template <int NT, int SMAX, bool SMEM>
 cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                      int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
                      cudaStream_t st) {
-  int warps = 8;
+  int warps = OMP_THREADS / 32;
   size_t smem = 0;
   if (SMEM) {
     const size_t per_warp = (size_t)(SMAX - 1) * NT * 32 * sizeof(float);
-    warps = (int)((200u * 1024u) / per_warp);
-    if (warps > 8) warps = 8;
+    warps = (int)((190u * 1024u) / per_warp);
+    if (warps > OMP_THREADS / 32) warps = OMP_THREADS / 32;
     if (warps < 1) warps = 1;
     smem = per_warp * warps;
     cudaFuncSetAttribute(omp_warp_kernel<NT, SMAX, SMEM>,
