@@ -18,7 +18,7 @@ namespace dlk {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int ACC_THREADS = 512;
+constexpr int ACC_THREADS = 1024;
 constexpr int ROW_THREADS = 256;
 
 __device__ __forceinline__ float warp_sum(float v) {
