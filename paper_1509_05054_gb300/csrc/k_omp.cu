@@ -39,21 +39,45 @@ constexpr int tbits() {
   return NT <= 1 ? 0 : NT <= 2 ? 1 : NT <= 4 ? 2 : NT <= 8 ? 3 : NT <= 16 ? 4 : 5;
 }
 
-// alpha[T] of the calling lane: read the value and mask the element (NaN).
-// Executed by one lane only, so the indexed branch costs a few instructions
-// instead of a select over all NT registers on every lane.
-template <int NT, int T>
-__device__ __forceinline__ void take_case(float (&alpha)[NT], int tsel, float& out, float qnan) {
-  if constexpr (T < NT) {
-    if (tsel == T) {
-      out = alpha[T];
-      alpha[T] = qnan;
-    }
-    take_case<NT, T + 1>(alpha, tsel, out, qnan);
+// alpha[tsel] of the calling lane: read the value and mask the element (NaN).
+// Executed by the owning lane only; the dense switch becomes an indexed branch,
+// a few instructions instead of a select over all NT registers on every lane.
+template <int NT>
+__device__ __forceinline__ float take(float (&alpha)[NT], int tsel, float qnan) {
+  float out = 0.f;
+#define DL_TAKE_CASE(T)                       \
+  case T:                                     \
+    if constexpr (T < NT) {                   \
+      out = alpha[T < NT ? T : 0];            \
+      alpha[T < NT ? T : 0] = qnan;           \
+    }                                         \
+    break;
+  switch (tsel) {
+    DL_TAKE_CASE(0) DL_TAKE_CASE(1) DL_TAKE_CASE(2) DL_TAKE_CASE(3) DL_TAKE_CASE(4)
+    DL_TAKE_CASE(5) DL_TAKE_CASE(6) DL_TAKE_CASE(7) DL_TAKE_CASE(8) DL_TAKE_CASE(9)
+    DL_TAKE_CASE(10) DL_TAKE_CASE(11) DL_TAKE_CASE(12) DL_TAKE_CASE(13) DL_TAKE_CASE(14)
+    DL_TAKE_CASE(15) DL_TAKE_CASE(16) DL_TAKE_CASE(17) DL_TAKE_CASE(18) DL_TAKE_CASE(19)
+    DL_TAKE_CASE(20) DL_TAKE_CASE(21) DL_TAKE_CASE(22) DL_TAKE_CASE(23) DL_TAKE_CASE(24)
+    DL_TAKE_CASE(25) DL_TAKE_CASE(26) DL_TAKE_CASE(27) DL_TAKE_CASE(28) DL_TAKE_CASE(29)
+    DL_TAKE_CASE(30) DL_TAKE_CASE(31)
+    default: break;
+  }
+#undef DL_TAKE_CASE
+  return out;
+}
+
+// Maximum of the packed argmax keys of the lane's NT elements (balanced tree).
+template <int NT, int LO, int CNT>
+__device__ __forceinline__ float key_max(const float (&alpha)[NT], unsigned vmask) {
+  if constexpr (CNT == 1) {
+    return __uint_as_float((__float_as_uint(alpha[LO]) & vmask) | (unsigned)(NT - 1 - LO));
+  } else {
+    return fmaxf(key_max<NT, LO, CNT / 2>(alpha, vmask),
+                 key_max<NT, LO + CNT / 2, CNT - CNT / 2>(alpha, vmask));
   }
 }
 
-template <int NT, int SMAX, bool SMEM_PHI>
+template <int NT, int SMAX, bool SMEM_PHI, bool FULLN>
 __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
     const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
@@ -87,12 +111,12 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
     const int j = 32 * t + lane;
-    alpha[t] = (j < n) ? A0[i * lda + j] : qnan;
+    alpha[t] = (FULLN || j < n) ? A0[i * lda + j] : qnan;
   }
   bool bad_in = false;
 #pragma unroll
   for (int t = 0; t < NT; ++t)
-    if (32 * t + lane < n && !isfinite(alpha[t])) bad_in = true;
+    if ((FULLN || 32 * t + lane < n) && !isfinite(alpha[t])) bad_in = true;
   const bool finite_in = isfinite(yy) && !__any_sync(FULL, bad_in);
   if (!finite_in && lane == 0) atomicOr(err, ERR_NONFINITE);
 
@@ -112,10 +136,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     // mantissa bits replaced by (NT-1-t): one float max gives the largest value and,
     // among values equal to 2^-(23-TB) relative, the lowest t; masked (NaN) entries
     // are ignored by fmaxf.  Across lanes the lowest lane wins.
-    float kmax = 0.f;
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-      kmax = fmaxf(kmax, __uint_as_float((__float_as_uint(alpha[t]) & VMASK) | (unsigned)(NT - 1 - t)));
+    const float kmax = fmaxf(0.f, key_max<NT, 0, NT>(alpha, VMASK));
     const unsigned kbits = __reduce_max_sync(FULL, __float_as_uint(kmax));
     if ((kbits & VMASK) == 0u) break;  // max |alpha| = 0
     const unsigned ball = __ballot_sync(FULL, __float_as_uint(kmax) == kbits);
@@ -130,7 +151,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         const int j = 32 * t + lane;
-        PHI(step < NPHI ? step : 0, t) = (j < n) ? __ldg(Gr + j) : 0.f;
+        PHI(step < NPHI ? step : 0, t) = (FULLN || j < n) ? __ldg(Gr + j) : 0.f;
       }
     }
     const float gI = (lane < step) ? __ldg(Gr + myI) : 0.f;  // lane q: G[I_q, sel]
@@ -138,7 +159,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
 
     // the selected alpha (exact, signed) and its masking, on the owning lane only
     float amine = 0.f;
-    if (lane == lsel) take_case<NT, 0>(alpha, tsel, amine, qnan);
+    if (lane == lsel) amine = take<NT>(alpha, tsel, qnan);
     const float asel = __shfl_sync(FULL, amine, lsel);
 
     // ---- Cholesky row append: forward substitution L w = G[I, sel]
@@ -158,8 +179,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
       if (!isfinite(delta) && lane == 0) atomicOr(err, ERR_NONFINITE);
       break;
     }
-    const float Lkk = sqrtf(delta);
-    const float invL = 1.0f / Lkk;
+    const float invL = __frsqrt_rn(delta);  // 1 / L_kk, correctly rounded
     const float zk = asel * invL;  // coefficient on the new orthonormal direction
     if (lane == step) {
       invLdiag = invL;
@@ -222,7 +242,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
   if (lane == 0) ocnt[i] = k;
 }
 
-template <int NT, int SMAX, bool SMEM>
+template <int NT, int SMAX, bool SMEM, bool FULLN>
 cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                      int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
                      cudaStream_t st) {
@@ -234,11 +254,11 @@ cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const 
     if (warps > OMP_THREADS / 32) warps = OMP_THREADS / 32;
     if (warps < 1) warps = 1;
     smem = per_warp * warps;
-    cudaFuncSetAttribute(omp_warp_kernel<NT, SMAX, SMEM>,
+    cudaFuncSetAttribute(omp_warp_kernel<NT, SMAX, SMEM, FULLN>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   const int64_t blocks = (m + warps - 1) / warps;
-  omp_warp_kernel<NT, SMAX, SMEM><<<(unsigned)blocks, warps * 32, smem, st>>>(
+  omp_warp_kernel<NT, SMAX, SMEM, FULLN><<<(unsigned)blocks, warps * 32, smem, st>>>(
       A0, lda, G, n, Y, p, m, s, idx, val, cnt, err);
   return cudaGetLastError();
 }
@@ -253,10 +273,10 @@ template <int NT, int SMAX>
 cudaError_t pick_store(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                        int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
                        cudaStream_t st) {
-  if constexpr (fits_regs<NT, SMAX>())
-    return launch_t<NT, SMAX, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
-  else
-    return launch_t<NT, SMAX, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  constexpr bool SM = !fits_regs<NT, SMAX>();
+  if (n == 32 * NT)
+    return launch_t<NT, SMAX, SM, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  return launch_t<NT, SMAX, SM, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
 }
 
 template <int NT>
