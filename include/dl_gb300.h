@@ -167,6 +167,34 @@ int dl_gram(dl_ctx* ctx, const float* D, float* G);
 int dl_correlate(dl_ctx* ctx, const float* Y, int64_t m, const float* D, float* A);
 
 /*
+ * dl_correlate_noalloc -- the correlations of dl_correlate, A = Y^T D
+ * (A[i*n + j] = d_j^T y_i, m x n row-major), computed without allocating any
+ * device memory and without a context.  The paper has no counterpart: this is
+ * an interface for callers that cannot call cudaMalloc -- code whose device
+ * memory is entirely reserved by another allocator (a framework's caching pool
+ * or a fixed arena) and code on a latency-critical path that cannot accept an
+ * allocation's implicit synchronisation.
+ *   Y, D, A  device pointers owned by the caller (inputs Y, D; output A).
+ *   p, n     1 <= p <= DL_NOALLOC_MAX_P, 1 <= n <= DL_NOALLOC_MAX_N; larger
+ *            sizes return DL_EINVAL.
+ *   stream   cudaStream_t the work is enqueued on (asynchronous).
+ * Scratch: the TF32 head/tail split of D lives in a fixed file-scope device
+ * array of 2 * DL_NOALLOC_MAX_N * DL_NOALLOC_MAX_P floats (256 KB) plus an
+ * error word, held on every GPU that loads the library until the process
+ * exits.  The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress, no allocation); make that first call before any
+ * stream capture.  Every call on a device shares the array and it keeps the
+ * previous call's contents (the error word is cleared by each call), so calls
+ * whose executions overlap on the GPU (different streams) race: order them.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Returns DL_OK, DL_EINVAL or DL_ECUDA.
+ */
+#define DL_NOALLOC_MAX_N 512
+#define DL_NOALLOC_MAX_P 64
+int dl_correlate_noalloc(const float* Y, int64_t m, const float* D, int p, int n, float* A,
+                         void* stream);
+
+/*
  * dl_uses_tensor_cores -- 1 if this context's shape (p % 4 == 0, p <= 64,
  * n <= 512) takes the split-TF32 tcgen05 path for D^T Y and D^T D, 0 if it
  * takes the FP32 CUDA-core path.  The environment variable

@@ -61,10 +61,11 @@ def load(build_if_missing: bool = True):
         lib.dl_gram.argtypes = [P, P, P]
         lib.dl_correlate.argtypes = [P, P, i64, P, P]
         lib.dl_uses_tensor_cores.argtypes = [P]
+        lib.dl_correlate_noalloc.argtypes = [P, i64, P, i32, i32, P, P]
         lib.dl_phase_times.argtypes = [P, P, i32]
         for name in ("dl_init", "dl_set_stream", "dl_destroy", "omp_code", "jau_update", "dl_iterate",
                      "dl_sync", "dl_set_profiling", "dl_phase_times", "dl_gram", "dl_correlate",
-                     "dl_uses_tensor_cores"):
+                     "dl_uses_tensor_cores", "dl_correlate_noalloc"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -147,6 +148,14 @@ def dl_gram(ctx: int, D, G) -> None:
 
 def dl_correlate(ctx: int, Y, m: int, D, A) -> None:
     _check(load().dl_correlate(ctx, _ptr(Y), m, _ptr(D), _ptr(A)), "dl_correlate")
+
+
+def dl_correlate_noalloc(Y, m: int, D, p: int, n: int, A, stream=None) -> None:
+    """A = Y^T D with no device allocation (for callers that cannot allocate:
+    their memory is reserved by another allocator, or an allocation's implicit
+    synchronisation is not acceptable).  p <= 64, n <= 512."""
+    _check(load().dl_correlate_noalloc(_ptr(Y), m, _ptr(D), p, n, _ptr(A), _stream_ptr(stream)),
+           "dl_correlate_noalloc")
 
 
 def dl_uses_tensor_cores(ctx: int) -> int:
