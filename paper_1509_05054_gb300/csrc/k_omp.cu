@@ -39,32 +39,40 @@ constexpr int tbits() {
   return NT <= 1 ? 0 : NT <= 2 ? 1 : NT <= 4 ? 2 : NT <= 8 ? 3 : NT <= 16 ? 4 : 5;
 }
 
-// alpha[tsel] of the calling lane: read the value and mask the element (NaN).
-// Executed by the owning lane only; the dense switch becomes an indexed branch,
-// a few instructions instead of a select over all NT registers on every lane.
-template <int NT>
-__device__ __forceinline__ float take(float (&alpha)[NT], int tsel, float qnan) {
-  float out = 0.f;
-#define DL_TAKE_CASE(T)                       \
-  case T:                                     \
-    if constexpr (T < NT) {                   \
-      out = alpha[T < NT ? T : 0];            \
-      alpha[T < NT ? T : 0] = qnan;           \
-    }                                         \
+// On the lane owning atom sel = 32*tsel + lane: read alpha[tsel] and mask it
+// (NaN), and read phi_q[tsel] for q < step (these are w_q = q_q^T d_sel, the new
+// row of the Cholesky factor).  Executed by one lane; the dense switch becomes
+// an indexed branch instead of a select over all NT registers on every lane.
+template <int NT, int NPHI>
+struct Take {
+  template <typename PhiAt>
+  __device__ __forceinline__ static float run(float (&alpha)[NT], PhiAt phi, int tsel, int step,
+                                              float (&wl)[NPHI], float qnan) {
+    float out = 0.f;
+#define DL_TAKE_CASE(T)                                     \
+  case T:                                                   \
+    if constexpr (T < NT) {                                 \
+      constexpr int TT = T < NT ? T : 0;                    \
+      out = alpha[TT];                                      \
+      alpha[TT] = qnan;                                     \
+      _Pragma("unroll") for (int q = 0; q < NPHI; ++q)      \
+        if (q < step) wl[q] = phi(q, TT);                   \
+    }                                                       \
     break;
-  switch (tsel) {
-    DL_TAKE_CASE(0) DL_TAKE_CASE(1) DL_TAKE_CASE(2) DL_TAKE_CASE(3) DL_TAKE_CASE(4)
-    DL_TAKE_CASE(5) DL_TAKE_CASE(6) DL_TAKE_CASE(7) DL_TAKE_CASE(8) DL_TAKE_CASE(9)
-    DL_TAKE_CASE(10) DL_TAKE_CASE(11) DL_TAKE_CASE(12) DL_TAKE_CASE(13) DL_TAKE_CASE(14)
-    DL_TAKE_CASE(15) DL_TAKE_CASE(16) DL_TAKE_CASE(17) DL_TAKE_CASE(18) DL_TAKE_CASE(19)
-    DL_TAKE_CASE(20) DL_TAKE_CASE(21) DL_TAKE_CASE(22) DL_TAKE_CASE(23) DL_TAKE_CASE(24)
-    DL_TAKE_CASE(25) DL_TAKE_CASE(26) DL_TAKE_CASE(27) DL_TAKE_CASE(28) DL_TAKE_CASE(29)
-    DL_TAKE_CASE(30) DL_TAKE_CASE(31)
-    default: break;
-  }
+    switch (tsel) {
+      DL_TAKE_CASE(0) DL_TAKE_CASE(1) DL_TAKE_CASE(2) DL_TAKE_CASE(3) DL_TAKE_CASE(4)
+      DL_TAKE_CASE(5) DL_TAKE_CASE(6) DL_TAKE_CASE(7) DL_TAKE_CASE(8) DL_TAKE_CASE(9)
+      DL_TAKE_CASE(10) DL_TAKE_CASE(11) DL_TAKE_CASE(12) DL_TAKE_CASE(13) DL_TAKE_CASE(14)
+      DL_TAKE_CASE(15) DL_TAKE_CASE(16) DL_TAKE_CASE(17) DL_TAKE_CASE(18) DL_TAKE_CASE(19)
+      DL_TAKE_CASE(20) DL_TAKE_CASE(21) DL_TAKE_CASE(22) DL_TAKE_CASE(23) DL_TAKE_CASE(24)
+      DL_TAKE_CASE(25) DL_TAKE_CASE(26) DL_TAKE_CASE(27) DL_TAKE_CASE(28) DL_TAKE_CASE(29)
+      DL_TAKE_CASE(30) DL_TAKE_CASE(31)
+      default: break;
+    }
 #undef DL_TAKE_CASE
-  return out;
-}
+    return out;
+  }
+};
 
 // Maximum of the packed argmax keys of the lane's NT elements (balanced tree).
 template <int NT, int LO, int CNT>
@@ -154,25 +162,26 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
         PHI(step < NPHI ? step : 0, t) = (FULLN || j < n) ? __ldg(Gr + j) : 0.f;
       }
     }
-    const float gI = (lane < step) ? __ldg(Gr + myI) : 0.f;  // lane q: G[I_q, sel]
     const float gss = __ldg(Gr + sel);
 
-    // the selected alpha (exact, signed) and its masking, on the owning lane only
+    // the selected alpha (exact, signed), its masking, and the Cholesky row
+    // w_q = phi_q[sel] (q < step), on the owning lane; then broadcast
     float amine = 0.f;
-    if (lane == lsel) amine = take<NT>(alpha, tsel, qnan);
+    float wl[NPHI];
+#pragma unroll
+    for (int q = 0; q < NPHI; ++q) wl[q] = 0.f;
+    if (lane == lsel) {
+      auto phi_at = [&](int q, int t) -> float { return PHI(q, t); };
+      amine = Take<NT, NPHI>::run(alpha, phi_at, tsel, step, wl, qnan);
+    }
     const float asel = __shfl_sync(FULL, amine, lsel);
-
-    // ---- Cholesky row append: forward substitution L w = G[I, sel]
-    float acc = 0.f, wsq = 0.f;
+    float wsq = 0.f;
 #pragma unroll
     for (int q = 0; q < SMAX - 1; ++q) {
       if (q >= step) break;
-      const float wl = (gI - acc) * invLdiag;  // valid on lane q
-      const float wq = __shfl_sync(FULL, wl, q);
-      if (lane > q && lane < step) acc = fmaf(L[lane][q], wq, acc);
-      if (lane == q) L[step][q] = wq;
-      wsq = fmaf(wq, wq, wsq);
-      wv[q] = wq;
+      wv[q] = __shfl_sync(FULL, wl[q], lsel);
+      wsq = fmaf(wv[q], wv[q], wsq);
+      if (lane == q) L[step][q] = wv[q];
     }
     const float delta = gss - wsq;
     if (!(delta > kPivotMin)) {
@@ -256,6 +265,9 @@ cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const 
     smem = per_warp * warps;
     cudaFuncSetAttribute(omp_warp_kernel<NT, SMAX, SMEM, FULLN>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  } else {  // Gram rows are re-read through L1: give L1 the shared-memory carveout
+    cudaFuncSetAttribute(omp_warp_kernel<NT, SMAX, SMEM, FULLN>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
   }
   const int64_t blocks = (m + warps - 1) / warps;
   omp_warp_kernel<NT, SMAX, SMEM, FULLN><<<(unsigned)blocks, warps * 32, smem, st>>>(
