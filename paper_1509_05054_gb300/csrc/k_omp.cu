@@ -2,21 +2,24 @@
 // tool named in Section 4 implements the Cholesky "Batch-OMP" of [RZE08]).
 //
 // Per signal y with correlations alpha0 = D^T y and Gram G = D^T D, step k:
-//   sel   = argmax_{j not selected} |alpha_j|        (lowest index on ties)
-//   w     = L^{-1} G[I, sel],  delta = G[sel,sel] - w.w,  L gets row (w, sqrt(delta))
-//   z_k   = alpha[sel] / L_kk        (coefficient of y on the new orthonormal direction)
-//   phi_k = (G[:, sel] - sum_{q<k} w_q phi_q) / L_kk    (= D^T q_k)
-//   alpha = alpha - z_k phi_k                             (= D^T r_k)
+//   sel   = argmax_{j not selected} |alpha_j|                (lowest index on ties)
+//   w_q   = q_q^T d_sel (q < k): the new row of the Cholesky factor of G[I,I]
+//   delta = G[sel,sel] - w.w,  c_k = 1/sqrt(delta) = 1/L_kk
+//   z_k   = c_k alpha[sel]     (coefficient of y on the new orthonormal direction q_k)
+//   u_k   = G[:, sel] - sum_{q<k} (w_q c_q) u_q       (D^T q_k = c_k u_k)
+//   alpha = alpha - (z_k c_k) u_k                         (= D^T r_k)
 // and at the end x_I = L^{-T} z.  This is the Gram-Schmidt (progressive
 // Cholesky) form of Batch-OMP: alpha is updated with one new vector per step
-// instead of being recomputed as alpha0 - G[:,I] gamma, which needs the same
-// n*k multiply-adds but no triangular solve per step.  Both give the same
-// alpha in exact arithmetic.
+// instead of being recomputed as alpha0 - G[:,I] gamma; the multiply-adds are
+// the same n*k per step, there is no triangular solve per step, and w_q is read
+// from the stored vectors (w_q = c_q u_q[sel]) instead of a forward
+// substitution.  Identical to the oracle's Batch-OMP in exact arithmetic.
 //
-// Lane l of the warp holds alpha[32t + l], t < NT = ceil(n/32), in registers,
-// and the phi vectors either in registers (small n*s) or in shared memory.
-// Selected atoms are masked by setting their alpha to NaN, which fmaxf and the
-// equality test of the argmax both ignore.
+// Lane l of the warp holds alpha[32t + l], t < NT = ceil(n/32), as NT/2 float2
+// pairs (elements t = 2v, 2v+1) so the updates issue as packed FP32x2 FMAs
+// (__ffma2_rn, sm_100 family); the u vectors live in registers (small n*s) or
+// in shared memory.  Selected atoms are masked by setting their alpha to NaN,
+// which the argmax ignores.
 #include "dl_internal.cuh"
 
 #include <math.h>
@@ -39,24 +42,47 @@ constexpr int tbits() {
   return NT <= 1 ? 0 : NT <= 2 ? 1 : NT <= 4 ? 2 : NT <= 8 ? 3 : NT <= 16 ? 4 : 5;
 }
 
+template <int NT>
+__device__ __forceinline__ float elem(const float2 (&a)[NT / 2], int t) {
+  return (t & 1) ? a[t >> 1].y : a[t >> 1].x;
+}
+
+// Argmax key of element t: |alpha| with the low TB mantissa bits replaced by
+// (NT-1-t).  The float maximum of the keys gives the largest |alpha| and, among
+// values equal to within 2^-(23-TB) relative, the lowest t; NaN (masked)
+// elements are ignored by fmaxf.
+template <int NT, int LO, int CNT>
+__device__ __forceinline__ float key_max(const float2 (&a)[NT / 2], unsigned vmask) {
+  if constexpr (CNT == 1) {
+    return __uint_as_float((__float_as_uint(elem<NT>(a, LO)) & vmask) | (unsigned)(NT - 1 - LO));
+  } else {
+    return fmaxf(key_max<NT, LO, CNT / 2>(a, vmask), key_max<NT, LO + CNT / 2, CNT - CNT / 2>(a, vmask));
+  }
+}
+
 // On the lane owning atom sel = 32*tsel + lane: read alpha[tsel] and mask it
-// (NaN), and read phi_q[tsel] for q < step (these are w_q = q_q^T d_sel, the new
-// row of the Cholesky factor).  Executed by one lane; the dense switch becomes
-// an indexed branch instead of a select over all NT registers on every lane.
+// (NaN), and read u_q[tsel] for q < step.  Executed by one lane; the dense
+// switch becomes an indexed branch instead of a select over all NT registers
+// on every lane.
 template <int NT, int NPHI>
 struct Take {
-  template <typename PhiAt>
-  __device__ __forceinline__ static float run(float (&alpha)[NT], PhiAt phi, int tsel, int step,
-                                              float (&wl)[NPHI], float qnan) {
+  template <typename UAt>
+  __device__ __forceinline__ static float run(float2 (&alpha)[NT / 2], UAt u_at, int tsel, int step,
+                                              float (&ul)[NPHI], float qnan) {
     float out = 0.f;
 #define DL_TAKE_CASE(T)                                     \
   case T:                                                   \
     if constexpr (T < NT) {                                 \
       constexpr int TT = T < NT ? T : 0;                    \
-      out = alpha[TT];                                      \
-      alpha[TT] = qnan;                                     \
+      if constexpr (TT & 1) {                               \
+        out = alpha[TT >> 1].y;                             \
+        alpha[TT >> 1].y = qnan;                            \
+      } else {                                              \
+        out = alpha[TT >> 1].x;                             \
+        alpha[TT >> 1].x = qnan;                            \
+      }                                                     \
       _Pragma("unroll") for (int q = 0; q < NPHI; ++q)      \
-        if (q < step) wl[q] = phi(q, TT);                   \
+        if (q < step) ul[q] = u_at(q, TT);                  \
     }                                                       \
     break;
     switch (tsel) {
@@ -74,37 +100,31 @@ struct Take {
   }
 };
 
-// Maximum of the packed argmax keys of the lane's NT elements (balanced tree).
-template <int NT, int LO, int CNT>
-__device__ __forceinline__ float key_max(const float (&alpha)[NT], unsigned vmask) {
-  if constexpr (CNT == 1) {
-    return __uint_as_float((__float_as_uint(alpha[LO]) & vmask) | (unsigned)(NT - 1 - LO));
-  } else {
-    return fmaxf(key_max<NT, LO, CNT / 2>(alpha, vmask),
-                 key_max<NT, LO + CNT / 2, CNT - CNT / 2>(alpha, vmask));
-  }
-}
-
-template <int NT, int SMAX, bool SMEM_PHI, bool FULLN>
+template <int NT, int SMAX, bool SMEM_U, bool FULLN>
 __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
     const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
     float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err) {
-  extern __shared__ float smem_phi[];
-  __shared__ float Lsh[OMP_THREADS / 32][SMAX][SMAX];  // per warp: L[j][q]
+  static_assert(NT >= 2 && NT % 2 == 0, "alpha is held in float2 pairs");
+  constexpr int NV = NT / 2;
+  constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
+  constexpr int TB = tbits<NT>();
+  constexpr unsigned TMASK = (1u << TB) - 1u;
+  constexpr unsigned VMASK = 0x7FFFFFFFu & ~TMASK;
+
+  extern __shared__ float2 smem_u[];
+  __shared__ float Lsh[OMP_THREADS / 32][SMAX][SMAX];  // per warp: L[j][q] (q < j)
+  __shared__ float Csh[OMP_THREADS / 32][SMAX];        // per warp: c_q = 1/L_qq
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   if (i >= m) return;
   float(&L)[SMAX][SMAX] = Lsh[wib];
+  float(&C)[SMAX] = Csh[wib];
 
-  constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
-  constexpr int TB = tbits<NT>();
-  constexpr unsigned TMASK = (1u << TB) - 1u;
-  constexpr unsigned VMASK = 0x7FFFFFFFu & ~TMASK;
-  float phi_r[SMEM_PHI ? 1 : NPHI][SMEM_PHI ? 1 : NT];
-  float* phi_s = SMEM_PHI ? smem_phi + (size_t)wib * NPHI * NT * 32 : nullptr;
-#define PHI(q, t) (*(SMEM_PHI ? &phi_s[((q) * NT + (t)) * 32 + lane] : &phi_r[SMEM_PHI ? 0 : (q)][SMEM_PHI ? 0 : (t)]))
+  float2 u_r[SMEM_U ? 1 : NPHI][SMEM_U ? 1 : NV];
+  float2* u_s = SMEM_U ? smem_u + (size_t)wib * NPHI * NV * 32 : nullptr;
+#define UV(q, v) (*(SMEM_U ? &u_s[((q) * NV + (v)) * 32 + lane] : &u_r[SMEM_U ? 0 : (q)][SMEM_U ? 0 : (v)]))
 
   // ||y||^2 for the residual stop rule and the non-finite check
   float yy = 0.f;
@@ -113,25 +133,22 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     yy = fmaf(v, v, yy);
   }
   yy = warp_sum(yy);
-
-  float alpha[NT];
-  const float qnan = __int_as_float(0x7fc00000);
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    const int j = 32 * t + lane;
-    alpha[t] = (FULLN || j < n) ? A0[i * lda + j] : qnan;
-  }
-  bool bad_in = false;
-#pragma unroll
-  for (int t = 0; t < NT; ++t)
-    if ((FULLN || 32 * t + lane < n) && !isfinite(alpha[t])) bad_in = true;
-  const bool finite_in = isfinite(yy) && !__any_sync(FULL, bad_in);
+  const bool finite_in = isfinite(yy);  // a non-finite D shows up as a non-finite pivot
   if (!finite_in && lane == 0) atomicOr(err, ERR_NONFINITE);
 
-  float wv[SMAX];  // current w, broadcast to all lanes
+  const float qnan = __int_as_float(0x7fc00000);
+  float2 alpha[NV];
 #pragma unroll
-  for (int q = 0; q < SMAX; ++q) wv[q] = 0.f;
-  float invLdiag = 0.f;  // lane j: 1 / L_jj
+  for (int v = 0; v < NV; ++v) {
+    const int j0 = 64 * v + lane, j1 = j0 + 32;
+    alpha[v].x = (FULLN || j0 < n) ? A0[i * lda + j0] : qnan;
+    alpha[v].y = (FULLN || j1 < n) ? A0[i * lda + j1] : qnan;
+  }
+
+  float negaw[SMAX];  // -(w_q c_q), broadcast to all lanes
+#pragma unroll
+  for (int q = 0; q < SMAX; ++q) negaw[q] = 0.f;
+  float invLdiag = 0.f;  // lane j: c_j = 1 / L_jj
   float myz = 0.f;       // lane j: z_j
   int myI = -1;          // lane j: I_j
   float rr = yy;
@@ -140,10 +157,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
 #pragma unroll
   for (int step = 0; step < SMAX; ++step) {
     if (step >= s || !finite_in) break;
-    // ---- argmax |alpha| over unselected atoms.  Key = |alpha| with the low TB
-    // mantissa bits replaced by (NT-1-t): one float max gives the largest value and,
-    // among values equal to 2^-(23-TB) relative, the lowest t; masked (NaN) entries
-    // are ignored by fmaxf.  Across lanes the lowest lane wins.
+    // ---- argmax |alpha| over unselected atoms (see key_max); lowest lane on ties
     const float kmax = fmaxf(0.f, key_max<NT, 0, NT>(alpha, VMASK));
     const unsigned kbits = __reduce_max_sync(FULL, __float_as_uint(kmax));
     if ((kbits & VMASK) == 0u) break;  // max |alpha| = 0
@@ -153,70 +167,79 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     const int sel = 32 * tsel + lsel;
     const float* __restrict__ Gr = G + (size_t)sel * n;  // row sel == column sel (G symmetric)
 
-    // issue the Gram row loads early (needed for phi unless this is the last step)
-    const bool need_phi = (step + 1 < s) && (step + 1 < SMAX);
-    if (need_phi) {
+    // issue the Gram row loads early (needed unless this is the last step)
+    const bool need_u = (step + 1 < s) && (step + 1 < SMAX);
+    if (need_u) {
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const int j = 32 * t + lane;
-        PHI(step < NPHI ? step : 0, t) = (FULLN || j < n) ? __ldg(Gr + j) : 0.f;
+      for (int v = 0; v < NV; ++v) {
+        const int j0 = 64 * v + lane, j1 = j0 + 32;
+        float2 g;
+        g.x = (FULLN || j0 < n) ? __ldg(Gr + j0) : 0.f;
+        g.y = (FULLN || j1 < n) ? __ldg(Gr + j1) : 0.f;
+        UV(step < NPHI ? step : 0, v) = g;
       }
     }
     const float gss = __ldg(Gr + sel);
 
-    // the selected alpha (exact, signed), its masking, and the Cholesky row
-    // w_q = phi_q[sel] (q < step), on the owning lane; then broadcast
+    // alpha[sel] (exact, signed), its masking, and u_q[sel] on the owning lane
     float amine = 0.f;
-    float wl[NPHI];
+    float ul[NPHI];
 #pragma unroll
-    for (int q = 0; q < NPHI; ++q) wl[q] = 0.f;
+    for (int q = 0; q < NPHI; ++q) ul[q] = 0.f;
     if (lane == lsel) {
-      auto phi_at = [&](int q, int t) -> float { return PHI(q, t); };
-      amine = Take<NT, NPHI>::run(alpha, phi_at, tsel, step, wl, qnan);
+      auto u_at = [&](int q, int t) -> float {
+        const float2 pr = UV(q, t >> 1);
+        return (t & 1) ? pr.y : pr.x;
+      };
+      amine = Take<NT, NPHI>::run(alpha, u_at, tsel, step, ul, qnan);
     }
     const float asel = __shfl_sync(FULL, amine, lsel);
     float wsq = 0.f;
 #pragma unroll
     for (int q = 0; q < SMAX - 1; ++q) {
       if (q >= step) break;
-      wv[q] = __shfl_sync(FULL, wl[q], lsel);
-      wsq = fmaf(wv[q], wv[q], wsq);
-      if (lane == q) L[step][q] = wv[q];
+      const float cq = C[q];
+      const float wq = __shfl_sync(FULL, ul[q], lsel) * cq;  // w_q = c_q u_q[sel]
+      wsq = fmaf(wq, wq, wsq);
+      negaw[q] = -wq * cq;
+      if (lane == q) L[step][q] = wq;
     }
     const float delta = gss - wsq;
     if (!(delta > kPivotMin)) {
       if (!isfinite(delta) && lane == 0) atomicOr(err, ERR_NONFINITE);
       break;
     }
-    const float invL = __frsqrt_rn(delta);  // 1 / L_kk, correctly rounded
-    const float zk = asel * invL;  // coefficient on the new orthonormal direction
+    const float ck = __frsqrt_rn(delta);  // c_k = 1 / L_kk, correctly rounded
+    const float zk = asel * ck;
     if (lane == step) {
-      invLdiag = invL;
+      invLdiag = ck;
       myz = zk;
       myI = sel;
     }
+    if (lane == 0) C[step] = ck;
     rr = fmaf(-zk, zk, rr);
     k = step + 1;
 
-    // ---- phi_k and alpha update
-    if (need_phi) {
+    // ---- u_k and alpha update, two elements per packed FMA
+    if (need_u) {
+      const float nz = -zk * ck;
+      const float2 nz2 = make_float2(nz, nz);
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        float g = PHI(step < NPHI ? step : 0, t);
+      for (int v = 0; v < NV; ++v) {
+        float2 g = UV(step < NPHI ? step : 0, v);
 #pragma unroll
         for (int q = 0; q < SMAX - 1; ++q) {
           if (q >= step) break;
-          g = fmaf(-wv[q], PHI(q, t), g);
+          g = __ffma2_rn(make_float2(negaw[q], negaw[q]), UV(q, v), g);
         }
-        g *= invL;
-        PHI(step < NPHI ? step : 0, t) = g;
-        alpha[t] = fmaf(-zk, g, alpha[t]);
+        UV(step < NPHI ? step : 0, v) = g;
+        alpha[v] = __ffma2_rn(nz2, g, alpha[v]);
       }
     }
-    __syncwarp();  // row `step` of L (written by lanes q < step) is read next step
+    __syncwarp();  // row `step` of L and c_step (shared memory) are read later
     if (rr <= kResidRel * yy) break;
   }
-#undef PHI
+#undef UV
   __syncwarp();
 
   // ---- back substitution L^T gamma = z
@@ -258,7 +281,7 @@ cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const 
   int warps = OMP_THREADS / 32;
   size_t smem = 0;
   if (SMEM) {
-    const size_t per_warp = (size_t)(SMAX - 1) * NT * 32 * sizeof(float);
+    const size_t per_warp = (size_t)(SMAX - 1) * (NT / 2) * 32 * sizeof(float2);
     warps = (int)((190u * 1024u) / per_warp);
     if (warps > OMP_THREADS / 32) warps = OMP_THREADS / 32;
     if (warps < 1) warps = 1;
@@ -275,7 +298,7 @@ cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const 
   return cudaGetLastError();
 }
 
-// register budget: alpha + phi must stay well inside 255 registers
+// register budget: alpha + the u vectors must stay well inside 255 registers
 template <int NT, int SMAX>
 constexpr bool fits_regs() {
   return NT * (SMAX - 1) <= 128;
@@ -310,7 +333,6 @@ cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const
                       cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   const int nt = (n + 31) / 32;
-  if (nt <= 1) return pick_s<1>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
   if (nt <= 2) return pick_s<2>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
   if (nt <= 4) return pick_s<4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
   if (nt <= 8) return pick_s<8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
