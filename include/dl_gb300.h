@@ -62,10 +62,10 @@ typedef struct dl_ctx dl_ctx;
 #define DL_ENOMEM (-5)
 #define DL_ENOTIMPL (-6)
 
-/* arithmetic of the correlation D^T Y and Gram D^T D products */
+/* arithmetic of the correlations D^T Y (the Gram D^T D stays FP32-accurate) */
 #define DL_FP32 0 /* FP32-accurate (split-TF32 tensor cores, FP32 accumulation) */
 #define DL_BF16 1 /* BF16 operands, FP32 accumulation */
-#define DL_FP8 2  /* E4M3 operands with per-atom / per-signal scales */
+#define DL_FP8 2  /* E4M3 operands with per-atom and per-signal scales, FP32 accumulation */
 
 /* compiled limits */
 #define DL_MAX_P 128
@@ -81,7 +81,15 @@ typedef struct dl_ctx dl_ctx;
  *   m_max      1 <= m_max; workspace is sized for m_max signals
  *              (about m_max * (4n + 8 s_max + 16) bytes plus O(n^2 + 152 n p)).
  *   s_max      1 <= s_max <= min(p, n, DL_MAX_S).
- *   precision  DL_FP32 (DL_BF16 / DL_FP8 return DL_ENOTIMPL when not built).
+ *   precision  DL_FP32, DL_BF16 or DL_FP8: the arithmetic of the correlations
+ *              D^T Y (mixed precision: BF16, or E4M3 with each atom and each
+ *              signal scaled so its largest entry maps to 448, accumulated in
+ *              FP32 on the tensor cores).  The Gram D^T D, the OMP loop, the
+ *              Cholesky and coefficient solves stay FP32 in every mode; a
+ *              signal whose Cholesky pivot falls below 1e-6 is redone in FP64
+ *              (see dl_last_resolved).  Shapes the reduced-precision kernel
+ *              does not cover (BF16 p > 128, E4M3 p > 256, n > 512) use the
+ *              FP32 path.
  *   stream     a cudaStream_t (NULL = the legacy default stream).
  * The context binds to the CUDA device current at the call.
  * Returns DL_OK, DL_EINVAL, DL_ENOMEM or DL_ECUDA.
@@ -193,6 +201,14 @@ int dl_correlate(dl_ctx* ctx, const float* Y, int64_t m, const float* D, float* 
 #define DL_NOALLOC_MAX_P 64
 int dl_correlate_noalloc(const float* Y, int64_t m, const float* D, int p, int n, float* A,
                          void* stream);
+
+/*
+ * dl_last_resolved -- synchronise and return how many signals of the most
+ * recent sparse-coding pass were redone in FP64 because an FP32 Cholesky pivot
+ * fell below 1e-6 (the FP64 pass uses the pivot threshold 1e-12 and the
+ * residual threshold 1e-14 ||y||^2), or a negative status.
+ */
+int64_t dl_last_resolved(dl_ctx* ctx);
 
 /*
  * dl_uses_tensor_cores -- 1 if this context's shape (p % 4 == 0, p <= 64,

@@ -21,7 +21,17 @@ struct dl_ctx {
   float* A0 = nullptr;
   float* Dhi = nullptr;  // TF32 head / tail of D for the tensor-core correlations
   float* Dlo = nullptr;
-  int use_tc = -1;       // -1 unknown, 0 CUDA-core path, 1 tcgen05 path
+  // reduced-precision correlations (precision DL_BF16 / DL_FP8)
+  int lp_kind = 0;        // 0 = FP32 path, dlk::LP_BF16, dlk::LP_E4M3
+  void* Ylp = nullptr;    // m_max x lp_row_elems, converted once per call
+  float* Ysc = nullptr;   // per-signal inverse scales (E4M3)
+  void* Dlp = nullptr;    // n x lp_row_elems, converted per iteration
+  float* Dsc = nullptr;   // per-atom inverse scales (E4M3)
+  // FP64 re-solve of signals whose FP32 pivot fell below 1e-6
+  int* rs_list = nullptr;
+  int* rs_count = nullptr;
+  double* rs_scratch = nullptr;
+  int64_t rs_flagged = 0;  // total flagged (read back at synchronising calls)
   int32_t* sidx = nullptr;
   float* sval = nullptr;
   int32_t* scnt = nullptr;
@@ -53,7 +63,7 @@ struct dl_ctx {
 
 namespace {
 
-constexpr int kKernelsOmp = 4;       // split, gram, correlations, omp
+constexpr int kKernelsOmp = 5;       // split, gram, correlations, omp, FP64 re-solve
 constexpr int kKernelsScan = 2;      // colptr scan
 constexpr int kKernelsJau = 5;       // accumulate, reduce, atoms, rows, finalize
 
@@ -65,7 +75,8 @@ void free_ctx(dl_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
-  void* ptrs[] = {c->G, c->A0, c->Dhi, c->Dlo, c->sidx, c->sval, c->scnt, c->bsum, c->err, c->iter, c->rmse,
+  void* ptrs[] = {c->G, c->A0, c->Dhi, c->Dlo, c->Ylp, c->Ysc, c->Dlp, c->Dsc, c->rs_list,
+                  c->rs_count, c->rs_scratch, c->sidx, c->sval, c->scnt, c->bsum, c->err, c->iter, c->rmse,
                   c->jw.Upart, c->jw.U, c->jw.epart_a, c->jw.epart_b, c->jw.Dn, c->jw.C,
                   c->hY, c->hD, c->hcolptr, c->hrowidx, c->hval};
   for (void* q : ptrs)
@@ -179,7 +190,21 @@ cudaError_t enq_gram(dl_ctx* c, const float* D, bool tc) {
   return dlk::corr_tf32x3(D, c->n, c->Dhi, c->Dlo, c->n, c->p, c->G, c->n, c->err, c->st);
 }
 
+bool lp_ok(dl_ctx* c) { return c->lp_kind != 0 && dlk::corr_lp_supported(c->lp_kind, c->p, c->n, c->lda); }
+
+// Y converted to the reduced-precision format (once per call, before any iteration).
+cudaError_t enq_convert_y(dl_ctx* c, const float* Y, int64_t m) {
+  if (!lp_ok(c)) return cudaSuccess;
+  return dlk::to_lowp(c->lp_kind, Y, m, c->p, c->Ylp, c->Ysc, c->st);
+}
+
 cudaError_t enq_corr(dl_ctx* c, const float* Y, int64_t m, const float* D, bool tc) {
+  if (lp_ok(c)) {
+    cudaError_t e = dlk::to_lowp(c->lp_kind, D, c->n, c->p, c->Dlp, c->Dsc, c->st);
+    if (e != cudaSuccess) return e;
+    return dlk::corr_lp(c->lp_kind, c->Ylp, m, c->Ysc, c->Dlp, c->Dsc, c->n, c->p, c->A0, c->lda,
+                        c->err, c->st);
+  }
   if (!tc) return dlk::gemm_nt_simt(Y, m, D, c->n, c->p, c->A0, c->lda, c->st);
   return dlk::corr_tf32x3(Y, m, c->Dhi, c->Dlo, c->n, c->p, c->A0, c->lda, c->err, c->st);
 }
@@ -193,8 +218,13 @@ cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s)
   e = enq_corr(c, Y, m, D, tc);
   if (e != cudaSuccess) return e;
   mark(c, 2);
+  e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st);
+  if (e != cudaSuccess) return e;
   e = dlk::omp_batch(c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval, c->scnt, c->err,
-                     c->st);
+                     c->rs_list, c->rs_count, (int)c->m_max, c->st);
+  if (e != cudaSuccess) return e;
+  e = dlk::omp_resolve64(Y, c->p, D, c->n, s, c->rs_list, c->rs_count, (int)c->m_max,
+                         c->rs_scratch, c->sidx, c->sval, c->scnt, c->st);
   mark(c, 3);
   return e;
 }
@@ -258,10 +288,7 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
   if (p < 1 || p > DL_MAX_P || n < 1 || n > DL_MAX_N || m_max < 1 || s_max < 1 ||
       s_max > DL_MAX_S || s_max > p || s_max > n)
     return DL_EINVAL;
-  if (precision != DL_FP32) {
-    if (precision == DL_BF16 || precision == DL_FP8) return DL_ENOTIMPL;
-    return DL_EINVAL;
-  }
+  if (precision != DL_FP32 && precision != DL_BF16 && precision != DL_FP8) return DL_EINVAL;
   dl_ctx* c = new dl_ctx();
   cudaGetDevice(&c->dev);
   c->p = p;
@@ -283,7 +310,15 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
             dalloc(&c->jw.U, ulen) && dalloc(&c->jw.epart_a, (size_t)2 * c->jw.nb_accum) &&
             dalloc(&c->jw.epart_b, (size_t)c->jw.nb_row) && dalloc(&c->jw.Dn, (size_t)n * p) &&
             dalloc(&c->jw.C, (size_t)n) && dalloc(&c->Dhi, (size_t)n * p) &&
-            dalloc(&c->Dlo, (size_t)n * p);
+            dalloc(&c->Dlo, (size_t)n * p) && dalloc(&c->rs_list, mm) && dalloc(&c->rs_count, 1) &&
+            dalloc(&c->rs_scratch, (size_t)dlk::DL_RESOLVE_WARPS * (dlk::DL_RESOLVE_SMAX + 1) * n);
+  if (ok && precision != DL_FP32) {
+    c->lp_kind = precision == DL_BF16 ? dlk::LP_BF16 : dlk::LP_E4M3;
+    const size_t esz = precision == DL_BF16 ? 2 : 1;
+    const size_t ld = (size_t)dlk::lp_row_elems(c->lp_kind, p);
+    ok = dalloc((uint8_t**)&c->Ylp, mm * ld * esz) && dalloc(&c->Ysc, mm) &&
+         dalloc((uint8_t**)&c->Dlp, (size_t)n * ld * esz) && dalloc(&c->Dsc, (size_t)n + 16);
+  }
   if (!ok) {
     cudaGetLastError();
     free_ctx(c);
@@ -363,12 +398,23 @@ int dl_correlate(dl_ctx* c, const float* Y, int64_t m, const float* D, float* A)
   DevGuard g(c->dev);
   const bool tc = tc_ok(c, Y, D);
   if (tc) DL_CHECK(dlk::split_tf32(D, (int64_t)c->n * c->p, c->Dhi, c->Dlo, c->st));
+  DL_CHECK(enq_convert_y(c, Y, m));
   DL_CHECK(enq_corr(c, Y, m, D, tc));
   if (m > 0)
     DL_CHECK(cudaMemcpy2DAsync(A, sizeof(float) * c->n, c->A0, sizeof(float) * c->lda,
                                sizeof(float) * c->n, (size_t)m, cudaMemcpyDeviceToDevice, c->st));
   c->launches += tc ? 2 : 1;
   return DL_OK;
+}
+
+int64_t dl_last_resolved(dl_ctx* c) {
+  if (!c) return DL_EINVAL;
+  DevGuard g(c->dev);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, c->rs_count, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess)
+    return DL_ECUDA;
+  return h;
 }
 
 int dl_uses_tensor_cores(dl_ctx* c) {
@@ -400,6 +446,7 @@ int omp_code(dl_ctx* c, const float* Y, int64_t m, const float* D, int s, int64_
     dri = c->hrowidx;
     dv = c->hval;
   }
+  DL_CHECK(enq_convert_y(c, dY, m));
   DL_CHECK(enq_omp(c, dY, m, dD, s));
   DL_CHECK(dlk::counts_to_colptr(c->scnt, m, c->bsum, dcp, c->st));
   DL_CHECK(dlk::slots_to_csc(c->sidx, c->sval, c->scnt, m, s, dcp, dri, dv, c->st));
@@ -500,6 +547,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
     c->gkey_seen = 0;
   }
   const bool can_graph = c->st != nullptr && m > 0;
+  DL_CHECK(enq_convert_y(c, dY, m));
   for (int it = 0; it < iters; ++it) {
     if (can_graph && c->gkey_seen >= 1 && !c->gexec) {
       cudaGraph_t graph = nullptr;

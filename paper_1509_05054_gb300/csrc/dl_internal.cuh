@@ -29,12 +29,32 @@ cudaError_t split_tf32(const float* B, int64_t count, float* hi, float* lo, cuda
 cudaError_t corr_tf32x3(const float* A, int64_t rows_a, const float* Bhi, const float* Blo, int n,
                         int p, float* C, int64_t ldc, int* err, cudaStream_t st);
 
+// Reduced-precision correlations (k_corr_lp.cu): operands converted to padded
+// row-major BF16 or E4M3 (+ inverse row scales) buffers, then tcgen05 MMAs.
+enum : int { LP_BF16 = 1, LP_E4M3 = 2 };
+int lp_row_elems(int kind, int p);  // padded row length in elements
+bool corr_lp_supported(int kind, int p, int n, int64_t ldc);
+cudaError_t to_lowp(int kind, const float* src, int64_t rows, int p, void* dst, float* inv_scale,
+                    cudaStream_t st);
+cudaError_t corr_lp(int kind, const void* A, int64_t rows_a, const float* a_inv_scale,
+                    const void* B, const float* b_inv_scale, int n, int p, float* C, int64_t ldc,
+                    int* err, cudaStream_t st);
+
 // ---- OMP ----------------------------------------------------------------------
 // Batch-OMP of m signals from their correlations A0 (row i = D^T y_i, stride lda) and G = D^T D.
 // Writes s slots per signal (atoms ascending, unused slots idx = -1) and the count.
+// Signals stopped by a pivot below kPivotMin are appended to rs_list (if given) for the
+// FP64 re-solve.
 cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                       int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                      cudaStream_t st);
+                      int* rs_list, int* rs_count, int rs_cap, cudaStream_t st);
+
+// FP64 re-solve (k_resolve.cu): full FP64 OMP of the listed signals, overwriting their slots.
+constexpr int DL_RESOLVE_SMAX = 16;
+constexpr int DL_RESOLVE_WARPS = 64;
+cudaError_t omp_resolve64(const float* Y, int p, const float* D, int n, int s, const int* list,
+                          const int* count, int cap, double* scratch, int32_t* idx, float* val,
+                          int32_t* cnt, cudaStream_t st);
 bool omp_supported(int n, int s);
 
 // ---- JAU / PAK-SVD (group size n) ---------------------------------------------

@@ -1,0 +1,269 @@
+// Reduced-precision correlations on tcgen05 tensor cores: alpha0 = D^T y for a
+// tile of 128 signals with BF16 operands (kind::f16) or E4M3 operands with
+// per-signal and per-atom scales (kind::f8f6f4), FP32 accumulation in TMEM.
+// This is the mixed-precision form of Algorithm 1 step 1; the OMP loop that
+// consumes alpha0 stays FP32.
+//
+// Operands are converted once into padded row-major buffers (row = one signal
+// or one atom, rows padded to a multiple of 128 bytes with zeros), so one TMA
+// box of 128 bytes x rows covers K in 128-byte swizzle chunks.  Per CTA: TMA
+// the A tile (128 signals), then per block of 256 atoms TMA the B block, issue
+// 4 MMAs per 128-byte chunk (K = 16 BF16 or 32 E4M3 per MMA), commit, and drain
+// TMEM with tcgen05.ld; E4M3 results are multiplied by the two inverse scales.
+// Every mbarrier wait is bounded (ERR_TIMEOUT on expiry).
+#include "dl_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+namespace dlk {
+namespace {
+
+using namespace tc;
+
+constexpr int LP_THREADS = 128;
+constexpr int TILE_M = 128;
+constexpr int BLOCK_N = 256;
+constexpr int CHUNK_BYTES = 128;
+
+template <int KIND>
+struct LpTraits;
+template <>
+struct LpTraits<LP_BF16> {
+  static constexpr int esize = 2;
+  // kind::f16: D F32, A/B BF16, K-major, N = 256, M = 128
+  static constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(BLOCK_N >> 3) << 17) | ((uint32_t)(TILE_M >> 4) << 24);
+};
+template <>
+struct LpTraits<LP_E4M3> {
+  static constexpr int esize = 1;
+  // kind::f8f6f4: D F32, A/B E4M3 (format 0), K-major, N = 256, M = 128
+  static constexpr uint32_t idesc = (1u << 4) | (0u << 7) | (0u << 10) |
+                                    ((uint32_t)(BLOCK_N >> 3) << 17) | ((uint32_t)(TILE_M >> 4) << 24);
+};
+
+constexpr size_t kAChunk = (size_t)TILE_M * CHUNK_BYTES;   // 16 KB
+constexpr size_t kBChunk = (size_t)BLOCK_N * CHUNK_BYTES;  // 32 KB
+
+template <int KIND>
+__global__ void __launch_bounds__(LP_THREADS, 1)
+    corr_lp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   int64_t rows_a, int n, int kb, const float* __restrict__ row_scale,
+                   const float* __restrict__ col_scale, float* __restrict__ C, int64_t ldc,
+                   int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* As = base;
+  uint8_t* Bs = base + kb * kAChunk;
+  uint64_t* bars = (uint64_t*)(Bs + kb * kBChunk);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 4);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = (int64_t)blockIdx.x * TILE_M;
+  const int nblocks = (n + BLOCK_N - 1) / BLOCK_N;
+  const uint32_t ncols = nblocks <= 1 ? 256u : 512u;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  constexpr int EPC = CHUNK_BYTES / LpTraits<KIND>::esize;  // elements per chunk
+
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bars[0], (uint32_t)(kb * kAChunk));
+    for (int q = 0; q < kb; ++q) tma_load_2d(As + q * kAChunk, &tmA, &bars[0], q * EPC, (int)i0);
+    bool ok = mbar_wait(&bars[0], 0);
+    for (int nb = 0; nb < nblocks && ok; ++nb) {
+      mbar_expect_tx(&bars[1], (uint32_t)(kb * kBChunk));
+      for (int q = 0; q < kb; ++q)
+        tma_load_2d(Bs + q * kBChunk, &tmB, &bars[1], q * EPC, nb * BLOCK_N);
+      ok = mbar_wait(&bars[1], (uint32_t)(nb & 1));
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t dcol = tmem + (uint32_t)(nb * BLOCK_N);
+      uint32_t accum = 0;
+      for (int q = 0; q < kb; ++q) {
+        const uint64_t ad = sw128_desc(As + q * kAChunk);
+        const uint64_t bd = sw128_desc(Bs + q * kBChunk);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {  // 32 bytes of K per MMA
+          if constexpr (KIND == LP_BF16)
+            mma_f16(dcol, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), LpTraits<KIND>::idesc, accum);
+          else
+            mma_f8f6f4(dcol, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), LpTraits<KIND>::idesc, accum);
+          accum = 1;
+        }
+      }
+      mma_commit(&bars[2]);
+      ok = mbar_wait(&bars[2], (uint32_t)(nb & 1));
+    }
+    if (!ok) s_fail = 1;
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (!s_fail) {
+    const int64_t row = i0 + warp * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const float rs = (KIND == LP_E4M3 && row < rows_a) ? row_scale[row] : 1.f;
+    for (int c0 = 0; c0 < n; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
+      if (row < rows_a) {
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          v[q] = __uint_as_float(r[q]);
+          if (KIND == LP_E4M3) v[q] *= rs * __ldg(col_scale + c0 + q);
+        }
+        float4* dst = (float4*)(C + row * ldc + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicOr(err, ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                 : "memory");
+}
+
+// rows x p FP32 -> rows x ld BF16 (zero padded).
+__global__ void to_bf16_kernel(const float* __restrict__ src, int64_t rows, int p, int ld,
+                               __nv_bfloat16* __restrict__ dst) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * ld) return;
+  const int64_t r = e / ld;
+  const int c = (int)(e - r * ld);
+  dst[e] = __float2bfloat16_rn(c < p ? src[r * p + c] : 0.f);
+}
+
+// rows x p FP32 -> rows x ld E4M3 (zero padded), one warp per row: the row is
+// scaled so that its largest magnitude maps to 448 (the E4M3 maximum);
+// inv_scale[r] = max|row| / 448 undoes it.
+__global__ void to_e4m3_kernel(const float* __restrict__ src, int64_t rows, int p, int ld,
+                               uint8_t* __restrict__ dst, float* __restrict__ inv_scale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= rows) return;
+  float mx = 0.f;
+  for (int c = lane; c < p; c += 32) mx = fmaxf(mx, fabsf(src[r * p + c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const float scale = mx > 0.f ? 448.f / mx : 1.f;
+  for (int c = lane; c < ld; c += 32) {
+    const float v = c < p ? src[r * p + c] * scale : 0.f;
+    dst[r * ld + c] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+  }
+  if (lane == 0) inv_scale[r] = mx > 0.f ? mx / 448.f : 1.f;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool make_map_lp(CUtensorMap* map, const void* ptr, int64_t rows, int ld, int esize, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
+  cuuint32_t box[2] = {(cuuint32_t)(CHUNK_BYTES / esize), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt =
+      esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  return fn(map, dt, 2, (void*)ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int lp_row_elems(int kind, int p) {
+  const int epc = CHUNK_BYTES / (kind == LP_BF16 ? 2 : 1);
+  return (p + epc - 1) / epc * epc;
+}
+
+bool corr_lp_supported(int kind, int p, int n, int64_t ldc) {
+  const int kb = lp_row_elems(kind, p) * (kind == LP_BF16 ? 2 : 1) / CHUNK_BYTES;
+  return (kind == LP_BF16 || kind == LP_E4M3) && p >= 1 && kb <= 2 && n >= 1 && n <= 512 &&
+         (ldc % 4) == 0 && ldc >= (int64_t)(n + 15) / 16 * 16 && encode_fn() != nullptr;
+}
+
+cudaError_t to_lowp(int kind, const float* src, int64_t rows, int p, void* dst, float* inv_scale,
+                    cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  const int ld = lp_row_elems(kind, p);
+  if (kind == LP_BF16) {
+    const int64_t tot = rows * ld;
+    to_bf16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, rows, p, ld,
+                                                                 (__nv_bfloat16*)dst);
+  } else {
+    to_e4m3_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(src, rows, p, ld, (uint8_t*)dst,
+                                                               inv_scale);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t corr_lp(int kind, const void* A, int64_t rows_a, const float* a_inv_scale,
+                    const void* B, const float* b_inv_scale, int n, int p, float* C, int64_t ldc,
+                    int* err, cudaStream_t st) {
+  if (rows_a <= 0) return cudaSuccess;
+  const int esize = kind == LP_BF16 ? 2 : 1;
+  const int ld = lp_row_elems(kind, p);
+  const int kb = ld * esize / CHUNK_BYTES;
+  CUtensorMap ma, mb;
+  if (!make_map_lp(&ma, A, rows_a, ld, esize, TILE_M) || !make_map_lp(&mb, B, n, ld, esize, BLOCK_N))
+    return cudaErrorInvalidValue;
+  size_t smem = 1024 + kb * (kAChunk + kBChunk) + 64;
+  // one CTA per SM when it holds all 512 TMEM columns
+  if (n > BLOCK_N && smem < 120 * 1024) smem = 120 * 1024;
+  const unsigned grid = (unsigned)((rows_a + TILE_M - 1) / TILE_M);
+  cudaError_t e;
+  if (kind == LP_BF16) {
+    e = cudaFuncSetAttribute(corr_lp_kernel<LP_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    corr_lp_kernel<LP_BF16><<<grid, LP_THREADS, smem, st>>>(ma, mb, rows_a, n, kb, a_inv_scale,
+                                                            b_inv_scale, C, ldc, err);
+  } else {
+    e = cudaFuncSetAttribute(corr_lp_kernel<LP_E4M3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    corr_lp_kernel<LP_E4M3><<<grid, LP_THREADS, smem, st>>>(ma, mb, rows_a, n, kb, a_inv_scale,
+                                                            b_inv_scale, C, ldc, err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace dlk

@@ -104,7 +104,8 @@ template <int NT, int SMAX, bool SMEM_U, bool FULLN>
 __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
     const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
-    float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err) {
+    float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err,
+    int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap) {
   static_assert(NT >= 2 && NT % 2 == 0, "alpha is held in float2 pairs");
   constexpr int NV = NT / 2;
   constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
@@ -206,7 +207,13 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     }
     const float delta = gss - wsq;
     if (!(delta > kPivotMin)) {
-      if (!isfinite(delta) && lane == 0) atomicOr(err, ERR_NONFINITE);
+      if (lane == 0) {
+        if (!isfinite(delta)) atomicOr(err, ERR_NONFINITE);
+        if (rs_count) {  // rounding dominates this pivot: redo the signal in FP64
+          const int pos = atomicAdd(rs_count, 1);
+          if (pos < rs_cap) rs_list[pos] = (int)i;
+        }
+      }
       break;
     }
     const float ck = __frsqrt_rn(delta);  // c_k = 1 / L_kk, correctly rounded
@@ -277,7 +284,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
 template <int NT, int SMAX, bool SMEM, bool FULLN>
 cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                      int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                     cudaStream_t st) {
+                     int* rs_list, int* rs_count, int rs_cap, cudaStream_t st) {
   int warps = OMP_THREADS / 32;
   size_t smem = 0;
   if (SMEM) {
@@ -294,7 +301,7 @@ cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const 
   }
   const int64_t blocks = (m + warps - 1) / warps;
   omp_warp_kernel<NT, SMAX, SMEM, FULLN><<<(unsigned)blocks, warps * 32, smem, st>>>(
-      A0, lda, G, n, Y, p, m, s, idx, val, cnt, err);
+      A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rs_list, rs_count, rs_cap);
   return cudaGetLastError();
 }
 
@@ -307,21 +314,21 @@ constexpr bool fits_regs() {
 template <int NT, int SMAX>
 cudaError_t pick_store(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                        int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                       cudaStream_t st) {
+                       int* rl, int* rc, int rcap, cudaStream_t st) {
   constexpr bool SM = !fits_regs<NT, SMAX>();
   if (n == 32 * NT)
-    return launch_t<NT, SMAX, SM, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
-  return launch_t<NT, SMAX, SM, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+    return launch_t<NT, SMAX, SM, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+  return launch_t<NT, SMAX, SM, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
 }
 
 template <int NT>
 cudaError_t pick_s(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                    int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                   cudaStream_t st) {
-  if (s <= 4) return pick_store<NT, 4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
-  if (s <= 8) return pick_store<NT, 8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
-  if (s <= 12) return pick_store<NT, 12>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
-  return pick_store<NT, 16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+                   int* rl, int* rc, int rcap, cudaStream_t st) {
+  if (s <= 4) return pick_store<NT, 4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+  if (s <= 8) return pick_store<NT, 8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+  if (s <= 12) return pick_store<NT, 12>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+  return pick_store<NT, 16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
 }
 
 }  // namespace
@@ -330,14 +337,14 @@ bool omp_supported(int n, int s) { return n >= 1 && n <= 1024 && s >= 1 && s <= 
 
 cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                       int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                      cudaStream_t st) {
+                      int* rl, int* rc, int rcap, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   const int nt = (n + 31) / 32;
-  if (nt <= 2) return pick_s<2>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
-  if (nt <= 4) return pick_s<4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
-  if (nt <= 8) return pick_s<8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
-  if (nt <= 16) return pick_s<16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
-  return pick_s<32>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, st);
+  if (nt <= 2) return pick_s<2>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+  if (nt <= 4) return pick_s<4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+  if (nt <= 8) return pick_s<8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+  if (nt <= 16) return pick_s<16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+  return pick_s<32>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
 }
 
 }  // namespace dlk

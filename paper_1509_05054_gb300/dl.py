@@ -62,6 +62,8 @@ def load(build_if_missing: bool = True):
         lib.dl_correlate.argtypes = [P, P, i64, P, P]
         lib.dl_uses_tensor_cores.argtypes = [P]
         lib.dl_correlate_noalloc.argtypes = [P, i64, P, i32, i32, P, P]
+        lib.dl_last_resolved.argtypes = [P]
+        lib.dl_last_resolved.restype = i64
         lib.dl_phase_times.argtypes = [P, P, i32]
         for name in ("dl_init", "dl_set_stream", "dl_destroy", "omp_code", "jau_update", "dl_iterate",
                      "dl_sync", "dl_set_profiling", "dl_phase_times", "dl_gram", "dl_correlate",
@@ -156,6 +158,13 @@ def dl_correlate_noalloc(Y, m: int, D, p: int, n: int, A, stream=None) -> None:
     synchronisation is not acceptable).  p <= 64, n <= 512."""
     _check(load().dl_correlate_noalloc(_ptr(Y), m, _ptr(D), p, n, _ptr(A), _stream_ptr(stream)),
            "dl_correlate_noalloc")
+
+
+def dl_last_resolved(ctx: int) -> int:
+    rc = int(load().dl_last_resolved(ctx))
+    if rc < 0:
+        raise DLError(rc, "dl_last_resolved")
+    return rc
 
 
 def dl_uses_tensor_cores(ctx: int) -> int:
