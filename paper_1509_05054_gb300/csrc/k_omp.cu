@@ -23,7 +23,6 @@
 #include "dl_internal.cuh"
 
 #include <math.h>
-#include <stdlib.h>
 
 namespace dlk {
 namespace {
@@ -101,71 +100,12 @@ struct Take {
   }
 };
 
-// Gram rows from global memory (L2): pair v of lane l = (G[sel][64v+l], G[sel][64v+32+l]).
-template <bool FULLN>
-struct GramGlobal {
-  const float* __restrict__ G;
-  int n;
-  template <int NV>
-  __device__ __forceinline__ void row(int sel, int lane, float2 (&out)[NV]) const {
-    const float* __restrict__ Gr = G + (size_t)sel * n;  // row sel == column sel (G symmetric)
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const int j0 = 64 * v + lane, j1 = j0 + 32;
-      out[v].x = (FULLN || j0 < n) ? __ldg(Gr + j0) : 0.f;
-      out[v].y = (FULLN || j1 < n) ? __ldg(Gr + j1) : 0.f;
-    }
-  }
-  __device__ __forceinline__ float diag(int sel) const { return __ldg(G + (size_t)sel * n + sel); }
-};
-
-// Gram rows distributed over the shared memory of a thread-block cluster: CTA
-// `rank` holds rows [rank*rows, (rank+1)*rows); inside a row, element 32t+l is
-// stored at float ((t/4)*32 + l)*4 + t%4, so lane l reads its NT values of a row
-// as NT/4 16-byte loads (ld.shared::cluster) from the owning CTA.
-template <int NT>
-struct GramCluster {
-  uint32_t base;  // shared-memory address of this CTA's slice
-  int rows;
-  __device__ __forceinline__ uint32_t remote(int sel, uint32_t off_bytes) const {
-    const int rank = sel / rows, r = sel - rank * rows;
-    const uint32_t local = base + (uint32_t)r * (uint32_t)(NT * 32 * 4) + off_bytes;
-    uint32_t addr;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(addr) : "r"(local), "r"(rank));
-    return addr;
-  }
-  template <int NV>
-  __device__ __forceinline__ void row(int sel, int lane, float2 (&out)[NV]) const {
-    const uint32_t a = remote(sel, (uint32_t)lane * 16u);
-#pragma unroll
-    for (int c = 0; c < NT / 4; ++c) {
-      float4 q;
-      asm volatile("ld.shared::cluster.v4.f32 {%0,%1,%2,%3}, [%4];"
-                   : "=f"(q.x), "=f"(q.y), "=f"(q.z), "=f"(q.w)
-                   : "r"(a + (uint32_t)c * 512u));
-      out[2 * c] = make_float2(q.x, q.y);
-      out[2 * c + 1] = make_float2(q.z, q.w);
-    }
-  }
-  __device__ __forceinline__ float diag(int sel) const {
-    const int t = sel >> 5, l = sel & 31;
-    float v;
-    asm volatile("ld.shared::cluster.f32 %0, [%1];"
-                 : "=f"(v)
-                 : "r"(remote(sel, (uint32_t)(((t >> 2) * 32 + l) * 4 + (t & 3)) * 4u)));
-    return v;
-  }
-};
-
-// One signal, one warp: the whole OMP of signal i (see the file header).
-// L, C: this warp's shared-memory Cholesky rows and 1/L_qq; u_s: its shared
-// u vectors when SMEM_U.
-template <int NT, int SMAX, bool SMEM_U, bool FULLN, class GSrc>
-__device__ __forceinline__ void omp_one(
-    int64_t i, const GSrc& gsrc, float (&L)[SMAX][SMAX], float (&C)[SMAX], float2* u_s,
-    const float* __restrict__ A0, int64_t lda, int n, const float* __restrict__ Y, int p, int s,
-    int32_t* __restrict__ oidx, float* __restrict__ oval, int32_t* __restrict__ ocnt,
-    int* __restrict__ err, int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap) {
+template <int NT, int SMAX, bool SMEM_U, bool FULLN>
+__global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
+    const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
+    const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
+    float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err,
+    int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap) {
   static_assert(NT >= 2 && NT % 2 == 0, "alpha is held in float2 pairs");
   constexpr int NV = NT / 2;
   constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
@@ -173,8 +113,18 @@ __device__ __forceinline__ void omp_one(
   constexpr unsigned TMASK = (1u << TB) - 1u;
   constexpr unsigned VMASK = 0x7FFFFFFFu & ~TMASK;
 
+  extern __shared__ float2 smem_u[];
+  __shared__ float Lsh[OMP_THREADS / 32][SMAX][SMAX];  // per warp: L[j][q] (q < j)
+  __shared__ float Csh[OMP_THREADS / 32][SMAX];        // per warp: c_q = 1/L_qq
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (i >= m) return;
+  float(&L)[SMAX][SMAX] = Lsh[wib];
+  float(&C)[SMAX] = Csh[wib];
+
   float2 u_r[SMEM_U ? 1 : NPHI][SMEM_U ? 1 : NV];
+  float2* u_s = SMEM_U ? smem_u + (size_t)wib * NPHI * NV * 32 : nullptr;
 #define UV(q, v) (*(SMEM_U ? &u_s[((q) * NV + (v)) * 32 + lane] : &u_r[SMEM_U ? 0 : (q)][SMEM_U ? 0 : (v)]))
 
   // ||y||^2 for the residual stop rule and the non-finite check
@@ -216,15 +166,21 @@ __device__ __forceinline__ void omp_one(
     const int lsel = __ffs(ball) - 1;
     const int tsel = NT - 1 - (int)(kbits & TMASK);
     const int sel = 32 * tsel + lsel;
+    const float* __restrict__ Gr = G + (size_t)sel * n;  // row sel == column sel (G symmetric)
+
     // issue the Gram row loads early (needed unless this is the last step)
     const bool need_u = (step + 1 < s) && (step + 1 < SMAX);
     if (need_u) {
-      float2 grow[NV];
-      gsrc.template row<NV>(sel, lane, grow);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) UV(step < NPHI ? step : 0, v) = grow[v];
+      for (int v = 0; v < NV; ++v) {
+        const int j0 = 64 * v + lane, j1 = j0 + 32;
+        float2 g;
+        g.x = (FULLN || j0 < n) ? __ldg(Gr + j0) : 0.f;
+        g.y = (FULLN || j1 < n) ? __ldg(Gr + j1) : 0.f;
+        UV(step < NPHI ? step : 0, v) = g;
+      }
     }
-    const float gss = gsrc.diag(sel);
+    const float gss = __ldg(Gr + sel);
 
     // alpha[sel] (exact, signed), its masking, and u_q[sel] on the owning lane
     float amine = 0.f;
@@ -325,65 +281,6 @@ __device__ __forceinline__ void omp_one(
   if (lane == 0) ocnt[i] = k;
 }
 
-template <int NT, int SMAX, bool SMEM_U, bool FULLN>
-__global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
-    const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
-    const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
-    float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err,
-    int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap) {
-  constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
-  extern __shared__ float2 smem_u[];
-  __shared__ float Lsh[OMP_THREADS / 32][SMAX][SMAX];  // per warp: L[j][q] (q < j)
-  __shared__ float Csh[OMP_THREADS / 32][SMAX];        // per warp: c_q = 1/L_qq
-  const int wib = threadIdx.x >> 5;
-  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-  if (i >= m) return;
-  float2* u_s = SMEM_U ? smem_u + (size_t)wib * NPHI * (NT / 2) * 32 : nullptr;
-  const GramGlobal<FULLN> gsrc{G, n};
-  omp_one<NT, SMAX, SMEM_U, FULLN>(i, gsrc, Lsh[wib], Csh[wib], u_s, A0, lda, n, Y, p, s, oidx,
-                                   oval, ocnt, err, rs_list, rs_count, rs_cap);
-}
-
-// Persistent cluster form: the Gram matrix lives in the shared memory of the
-// cluster's CTAs (one CTA per SM, OMP_CL_WARPS warps each); every warp walks
-// signals gw, gw + total_warps, ...  The cluster barriers make the slices visible
-// before the first remote read and keep every CTA resident until its cluster's
-// last remote read has completed.
-constexpr int OMP_CL_WARPS = 12;
-
-template <int NT, int SMAX>
-__global__ void __launch_bounds__(OMP_CL_WARPS * 32, 1) omp_cluster_kernel(
-    const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n, int rows,
-    const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
-    float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err,
-    int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap) {
-  extern __shared__ float4 gslice[];
-  __shared__ float Lsh[OMP_CL_WARPS][SMAX][SMAX];
-  __shared__ float Csh[OMP_CL_WARPS][SMAX];
-  uint32_t rank;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-  // this CTA's slice of G, rows [rank*rows, rank*rows + rows), permuted layout
-  float* sl = (float*)gslice;
-  const float* __restrict__ src = G + (size_t)rank * rows * n;
-  for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
-    const int r = e / n, col = e - r * n;
-    const int t = col >> 5, l = col & 31;
-    sl[(size_t)r * n + ((t >> 2) * 32 + l) * 4 + (t & 3)] = src[e];
-  }
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-
-  const GramCluster<NT> gsrc{(uint32_t)__cvta_generic_to_shared(gslice), rows};
-  const int wib = threadIdx.x >> 5;
-  const int64_t total = (int64_t)gridDim.x * OMP_CL_WARPS;
-  for (int64_t i = (int64_t)blockIdx.x * OMP_CL_WARPS + wib; i < m; i += total)
-    omp_one<NT, SMAX, false, true>(i, gsrc, Lsh[wib], Csh[wib], nullptr, A0, lda, n, Y, p, s, oidx,
-                                   oval, ocnt, err, rs_list, rs_count, rs_cap);
-  __syncwarp();
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 template <int NT, int SMAX, bool SMEM, bool FULLN>
 cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                      int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
@@ -414,74 +311,11 @@ constexpr bool fits_regs() {
   return NT * (SMAX - 1) <= 128;
 }
 
-// Cluster size that puts the n x n Gram matrix in at most 160 KB of shared memory
-// per CTA (0: does not fit in a portable cluster of 8).
-inline int gram_cluster_size(int n) {
-  for (int cl = 1; cl <= 8; cl *= 2)
-    if ((size_t)n * n * 4 / cl <= 160u * 1024u && n % cl == 0) return cl;
-  return 0;
-}
-
-template <int NT, int SMAX>
-cudaError_t launch_cluster(const float* A0, int64_t lda, const float* G, int n, const float* Y,
-                           int p, int64_t m, int s, int32_t* idx, float* val, int32_t* cnt,
-                           int* err, int* rl, int* rc, int rcap, cudaStream_t st, bool* launched) {
-  *launched = false;
-  if constexpr (NT % 4 != 0 || !fits_regs<NT, SMAX>()) {
-    return cudaSuccess;
-  } else {
-    const int cl = gram_cluster_size(n);
-    if (cl == 0 || getenv("DL_OMP_NO_CLUSTER")) return cudaSuccess;
-    const int rows = n / cl;
-    const size_t smem = (size_t)rows * n * sizeof(float);
-    auto kern = omp_cluster_kernel<NT, SMAX>;
-    static int max_clusters = -1;  // per instantiation; queried on the first (uncaptured) call
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)cl;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(OMP_CL_WARPS * 32);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (max_clusters < 0) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      cfg.gridDim = dim3((unsigned)cl);
-      int nc = 0;
-      e = cudaOccupancyMaxActiveClusters(&nc, (void*)kern, &cfg);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        nc = 0;
-      }
-      max_clusters = nc;
-    }
-    if (max_clusters <= 0) return cudaSuccess;
-    const int64_t want = (m + OMP_CL_WARPS - 1) / OMP_CL_WARPS;  // CTAs that have work
-    int64_t clusters = (want + cl - 1) / cl;
-    if (clusters > max_clusters) clusters = max_clusters;
-    cfg.gridDim = dim3((unsigned)(clusters * cl));
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A0, lda, G, n, rows, Y, p, m, s, idx, val, cnt,
-                                       err, rl, rc, rcap);
-    if (e == cudaSuccess) *launched = true;
-    return e;
-  }
-}
-
 template <int NT, int SMAX>
 cudaError_t pick_store(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                        int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
                        int* rl, int* rc, int rcap, cudaStream_t st) {
   constexpr bool SM = !fits_regs<NT, SMAX>();
-  if (n == 32 * NT) {
-    bool launched = false;
-    cudaError_t e = launch_cluster<NT, SMAX>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc,
-                                             rcap, st, &launched);
-    if (e != cudaSuccess || launched) return e;
-  }
   if (n == 32 * NT)
     return launch_t<NT, SMAX, SM, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
   return launch_t<NT, SMAX, SM, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
