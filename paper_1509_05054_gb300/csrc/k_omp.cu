@@ -23,7 +23,6 @@
 #include "dl_internal.cuh"
 
 #include <math.h>
-#include <stdlib.h>
 
 namespace dlk {
 namespace {
@@ -106,7 +105,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
     const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
     float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err,
-    int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap, int prefetch) {
+    int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap) {
   static_assert(NT >= 2 && NT % 2 == 0, "alpha is held in float2 pairs");
   constexpr int NV = NT / 2;
   constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
@@ -182,28 +181,6 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
       }
     }
     const float gss = __ldg(Gr + sel);
-
-    // The next step's atom is often one of this step's runner-ups (about 40% for
-    // the best two other lanes' maxima on image patches): prefetch their Gram
-    // rows into L1, off the critical path, so that a correct guess turns the
-    // next step's L2 round trip into an L1 hit.
-    if (prefetch && step + 2 < s) {
-      constexpr int LINES = NT;                 // 128-byte lines per Gram row
-      constexpr int CAND = LINES <= 16 ? 32 / LINES : 1;
-      unsigned mykey = (lane == lsel) ? 0u : __float_as_uint(kmax);
-      int mycand = -1;
-#pragma unroll
-      for (int c = 0; c < (CAND < 2 ? CAND : 2); ++c) {
-        const unsigned kb2 = __reduce_max_sync(FULL, mykey);
-        if ((kb2 & VMASK) == 0u) break;
-        const int l2 = __ffs(__ballot_sync(FULL, mykey == kb2)) - 1;
-        const int sel2 = 32 * (NT - 1 - (int)(kb2 & TMASK)) + l2;
-        if (lane / LINES == c) mycand = sel2;
-        if (lane == l2) mykey = 0u;
-      }
-      if (mycand >= 0)
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(G + (size_t)mycand * n + (lane % LINES) * 32));
-    }
 
     // alpha[sel] (exact, signed), its masking, and u_q[sel] on the owning lane
     float amine = 0.f;
@@ -324,8 +301,7 @@ cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const 
   }
   const int64_t blocks = (m + warps - 1) / warps;
   omp_warp_kernel<NT, SMAX, SMEM, FULLN><<<(unsigned)blocks, warps * 32, smem, st>>>(
-      A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rs_list, rs_count, rs_cap,
-      getenv("DL_OMP_NO_PREFETCH") ? 0 : 1);
+      A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rs_list, rs_count, rs_cap);
   return cudaGetLastError();
 }
 
