@@ -219,6 +219,69 @@ int64_t dl_last_resolved(dl_ctx* ctx);
 int dl_uses_tensor_cores(dl_ctx* ctx);
 
 /*
+ * dl_autotune -- pick this context's launch shapes for the problem (Y, m, D, s):
+ * tensor-core or CUDA-core correlations, OMP warps per CTA (4/2/1), CTAs of the
+ * error-accumulation pass (1x/2x), CTAs per SM of the row update (4/2/8), by a
+ * coordinate search timing one DL iteration per candidate (best of 3, CUDA
+ * events) from a scratch copy of D.  Y and D are device pointers and are not
+ * modified.  Allocates and frees temporary device buffers and synchronises.
+ * Later calls on the context use the chosen shapes.  Returns DL_OK, DL_EINVAL,
+ * DL_ENOMEM or DL_ECUDA.
+ */
+int dl_autotune(dl_ctx* ctx, const float* Y, int64_t m, const float* D, int s);
+
+/* dl_get_config -- the four launch-shape choices above, in that order. */
+int dl_get_config(dl_ctx* ctx, int* cfg4);
+
+/*
+ * Batches of independent DL problems of uneven shapes (p, n, m, s each their
+ * own), run together: each problem gets its own context (workspace) and CUDA
+ * stream; all problems' iterations are captured once into one CUDA graph with
+ * one branch per problem, so one graph launch runs every problem's `iters`
+ * iterations concurrently (Algorithm 1 per problem, group size n).
+ */
+typedef struct dl_problem {
+  int p, n, s;          /* signal length, atoms, sparsity (limits as dl_init) */
+  int64_t m;            /* signals */
+  const float* Y;       /* device, p x m column-major */
+  float* D;             /* device, p x n column-major, updated in place */
+  int64_t* colptr;      /* device CSC output of X: m + 1 */
+  int32_t* rowidx;      /* device, capacity s * m */
+  float* val;           /* device, capacity s * m */
+} dl_problem;
+
+typedef struct dl_batch dl_batch;
+
+/*
+ * dl_batch_create -- contexts for `count` problems (pointers are kept: the
+ * arrays must stay valid while the batch lives), precision as in dl_init,
+ * optional autotuning of every problem (dl_autotune), and one eager iteration
+ * of each problem on scratch D (sets kernel attributes before any capture).
+ * `stream` must be a non-default cudaStream_t (graph capture).  Returns DL_OK,
+ * DL_EINVAL, DL_ENOMEM or DL_ECUDA.
+ */
+int dl_batch_create(dl_batch** out, const dl_problem* problems, int count, int precision,
+                    int autotune, void* stream);
+
+/*
+ * dl_batch_iterate -- run `iters` DL iterations of every problem as one CUDA
+ * graph launch on the batch stream (the graph is captured on the first call
+ * with a given `iters`).  rmse: NULL, or host double[count * 2 * iters] with,
+ * for problem k, the pairs of dl_iterate at rmse[k * 2 * iters]; the call then
+ * synchronises.  Returns DL_OK, DL_EINVAL, DL_ECUDA or DL_ENUMERIC.
+ */
+int dl_batch_iterate(dl_batch* batch, int iters, double* rmse);
+
+/* dl_batch_destroy -- free the batch's contexts, streams and graph. */
+int dl_batch_destroy(dl_batch* batch);
+
+/* dl_batch_kernel_launches -- kernels enqueued by all problems of the batch. */
+int64_t dl_batch_kernel_launches(dl_batch* batch);
+
+/* dl_batch_config -- launch shapes chosen for problem k (see dl_get_config). */
+int dl_batch_config(dl_batch* batch, int k, int* cfg4);
+
+/*
  * dl_sync -- wait for the context's stream and report a pending device-side
  * error (DL_ENUMERIC for non-finite inputs met by a kernel) or DL_OK.
  */

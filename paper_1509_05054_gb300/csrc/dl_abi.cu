@@ -10,6 +10,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 struct dl_ctx {
   int dev = 0;
   int p = 0, n = 0, s_max = 0, precision = 0;
@@ -54,6 +56,11 @@ struct dl_ctx {
   int gkey_s = -1;
   int gkey_seen = 0;
   int64_t launches = 0;
+  // launch shapes (chosen by dl_autotune; defaults otherwise)
+  int cfg_omp_warps = 4;  // warps per CTA of the OMP kernel
+  int cfg_acc_mult = 1;   // accumulation CTAs: 1x or 2x the base count
+  int cfg_row_per_sm = 4; // row-update CTAs per SM
+  int cfg_corr_tc = 1;    // tensor-core correlations when the shape allows
   // optional per-phase timing with CUDA events recorded on the context's stream
   bool prof = false;
   cudaEvent_t ev[9] = {};
@@ -178,7 +185,7 @@ void mark(dl_ctx* c, int k) {
 // The tensor-core path needs p % 4 == 0, p <= 64, n <= 512 and 16-byte aligned operands;
 // other shapes use the FP32 CUDA-core GEMM.
 bool tc_ok(dl_ctx* c, const float* Y, const float* D) {
-  if (getenv("DL_FORCE_SIMT_GEMM")) return false;
+  if (getenv("DL_FORCE_SIMT_GEMM") || !c->cfg_corr_tc) return false;
   return dlk::corr_tc_supported(Y, c->p, c->n, c->lda) &&
          dlk::corr_tc_supported(D, c->p, c->n, c->n);
 }
@@ -221,7 +228,7 @@ cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s)
   e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st);
   if (e != cudaSuccess) return e;
   e = dlk::omp_batch(c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval, c->scnt, c->err,
-                     c->rs_list, c->rs_count, (int)c->m_max, c->st);
+                     c->rs_list, c->rs_count, (int)c->m_max, c->cfg_omp_warps, c->st);
   if (e != cudaSuccess) return e;
   e = dlk::omp_resolve64(Y, c->p, D, c->n, s, c->rs_list, c->rs_count, (int)c->m_max,
                          c->rs_scratch, c->sidx, c->sval, c->scnt, c->st);
@@ -231,6 +238,8 @@ cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s)
 
 cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const int64_t* colptr,
                     int32_t* rowidx_out, float* val_out) {
+  c->jw.nb_accum = dlk::jau_accum_blocks(c->p, c->n, c->cfg_acc_mult);
+  c->jw.nb_row = dlk::jau_row_blocks(c->cfg_row_per_sm);
   mark(c, 4);
   cudaError_t e = dlk::jau_accumulate(Y, c->p, m, D, c->n, s, c->sidx, c->sval, c->scnt, c->jw,
                                       c->err, c->st);
@@ -299,8 +308,8 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
   c->st = (cudaStream_t)stream;
   c->lda = ((int64_t)n + 31) / 32 * 32;
   const size_t mm = (size_t)m_max;
-  c->jw.nb_accum = dlk::jau_accum_blocks(p, n);
-  c->jw.nb_row = dlk::jau_row_blocks();
+  c->jw.nb_accum = dlk::jau_accum_blocks_max(p, n);
+  c->jw.nb_row = dlk::jau_row_blocks_max();
   const size_t ulen = (size_t)n * p + n;
   const size_t nslices = dlk::jau_accum_smem(p, n) > 0 ? (size_t)c->jw.nb_accum : 1;
   bool ok = dalloc(&c->G, (size_t)n * n) && dalloc(&c->A0, mm * c->lda) &&
@@ -596,3 +605,256 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Autotuner: coordinate search over the launch shapes of one context, timing one
+// DL iteration per candidate (median of 3, CUDA events) from a scratch copy of D.
+
+namespace {
+
+float time_iteration(dl_ctx* c, const float* Y, int64_t m, const float* D, float* Dtmp, int s,
+                     int64_t* cp, int32_t* ri, float* v, cudaEvent_t e0, cudaEvent_t e1) {
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaMemcpyAsync(Dtmp, D, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyDeviceToDevice, c->st);
+    cudaMemsetAsync(c->iter, 0, sizeof(int), c->st);
+    cudaEventRecord(e0, c->st);
+    if (enq_iteration(c, Y, m, Dtmp, s, cp, ri, v) != cudaSuccess) return 1e30f;
+    cudaEventRecord(e1, c->st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  return best;
+}
+
+}  // namespace
+
+extern "C" int dl_autotune(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
+  int rc = check_common(c, m);
+  if (rc) return rc;
+  if (m < 1 || s < 1 || s > c->s_max || ptr_kind(Y) != 1 || ptr_kind(D) != 1) return DL_EINVAL;
+  DevGuard g(c->dev);
+  float* Dtmp = nullptr;
+  int64_t* cp = nullptr;
+  int32_t* ri = nullptr;
+  float* v = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!dalloc(&Dtmp, (size_t)c->n * c->p) || !dalloc(&cp, (size_t)m + 1) ||
+      !dalloc(&ri, (size_t)m * s) || !dalloc(&v, (size_t)m * s) ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaFree(Dtmp); cudaFree(cp); cudaFree(ri); cudaFree(v);
+    return DL_ENOMEM;
+  }
+  rc = enq_convert_y(c, Y, m) == cudaSuccess ? DL_OK : DL_ECUDA;
+  const bool prof = c->prof;
+  c->prof = false;
+  int* knobs[4] = {&c->cfg_corr_tc, &c->cfg_omp_warps, &c->cfg_acc_mult, &c->cfg_row_per_sm};
+  const int choices[4][3] = {{1, 0, -1}, {4, 2, 1}, {1, 2, -1}, {4, 2, 8}};
+  time_iteration(c, Y, m, D, Dtmp, s, cp, ri, v, e0, e1);  // warm-up
+  float best = time_iteration(c, Y, m, D, Dtmp, s, cp, ri, v, e0, e1);
+  for (int k = 0; k < 4 && rc == DL_OK; ++k) {
+    const int keep = *knobs[k];
+    int arg = keep;
+    for (int q = 0; q < 3; ++q) {
+      const int cand = choices[k][q];
+      if (cand < 0 || cand == keep) continue;
+      if (k == 0 && !dlk::corr_tc_supported(Y, c->p, c->n, c->lda)) continue;
+      *knobs[k] = cand;
+      const float t = time_iteration(c, Y, m, D, Dtmp, s, cp, ri, v, e0, e1);
+      if (t < best) {
+        best = t;
+        arg = cand;
+      }
+    }
+    *knobs[k] = arg;
+  }
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) rc = DL_ECUDA;
+  c->prof = prof;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->gkey_seen = 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(Dtmp); cudaFree(cp); cudaFree(ri); cudaFree(v);
+  cudaMemset(c->err, 0, sizeof(int));
+  return rc;
+}
+
+extern "C" int dl_get_config(dl_ctx* c, int* cfg4) {
+  if (!c || !cfg4) return DL_EINVAL;
+  cfg4[0] = c->cfg_corr_tc;
+  cfg4[1] = c->cfg_omp_warps;
+  cfg4[2] = c->cfg_acc_mult;
+  cfg4[3] = c->cfg_row_per_sm;
+  return DL_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Batches of independent problems: one context per problem, all problems'
+// iterations captured into one CUDA graph with one branch (stream) per problem.
+
+struct dl_batch {
+  int count = 0;
+  int dev = 0;
+  cudaStream_t main = nullptr;
+  std::vector<dl_problem> probs;
+  std::vector<dl_ctx*> ctxs;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_iters = -1;
+};
+
+namespace {
+
+void free_batch(dl_batch* b) {
+  if (!b) return;
+  DevGuard g(b->dev);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (dl_ctx* c : b->ctxs) free_ctx(c);
+  for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+
+cudaError_t enq_batch(dl_batch* b, int iters) {
+  cudaError_t e = cudaEventRecord(b->fork, b->main);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < b->count; ++k) {
+    dl_ctx* c = b->ctxs[k];
+    const dl_problem& q = b->probs[k];
+    if ((e = cudaStreamWaitEvent(c->st, b->fork, 0)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->iter, 0, sizeof(int), c->st)) != cudaSuccess) return e;
+    if ((e = enq_convert_y(c, q.Y, q.m)) != cudaSuccess) return e;
+    for (int it = 0; it < iters; ++it)
+      if ((e = enq_iteration(c, q.Y, q.m, q.D, q.s, q.colptr, q.rowidx, q.val)) != cudaSuccess)
+        return e;
+    if ((e = cudaEventRecord(b->joins[k], c->st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(b->main, b->joins[k], 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int dl_batch_create(dl_batch** out, const dl_problem* problems, int count, int precision,
+                               int autotune, void* stream) {
+  if (!out || !problems || count < 1) return DL_EINVAL;
+  for (int k = 0; k < count; ++k) {
+    const dl_problem& q = problems[k];
+    if (q.m < 1 || !q.Y || !q.D || !q.colptr || !q.rowidx || !q.val || ptr_kind(q.Y) != 1 ||
+        ptr_kind(q.D) != 1 || ptr_kind(q.colptr) != 1 || ptr_kind(q.rowidx) != 1 ||
+        ptr_kind(q.val) != 1)
+      return DL_EINVAL;
+  }
+  dl_batch* b = new dl_batch();
+  cudaGetDevice(&b->dev);
+  b->count = count;
+  b->main = (cudaStream_t)stream;
+  b->probs.assign(problems, problems + count);
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    free_batch(b);
+    return DL_ECUDA;
+  }
+  for (int k = 0; k < count; ++k) {
+    const dl_problem& q = problems[k];
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      free_batch(b);
+      return DL_ECUDA;
+    }
+    b->streams.push_back(st);
+    b->joins.push_back(ev);
+    dl_ctx* c = nullptr;
+    const int rc = dl_init(&c, q.p, q.n, q.m, q.s, precision, st);
+    if (rc != DL_OK) {
+      free_batch(b);
+      return rc;
+    }
+    b->ctxs.push_back(c);
+  }
+  // one eager iteration per problem (sets kernel attributes outside any capture), then tune
+  for (int k = 0; k < count; ++k) {
+    dl_ctx* c = b->ctxs[k];
+    const dl_problem& q = b->probs[k];
+    int rc = autotune ? dl_autotune(c, q.Y, q.m, q.D, q.s) : DL_OK;
+    if (rc == DL_OK && !autotune) {
+      float* Dtmp = nullptr;
+      if (!dalloc(&Dtmp, (size_t)c->n * c->p)) rc = DL_ENOMEM;
+      if (rc == DL_OK && (cudaMemcpyAsync(Dtmp, q.D, sizeof(float) * (size_t)c->n * c->p,
+                                          cudaMemcpyDeviceToDevice, c->st) != cudaSuccess ||
+                          enq_convert_y(c, q.Y, q.m) != cudaSuccess ||
+                          enq_iteration(c, q.Y, q.m, Dtmp, q.s, q.colptr, q.rowidx, q.val) !=
+                              cudaSuccess ||
+                          cudaStreamSynchronize(c->st) != cudaSuccess))
+        rc = DL_ECUDA;
+      cudaFree(Dtmp);
+    }
+    if (rc != DL_OK) {
+      free_batch(b);
+      return rc;
+    }
+  }
+  *out = b;
+  return DL_OK;
+}
+
+extern "C" int dl_batch_iterate(dl_batch* b, int iters, double* rmse) {
+  if (!b || iters < 0) return DL_EINVAL;
+  if (iters == 0) return DL_OK;
+  DevGuard g(b->dev);
+  for (dl_ctx* c : b->ctxs)
+    if (int rc = ensure_rmse(c, iters)) return rc;
+  if (!b->gexec || b->graph_iters != iters) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    if (!b->main) return DL_EINVAL;  // capture needs a non-default stream
+    cudaGraph_t graph = nullptr;
+    DL_CHECK(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t e = enq_batch(b, iters);
+    const cudaError_t e2 = cudaStreamEndCapture(b->main, &graph);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (e2 != cudaSuccess) return cuda_status(e2);
+    const cudaError_t e3 = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) {
+      b->gexec = nullptr;
+      return cuda_status(e3);
+    }
+    b->graph_iters = iters;
+  }
+  DL_CHECK(cudaGraphLaunch(b->gexec, b->main));
+  for (dl_ctx* c : b->ctxs) c->launches += (int64_t)iters * (kKernelsOmp + kKernelsScan + kKernelsJau);
+  if (rmse) {
+    DL_CHECK(cudaStreamSynchronize(b->main));
+    for (int k = 0; k < b->count; ++k)
+      DL_CHECK(cudaMemcpy(rmse + (size_t)k * 2 * iters, b->ctxs[k]->rmse, sizeof(double) * 2 * iters,
+                          cudaMemcpyDeviceToHost));
+    for (dl_ctx* c : b->ctxs)
+      if (int rc = take_device_error(c)) return rc;
+  }
+  return DL_OK;
+}
+
+extern "C" int dl_batch_destroy(dl_batch* b) {
+  free_batch(b);
+  return DL_OK;
+}
+
+extern "C" int64_t dl_batch_kernel_launches(dl_batch* b) {
+  if (!b) return 0;
+  int64_t t = 0;
+  for (dl_ctx* c : b->ctxs) t += c->launches;
+  return t;
+}
+
+extern "C" int dl_batch_config(dl_batch* b, int k, int* cfg4) {
+  if (!b || k < 0 || k >= b->count) return DL_EINVAL;
+  return dl_get_config(b->ctxs[k], cfg4);
+}

@@ -47,7 +47,8 @@ cudaError_t corr_lp(int kind, const void* A, int64_t rows_a, const float* a_inv_
 // FP64 re-solve.
 cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                       int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                      int* rs_list, int* rs_count, int rs_cap, cudaStream_t st);
+                      int* rs_list, int* rs_count, int rs_cap, int warps_per_block,
+                      cudaStream_t st);
 
 // FP64 re-solve (k_resolve.cu): full FP64 OMP of the listed signals, overwriting their slots.
 constexpr int DL_RESOLVE_SMAX = 16;
@@ -68,8 +69,12 @@ struct JauWork {
   int nb_accum;
   int nb_row;
 };
-int jau_accum_blocks(int p, int n);
-int jau_row_blocks();
+// Grid sizes: mult selects 1x/2x the base CTA count of the accumulation pass
+// and 2/4/8 CTAs per SM for the row pass; *_max give the partial-buffer sizes.
+int jau_accum_blocks(int p, int n, int mult);
+int jau_accum_blocks_max(int p, int n);
+int jau_row_blocks(int per_sm);
+int jau_row_blocks_max();
 size_t jau_accum_smem(int p, int n);
 
 cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int n, int s,

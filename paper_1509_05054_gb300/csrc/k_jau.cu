@@ -400,8 +400,15 @@ size_t jau_accum_smem(int p, int n) {
   const size_t bytes = sizeof(float) * ((size_t)n * p + n);
   return bytes <= 200u * 1024u ? bytes : 0;
 }
-int jau_accum_blocks(int p, int n) { return jau_accum_smem(p, n) > 0 ? num_sms() : 4 * num_sms(); }
-int jau_row_blocks() { return 4 * num_sms(); }
+int jau_accum_blocks(int p, int n, int mult) {
+  // the shared-memory form runs 1 CTA per SM unless two partial slices fit on one SM
+  if (jau_accum_smem(p, n) > 0)
+    return (mult >= 2 && jau_accum_smem(p, n) <= 100u * 1024u) ? 2 * num_sms() : num_sms();
+  return (mult >= 2 ? 8 : 4) * num_sms();
+}
+int jau_accum_blocks_max(int p, int n) { return jau_accum_smem(p, n) > 0 ? 2 * num_sms() : 8 * num_sms(); }
+int jau_row_blocks(int per_sm) { return (per_sm == 2 || per_sm == 8 ? per_sm : 4) * num_sms(); }
+int jau_row_blocks_max() { return 8 * num_sms(); }
 
 cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int n, int s,
                            const int32_t* idx, const float* val, const int32_t* cnt,

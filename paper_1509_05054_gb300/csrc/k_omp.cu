@@ -284,13 +284,13 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
 template <int NT, int SMAX, bool SMEM, bool FULLN>
 cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                      int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                     int* rs_list, int* rs_count, int rs_cap, cudaStream_t st) {
-  int warps = OMP_THREADS / 32;
+                     int* rs_list, int* rs_count, int rs_cap, int warps_hint, cudaStream_t st) {
+  int warps = (warps_hint >= 1 && warps_hint <= OMP_THREADS / 32) ? warps_hint : OMP_THREADS / 32;
   size_t smem = 0;
   if (SMEM) {
     const size_t per_warp = (size_t)(SMAX - 1) * (NT / 2) * 32 * sizeof(float2);
-    warps = (int)((190u * 1024u) / per_warp);
-    if (warps > OMP_THREADS / 32) warps = OMP_THREADS / 32;
+    const int cap = (int)((190u * 1024u) / per_warp);
+    if (warps > cap) warps = cap;
     if (warps < 1) warps = 1;
     smem = per_warp * warps;
     cudaFuncSetAttribute(omp_warp_kernel<NT, SMAX, SMEM, FULLN>,
@@ -314,21 +314,21 @@ constexpr bool fits_regs() {
 template <int NT, int SMAX>
 cudaError_t pick_store(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                        int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                       int* rl, int* rc, int rcap, cudaStream_t st) {
+                       int* rl, int* rc, int rcap, int wh, cudaStream_t st) {
   constexpr bool SM = !fits_regs<NT, SMAX>();
   if (n == 32 * NT)
-    return launch_t<NT, SMAX, SM, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
-  return launch_t<NT, SMAX, SM, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+    return launch_t<NT, SMAX, SM, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
+  return launch_t<NT, SMAX, SM, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
 }
 
 template <int NT>
 cudaError_t pick_s(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                    int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                   int* rl, int* rc, int rcap, cudaStream_t st) {
-  if (s <= 4) return pick_store<NT, 4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
-  if (s <= 8) return pick_store<NT, 8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
-  if (s <= 12) return pick_store<NT, 12>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
-  return pick_store<NT, 16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+                   int* rl, int* rc, int rcap, int wh, cudaStream_t st) {
+  if (s <= 4) return pick_store<NT, 4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
+  if (s <= 8) return pick_store<NT, 8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
+  if (s <= 12) return pick_store<NT, 12>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
+  return pick_store<NT, 16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
 }
 
 }  // namespace
@@ -337,14 +337,14 @@ bool omp_supported(int n, int s) { return n >= 1 && n <= 1024 && s >= 1 && s <= 
 
 cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                       int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                      int* rl, int* rc, int rcap, cudaStream_t st) {
+                      int* rl, int* rc, int rcap, int wh, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   const int nt = (n + 31) / 32;
-  if (nt <= 2) return pick_s<2>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
-  if (nt <= 4) return pick_s<4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
-  if (nt <= 8) return pick_s<8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
-  if (nt <= 16) return pick_s<16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
-  return pick_s<32>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+  if (nt <= 2) return pick_s<2>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
+  if (nt <= 4) return pick_s<4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
+  if (nt <= 8) return pick_s<8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
+  if (nt <= 16) return pick_s<16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
+  return pick_s<32>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
 }
 
 }  // namespace dlk

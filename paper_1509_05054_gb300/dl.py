@@ -27,6 +27,13 @@ _lib = None
 _lock = threading.Lock()
 
 
+class DLProblem(ctypes.Structure):
+    """struct dl_problem of the C header."""
+    _fields_ = [("p", ctypes.c_int), ("n", ctypes.c_int), ("s", ctypes.c_int),
+                ("m", ctypes.c_int64), ("Y", ctypes.c_void_p), ("D", ctypes.c_void_p),
+                ("colptr", ctypes.c_void_p), ("rowidx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
 class DLError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -65,6 +72,17 @@ def load(build_if_missing: bool = True):
         lib.dl_last_resolved.argtypes = [P]
         lib.dl_last_resolved.restype = i64
         lib.dl_phase_times.argtypes = [P, P, i32]
+        lib.dl_autotune.argtypes = [P, P, i64, P, i32]
+        lib.dl_get_config.argtypes = [P, P]
+        lib.dl_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(DLProblem), i32, i32, i32, P]
+        lib.dl_batch_iterate.argtypes = [P, i32, P]
+        lib.dl_batch_destroy.argtypes = [P]
+        lib.dl_batch_kernel_launches.argtypes = [P]
+        lib.dl_batch_kernel_launches.restype = i64
+        lib.dl_batch_config.argtypes = [P, i32, P]
+        for name in ("dl_autotune", "dl_get_config", "dl_batch_create", "dl_batch_iterate",
+                     "dl_batch_destroy", "dl_batch_config"):
+            getattr(lib, name).restype = i32
         for name in ("dl_init", "dl_set_stream", "dl_destroy", "omp_code", "jau_update", "dl_iterate",
                      "dl_sync", "dl_set_profiling", "dl_phase_times", "dl_gram", "dl_correlate",
                      "dl_uses_tensor_cores", "dl_correlate_noalloc"):
@@ -187,6 +205,48 @@ def jau_update(ctx: int, Y, m: int, D, colptr, rowidx, val, rmse2=None) -> None:
 def dl_iterate(ctx: int, Y, m: int, D, s: int, iters: int, colptr, rowidx, val, rmse=None) -> None:
     _check(load().dl_iterate(ctx, _ptr(Y), m, _ptr(D), s, iters, _ptr(colptr), _ptr(rowidx),
                              _ptr(val), _ptr(rmse)), "dl_iterate")
+
+
+def dl_autotune(ctx: int, Y, m: int, D, s: int) -> None:
+    _check(load().dl_autotune(ctx, _ptr(Y), m, _ptr(D), s), "dl_autotune")
+
+
+def dl_get_config(ctx: int) -> dict:
+    import numpy as np
+    out = np.zeros(4, np.int32)
+    _check(load().dl_get_config(ctx, out.ctypes.data), "dl_get_config")
+    return dict(zip(("corr_tensor_cores", "omp_warps", "accum_mult", "rows_per_sm"), out.tolist()))
+
+
+def dl_batch_create(problems, precision: int = DL_FP32, autotune: bool = True, stream=None):
+    """problems: list of dicts with p, n, s, m and device tensors Y, D, colptr, rowidx, val."""
+    arr = (DLProblem * len(problems))()
+    for k, q in enumerate(problems):
+        arr[k] = DLProblem(q["p"], q["n"], q["s"], q["m"], _ptr(q["Y"]), _ptr(q["D"]),
+                           _ptr(q["colptr"]), _ptr(q["rowidx"]), _ptr(q["val"]))
+    b = ctypes.c_void_p()
+    _check(load().dl_batch_create(ctypes.byref(b), arr, len(problems), precision,
+                                  1 if autotune else 0, _stream_ptr(stream)), "dl_batch_create")
+    return b.value
+
+
+def dl_batch_iterate(batch: int, iters: int, rmse=None) -> None:
+    _check(load().dl_batch_iterate(batch, iters, _ptr(rmse)), "dl_batch_iterate")
+
+
+def dl_batch_destroy(batch: int) -> None:
+    load().dl_batch_destroy(batch)
+
+
+def dl_batch_kernel_launches(batch: int) -> int:
+    return int(load().dl_batch_kernel_launches(batch))
+
+
+def dl_batch_config(batch: int, k: int) -> dict:
+    import numpy as np
+    out = np.zeros(4, np.int32)
+    _check(load().dl_batch_config(batch, k, out.ctypes.data), "dl_batch_config")
+    return dict(zip(("corr_tensor_cores", "omp_warps", "accum_mult", "rows_per_sm"), out.tolist()))
 
 
 class Context:

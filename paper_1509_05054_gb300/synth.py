@@ -145,6 +145,25 @@ WORKLOADS = {
 }
 
 
+def batched_problems(count: int = 16, m_scale: float = 1.0, seed: int = 5000, dtype=np.float32):
+    """Independent DL problems of uneven shapes (the batched workload): p in
+    {36, 64, 100} (6x6, 8x8, 10x10 patches of the 1/f^2 images), n in
+    {128, 256, 512, 1024}, m uniform in 5000..60000 (times m_scale), s uniform in
+    4..12.  Returns a list of dicts with p, n, m, s, Y (m, p) and D (n, p)."""
+    g = _rng(seed)
+    out = []
+    for k in range(count):
+        side = int(g.choice([6, 8, 10]))
+        n = int(g.choice([128, 256, 512, 1024]))
+        m = max(64, int(round(int(g.integers(5000, 60001)) * m_scale)))
+        s = int(g.integers(4, 13))
+        p = side * side
+        Y = image_patches(m, side=side, workload_id=100 + k, first_image=200 + 20 * k, dtype=dtype)
+        D = random_dictionary(p, n, seed=6000 + k, dtype=dtype)
+        out.append(dict(p=p, n=n, m=m, s=s, Y=np.ascontiguousarray(Y), D=np.ascontiguousarray(D)))
+    return out
+
+
 def workload_inputs(name: str, m: int | None = None, dtype=np.float32):
     """(Y, D_init, spec) for a named workload; m may be reduced for sampling."""
     spec = dict(WORKLOADS[name])
