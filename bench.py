@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--forms", default="fp32,bf16,fp8",
                     help="precision forms to time; the reported value is the fastest form whose "
                          "final RMSE is within 1%% of the plain FP32 form")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-problems measurement")
+    ap.add_argument("--batched-iters", type=int, default=20)
     ap.add_argument("--m", type=int, default=None,
                     help="override the number of signals (profiling of smaller cases)")
     return ap.parse_args()
@@ -354,6 +357,10 @@ def run_ours(args):
                "d2h_bytes_per_step": 4 * n * p + 8 * (m + 1) + 8 * nnz + 16 + 4,
                "steps": args.e2e_steps}
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, dl, torch, st)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         Ys, Ds, sp = synth.workload_inputs(args.workload, m=args.cpu_sample)
@@ -377,11 +384,59 @@ def run_ours(args):
                     "equal_rmse": f"final relative RMSE after {RMSE_ITERS} iterations within "
                                   f"{100 * EQUAL_RMSE:.0f}% of the plain FP32 form"}),
                 "roofline": roof, "phases_ms": phases, "phase_roofline": per_phase,
-                "forms": forms,
+                "forms": forms, "batched": batched,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def run_batched(args, dl, torch, st):
+    """16 independent problems of uneven p, n, m, s; all their iterations in one
+    CUDA graph launch (one branch per problem), launch shapes autotuned."""
+    probs = synth.batched_problems(16)
+    dev = []
+    for q in probs:
+        m, s = q["m"], q["s"]
+        dev.append(dict(p=q["p"], n=q["n"], s=s, m=m, Y=torch.from_numpy(q["Y"]).cuda(),
+                        D=torch.from_numpy(q["D"]).cuda(),
+                        colptr=torch.zeros(m + 1, dtype=torch.int64, device="cuda"),
+                        rowidx=torch.zeros(m * s, dtype=torch.int32, device="cuda"),
+                        val=torch.zeros(m * s, dtype=torch.float32, device="cuda")))
+    D0 = [d["D"].clone() for d in dev]
+    t0 = time.perf_counter()
+    b = dl.dl_batch_create(dev, autotune=True, stream=st)
+    tune_s = time.perf_counter() - t0
+    iters = args.batched_iters
+    dl.dl_batch_iterate(b, iters, None)              # capture + warm-up launch
+    st.synchronize()
+    for d, d0 in zip(dev, D0):
+        d["D"].copy_(d0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = dl.dl_batch_kernel_launches(b)
+    e0.record(st)
+    rm = np.zeros(len(dev) * 2 * iters)
+    dl.dl_batch_iterate(b, iters, None)
+    e1.record(st)
+    st.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = dl.dl_batch_kernel_launches(b) - launches0
+    # RMSE of the timed run (read after timing)
+    for d, d0 in zip(dev, D0):
+        d["D"].copy_(d0)
+    torch.cuda.synchronize()
+    dl.dl_batch_iterate(b, iters, rm)
+    cfgs = [dl.dl_batch_config(b, k) for k in range(len(dev))]
+    dl.dl_batch_destroy(b)
+    rm = rm.reshape(len(dev), iters, 2)
+    total = sum(q["m"] for q in probs)
+    return {"value": total * iters / (ms * 1e-3), "unit": "signal-iterations/s",
+            "ms": ms, "iters": iters, "problems": len(probs), "signals": total,
+            "one_graph_launch": True, "gpu_launches": launches, "autotune_s": tune_s,
+            "shapes": [dict(p=q["p"], n=q["n"], m=q["m"], s=q["s"], cfg=c,
+                            final_rmse=float(rm[k, -1, 1]))
+                       for k, (q, c) in enumerate(zip(probs, cfgs))]}
 
 
 def main():
