@@ -282,6 +282,66 @@ int64_t dl_batch_kernel_launches(dl_batch* batch);
 int dl_batch_config(dl_batch* batch, int k, int* cfg4);
 
 /*
+ * Learned support proposer.  A small MLP p -> hidden -> hidden -> n (GELU
+ * activations, sigmoid outputs; BF16 weights with FP32 master copies) trained
+ * with binary cross-entropy on the multi-hot OMP supports the method itself
+ * produces, on the tensor cores with the library's own forward and backward
+ * kernels and Adam.  At sparse coding it proposes the K atoms with the largest
+ * logits per signal; OMP then runs over those candidates only, and a signal
+ * whose residual norm exceeds (1 + tol) times the residual of its last full
+ * OMP is coded again by full OMP (the fallback, which also judges the error).
+ * This is the learned form of Algorithm 1 step 1; the atom update is unchanged.
+ */
+typedef struct dl_proposer dl_proposer;
+
+/*
+ * dl_proposer_create -- p <= DL_MAX_P, n and hidden multiples of 64, batch (rows
+ * per training step and per inference chunk) a multiple of 64.  Weights start
+ * at zero: set them with dl_proposer_set_weights.  Returns DL_OK, DL_EINVAL or
+ * DL_ENOMEM.
+ */
+int dl_proposer_create(dl_proposer** out, int p, int n, int hidden, int64_t batch, void* stream);
+int dl_proposer_destroy(dl_proposer* prop);
+
+/* Host FP32 weights: W1 hidden x p, b1 hidden, W2 hidden x hidden, b2 hidden,
+ * W3 n x hidden, b3 n (row-major, out x in).  Resets the Adam state. */
+int dl_proposer_set_weights(dl_proposer* prop, const float* W1, const float* b1, const float* W2,
+                            const float* b2, const float* W3, const float* b3);
+
+/* which = 0: current weights; 1: gradients of the last training step.  Host
+ * outputs, same shapes as dl_proposer_set_weights.  Synchronises. */
+int dl_proposer_get(dl_proposer* prop, int which, float* W1, float* b1, float* W2, float* b2,
+                    float* W3, float* b3);
+
+/*
+ * dl_proposer_train -- one pass over m training signals in batches of `batch`
+ * rows (the last partial batch is skipped): Y device m x p, sup device m x s
+ * support slots (-1 = empty), perm device int64 row order or NULL (in order),
+ * Adam step lr (lr = 0 computes gradients only).  mean_loss: host, mean BCE of
+ * the batches, or NULL.  Synchronises when mean_loss is given.
+ */
+int dl_proposer_train(dl_proposer* prop, const float* Y, int64_t m, const int32_t* sup, int s,
+                      const int64_t* perm, int64_t batch, float lr, double* mean_loss);
+
+/* dl_proposer_forward -- logits (device m x n FP32) and/or the K largest-logit
+ * atoms (device m x K int32, ascending) of m signals.  Synchronises. */
+int dl_proposer_forward(dl_proposer* prop, const float* Y, int64_t m, float* logits, int32_t* cand,
+                        int K);
+
+/*
+ * dl_attach_proposer -- sparse coding of dl_iterate on ctx uses the proposer:
+ * K candidates (s_max <= K <= 32) per signal; every full_every-th iteration
+ * (starting with the first after attaching) runs full OMP for all signals and
+ * records their residuals; tol is the fallback margin (0.01 = 1%).  prop NULL
+ * detaches.  Returns DL_OK, DL_EINVAL or DL_ENOMEM.
+ */
+int dl_attach_proposer(dl_ctx* ctx, dl_proposer* prop, int K, int full_every, double tol);
+
+/* dl_last_fallbacks -- signals sent to full OMP by the most recent learned
+ * iteration (synchronises). */
+int64_t dl_last_fallbacks(dl_ctx* ctx);
+
+/*
  * dl_sync -- wait for the context's stream and report a pending device-side
  * error (DL_ENUMERIC for non-finite inputs met by a kernel) or DL_OK.
  */

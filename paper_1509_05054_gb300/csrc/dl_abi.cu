@@ -4,6 +4,7 @@
 #include "../../include/dl_gb300.h"
 #include "dl_internal.cuh"
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -11,6 +12,36 @@
 #include <string.h>
 
 #include <vector>
+
+// The learned support proposer (MLP p -> hidden -> hidden -> n, BF16 weights
+// with FP32 masters and Adam state; see k_mlp.cu).
+struct dl_proposer {
+  int dev = 0, p = 0, pk = 0, n = 0, hidden = 0;
+  int64_t bmax = 0;        // rows per forward chunk / training batch
+  cudaStream_t st = nullptr;
+  float* w[6] = {};        // W1 (hidden x pk), b1, W2 (hidden x hidden), b2, W3 (n x hidden), b3
+  float* g[6] = {};        // gradients of the last training step
+  float* am[6] = {};       // Adam first moments
+  float* av[6] = {};       // Adam second moments
+  int64_t wlen[6] = {};
+  void* wb[3] = {};        // BF16 copies of W1, W2, W3
+  void* wt[2] = {};        // BF16 transposes of W2 (hidden x hidden) and W3 (hidden x n)
+  // activations (bmax rows)
+  void* X = nullptr;       // BF16 bmax x pk
+  float* A1 = nullptr;     // FP32 pre-activations (training)
+  float* A2 = nullptr;
+  void* H1 = nullptr;      // BF16 activations
+  void* H2 = nullptr;
+  float* Z = nullptr;      // FP32 logits (training)
+  void* Zb = nullptr;      // BF16 logits (inference)
+  int32_t* sup = nullptr;  // gathered supports of the batch (bmax x 16)
+  // backward scratch (BF16)
+  void *dZ = nullptr, *dZt = nullptr, *H2t = nullptr, *dA2 = nullptr, *dA2t = nullptr, *H1t = nullptr,
+       *dA1 = nullptr, *dA1t = nullptr, *Xt = nullptr;
+  double* loss = nullptr;
+  int* err = nullptr;
+  int step = 0;
+};
 
 struct dl_ctx {
   int dev = 0;
@@ -34,6 +65,19 @@ struct dl_ctx {
   int* rs_count = nullptr;
   double* rs_scratch = nullptr;
   int64_t rs_flagged = 0;  // total flagged (read back at synchronising calls)
+  // learned proposer attached (dl_attach_proposer)
+  dl_proposer* prop = nullptr;
+  int prop_K = 0, prop_full_every = 10;
+  float prop_tol2 = 1.0201f;
+  int64_t prop_counter = 0;
+  float* rr_ref = nullptr;   // residual energy of the last full OMP of each signal
+  float* rr_L = nullptr;     // residual energy of the restricted OMP
+  int* fb_list = nullptr;
+  int* fb_count = nullptr;
+  int32_t* cand = nullptr;   // m_max x K
+  void* Ybf = nullptr;       // m_max x pk BF16 copy of Y for the proposer
+  bool learned_now = false;  // the iteration being enqueued uses the proposer
+  cudaGraphExec_t gexec_learned = nullptr;
   int32_t* sidx = nullptr;
   float* sval = nullptr;
   int32_t* scnt = nullptr;
@@ -55,6 +99,7 @@ struct dl_ctx {
   int64_t gkey_m = -1;
   int gkey_s = -1;
   int gkey_seen = 0;
+  int gkey_seen_l = 0;
   int64_t launches = 0;
   // launch shapes (chosen by dl_autotune; defaults otherwise)
   int cfg_omp_warps = 4;  // warps per CTA of the OMP kernel
@@ -80,6 +125,10 @@ void free_ctx(dl_ctx* c) {
   cudaGetDevice(&prev);
   cudaSetDevice(c->dev);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gexec_learned) cudaGraphExecDestroy(c->gexec_learned);
+  for (void* q : {(void*)c->rr_ref, (void*)c->rr_L, (void*)c->fb_list, (void*)c->fb_count,
+                  (void*)c->cand, c->Ybf})
+    if (q) cudaFree(q);
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
   void* ptrs[] = {c->G, c->A0, c->Dhi, c->Dlo, c->Ylp, c->Ysc, c->Dlp, c->Dsc, c->rs_list,
@@ -216,19 +265,46 @@ cudaError_t enq_corr(dl_ctx* c, const float* Y, int64_t m, const float* D, bool 
   return dlk::corr_tf32x3(Y, m, c->Dhi, c->Dlo, c->n, c->p, c->A0, c->lda, c->err, c->st);
 }
 
+cudaError_t enq_proposer_forward(dl_proposer* P, const void* Xbf, int64_t m, int K, int32_t* cand,
+                                 cudaStream_t st);
+
+// Sparse coding with the learned proposer: top-K candidates from the MLP,
+// OMP restricted to them, full OMP for the signals whose residual energy
+// exceeds tol2 times the one of their last full OMP.
+cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
+  cudaError_t e = enq_proposer_forward(c->prop, c->Ybf, m, c->prop_K, c->cand, c->st);
+  if (e != cudaSuccess) return e;
+  mark(c, 2);
+  if ((e = cudaMemsetAsync(c->fb_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
+  e = dlk::omp_restricted(c->cand, c->prop_K, D, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval,
+                          c->scnt, c->rr_L, c->rr_ref, c->prop_tol2, c->fb_list, c->fb_count, c->err,
+                          c->st);
+  if (e != cudaSuccess) return e;
+  e = dlk::omp_listed(c->fb_list, c->fb_count, D, c->G, c->n, Y, c->p, s, c->sidx, c->sval, c->scnt,
+                      c->rr_ref, c->err, c->rs_list, c->rs_count, (int)c->m_max, c->st);
+  if (e != cudaSuccess) return e;
+  e = dlk::omp_resolve64(Y, c->p, D, c->n, s, c->rs_list, c->rs_count, (int)c->m_max,
+                         c->rs_scratch, c->sidx, c->sval, c->scnt, c->st);
+  mark(c, 3);
+  return e;
+}
+
 cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
   const bool tc = tc_ok(c, Y, D);
   mark(c, 0);
   cudaError_t e = enq_gram(c, D, tc);
   if (e != cudaSuccess) return e;
   mark(c, 1);
+  if (c->prop && c->learned_now) return enq_omp_learned(c, Y, m, D, s);
   e = enq_corr(c, Y, m, D, tc);
   if (e != cudaSuccess) return e;
   mark(c, 2);
   e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st);
   if (e != cudaSuccess) return e;
   e = dlk::omp_batch(c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval, c->scnt, c->err,
-                     c->rs_list, c->rs_count, (int)c->m_max, c->cfg_omp_warps, c->st);
+                     c->rs_list, c->rs_count, (int)c->m_max, c->cfg_omp_warps,
+                     c->prop ? c->rr_ref : nullptr, c->st);
   if (e != cudaSuccess) return e;
   e = dlk::omp_resolve64(Y, c->p, D, c->n, s, c->rs_list, c->rs_count, (int)c->m_max,
                          c->rs_scratch, c->sidx, c->sval, c->scnt, c->st);
@@ -267,6 +343,20 @@ cudaError_t enq_iteration(dl_ctx* c, const float* Y, int64_t m, float* D, int s,
   e = dlk::counts_to_colptr(c->scnt, m, c->bsum, colptr, c->st);
   if (e != cudaSuccess) return e;
   return enq_jau(c, Y, m, D, s, colptr, rowidx, val);
+}
+
+int64_t proposer_chunks(dl_proposer* P, int64_t m);
+
+// Kernels one DL iteration enqueues (the claim behind dl_kernel_launches).
+int64_t kernels_per_iteration(dl_ctx* c, bool learned, int64_t m) {
+  const bool tc = dlk::corr_tc_supported(nullptr, c->p, c->n, c->lda) && c->cfg_corr_tc &&
+                  !getenv("DL_FORCE_SIMT_GEMM");
+  int64_t k = (tc ? 2 : 1) /* split + Gram */ + kKernelsScan + kKernelsJau;
+  if (learned)
+    k += 4 * proposer_chunks(c->prop, m) /* 3 GEMMs + top-K */ + 3 /* restricted, listed, FP64 */;
+  else
+    k += (c->lp_kind ? 2 : 1) /* correlations */ + 2 /* OMP, FP64 re-solve */;
+  return k;
 }
 
 int check_common(dl_ctx* c, int64_t m) {
@@ -456,6 +546,7 @@ int omp_code(dl_ctx* c, const float* Y, int64_t m, const float* D, int s, int64_
     dv = c->hval;
   }
   DL_CHECK(enq_convert_y(c, dY, m));
+  c->learned_now = false;
   DL_CHECK(enq_omp(c, dY, m, dD, s));
   DL_CHECK(dlk::counts_to_colptr(c->scnt, m, c->bsum, dcp, c->st));
   DL_CHECK(dlk::slots_to_csc(c->sidx, c->sval, c->scnt, m, s, dcp, dri, dv, c->st));
@@ -550,6 +641,9 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
   if (!same) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
+    if (c->gexec_learned) cudaGraphExecDestroy(c->gexec_learned);
+    c->gexec_learned = nullptr;
+    c->gkey_seen_l = 0;
     memcpy(c->gkey, key, sizeof(key));
     c->gkey_m = m;
     c->gkey_s = s;
@@ -557,28 +651,35 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
   }
   const bool can_graph = c->st != nullptr && m > 0;
   DL_CHECK(enq_convert_y(c, dY, m));
+  if (c->prop) DL_CHECK(dlk::to_lowp(dlk::LP_BF16, dY, m, c->p, c->Ybf, nullptr, c->st));
   for (int it = 0; it < iters; ++it) {
-    if (can_graph && c->gkey_seen >= 1 && !c->gexec) {
+    const bool learned = c->prop && (c->prop_counter % c->prop_full_every) != 0;
+    c->learned_now = learned;
+    cudaGraphExec_t& gx = learned ? c->gexec_learned : c->gexec;
+    int& seen = learned ? c->gkey_seen_l : c->gkey_seen;
+    if (can_graph && seen >= 1 && !gx) {
       cudaGraph_t graph = nullptr;
       DL_CHECK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
       cudaError_t e = enq_iteration(c, dY, m, dD, s, dcp, dri, dv);
       cudaError_t e2 = cudaStreamEndCapture(c->st, &graph);
       if (e != cudaSuccess) return cuda_status(e);
       if (e2 != cudaSuccess) return cuda_status(e2);
-      e = cudaGraphInstantiate(&c->gexec, graph, 0);
+      e = cudaGraphInstantiate(&gx, graph, 0);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) {
-        c->gexec = nullptr;
+        gx = nullptr;
         return cuda_status(e);
       }
     }
-    if (c->gexec) {
-      DL_CHECK(cudaGraphLaunch(c->gexec, c->st));
+    if (gx) {
+      DL_CHECK(cudaGraphLaunch(gx, c->st));
     } else {
       DL_CHECK(enq_iteration(c, dY, m, dD, s, dcp, dri, dv));
-      c->gkey_seen++;
+      seen++;
     }
-    c->launches += kKernelsOmp + kKernelsScan + kKernelsJau;
+    c->launches += kernels_per_iteration(c, learned, m);
+    if (c->prop) c->prop_counter++;
+    c->learned_now = false;
     if (c->prof) {
       DL_CHECK(cudaStreamSynchronize(c->st));
       for (int k = 0; k < 8; ++k) {
@@ -857,4 +958,303 @@ extern "C" int64_t dl_batch_kernel_launches(dl_batch* b) {
 extern "C" int dl_batch_config(dl_batch* b, int k, int* cfg4) {
   if (!b || k < 0 || k >= b->count) return DL_EINVAL;
   return dl_get_config(b->ctxs[k], cfg4);
+}
+
+// ---------------------------------------------------------------------------------
+// Learned support proposer: MLP p -> hidden -> hidden -> n with GELU and sigmoid
+// outputs, BCE-with-logits on multi-hot OMP supports, Adam; top-K candidates.
+
+namespace {
+
+constexpr int kPropMaxS = 16;  // support slots gathered per training row
+
+void free_proposer(dl_proposer* P) {
+  if (!P) return;
+  DevGuard g(P->dev);
+  for (int k = 0; k < 6; ++k)
+    for (void* q : {(void*)P->w[k], (void*)P->g[k], (void*)P->am[k], (void*)P->av[k]})
+      if (q) cudaFree(q);
+  for (void* q : {P->wb[0], P->wb[1], P->wb[2], P->wt[0], P->wt[1], P->X, (void*)P->A1,
+                  (void*)P->A2, P->H1, P->H2, (void*)P->Z, P->Zb, (void*)P->sup, P->dZ, P->dZt,
+                  P->H2t, P->dA2, P->dA2t, P->H1t, P->dA1, P->dA1t, P->Xt, (void*)P->loss,
+                  (void*)P->err})
+    if (q) cudaFree(q);
+  delete P;
+}
+
+int64_t proposer_chunks(dl_proposer* P, int64_t m) { return P ? (m + P->bmax - 1) / P->bmax : 0; }
+
+// rows of Y (FP32, p wide; selected by idx when given) -> BF16 rows pk wide, and
+// their support slots (-1 padded to kPropMaxS) when sup is given.
+__global__ void gather_rows_kernel(const float* __restrict__ Y, int p, int pk,
+                                   const int64_t* __restrict__ idx, int64_t B,
+                                   const int32_t* __restrict__ sup_in, int s,
+                                   __nv_bfloat16* __restrict__ X, int32_t* __restrict__ sup_out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * pk) return;
+  const int64_t b = e / pk;
+  const int c = (int)(e - b * pk);
+  const int64_t r = idx ? idx[b] : b;
+  X[e] = __float2bfloat16_rn(c < p ? Y[r * p + c] : 0.f);
+  if (sup_in && c < kPropMaxS) sup_out[b * kPropMaxS + c] = c < s ? sup_in[r * s + c] : -1;
+}
+
+cudaError_t enq_forward_chunk(dl_proposer* P, const void* X, int64_t B, bool train) {
+  const int h = P->hidden;
+  cudaError_t e = dlk::mlp_gemm(X, B, P->wb[0], h, P->pk, dlk::MLP_EPI_GELU_FWD, P->w[1], nullptr, 0,
+                                train ? P->A1 : nullptr, P->H1, h, P->err, P->st);
+  if (e != cudaSuccess) return e;
+  e = dlk::mlp_gemm(P->H1, B, P->wb[1], h, h, dlk::MLP_EPI_GELU_FWD, P->w[3], nullptr, 0,
+                    train ? P->A2 : nullptr, P->H2, h, P->err, P->st);
+  if (e != cudaSuccess) return e;
+  return dlk::mlp_gemm(P->H2, B, P->wb[2], P->n, h, train ? dlk::MLP_EPI_F32 : dlk::MLP_EPI_BF16,
+                       P->w[5], nullptr, 0, train ? P->Z : nullptr, train ? nullptr : P->Zb, P->n,
+                       P->err, P->st);
+}
+
+// Logits/top-K of m signals already converted to BF16 rows (pk wide), in chunks
+// of bmax rows whose activations stay in L2.
+cudaError_t enq_proposer_forward(dl_proposer* P, const void* Xbf, int64_t m, int K, int32_t* cand,
+                                 cudaStream_t st) {
+  P->st = st;
+  for (int64_t r0 = 0; r0 < m; r0 += P->bmax) {
+    const int64_t B = m - r0 < P->bmax ? m - r0 : P->bmax;
+    const void* X = (const __nv_bfloat16*)Xbf + r0 * P->pk;
+    cudaError_t e = enq_forward_chunk(P, X, B, false);
+    if (e != cudaSuccess) return e;
+    if ((e = dlk::mlp_topk(P->Zb, B, P->n, K, cand + r0 * K, st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// One training step on B gathered rows already in P->X / P->sup.
+cudaError_t enq_train_step(dl_proposer* P, int64_t B, float lr) {
+  const int h = P->hidden, n = P->n;
+  cudaError_t e = enq_forward_chunk(P, P->X, B, true);
+  if (e != cudaSuccess) return e;
+  if ((e = dlk::mlp_bce_grad(P->Z, B, n, P->sup, kPropMaxS, P->dZ, P->loss, P->st))) return e;
+  // layer 3
+  if ((e = dlk::mlp_transpose(P->dZ, B, n, P->dZt, P->st))) return e;
+  if ((e = dlk::mlp_transpose(P->H2, B, h, P->H2t, P->st))) return e;
+  if ((e = dlk::mlp_gemm(P->dZt, n, P->H2t, h, (int)B, dlk::MLP_EPI_F32, nullptr, nullptr, 0, P->g[4],
+                         nullptr, h, P->err, P->st)))
+    return e;
+  if ((e = dlk::mlp_colsum(P->dZ, B, n, P->g[5], P->st))) return e;
+  if ((e = dlk::mlp_transpose(P->wb[2], n, h, P->wt[1], P->st))) return e;
+  if ((e = dlk::mlp_gemm(P->dZ, B, P->wt[1], h, n, dlk::MLP_EPI_GELU_BWD, nullptr, P->A2, h, nullptr,
+                         P->dA2, h, P->err, P->st)))
+    return e;
+  // layer 2
+  if ((e = dlk::mlp_transpose(P->dA2, B, h, P->dA2t, P->st))) return e;
+  if ((e = dlk::mlp_transpose(P->H1, B, h, P->H1t, P->st))) return e;
+  if ((e = dlk::mlp_gemm(P->dA2t, h, P->H1t, h, (int)B, dlk::MLP_EPI_F32, nullptr, nullptr, 0, P->g[2],
+                         nullptr, h, P->err, P->st)))
+    return e;
+  if ((e = dlk::mlp_colsum(P->dA2, B, h, P->g[3], P->st))) return e;
+  if ((e = dlk::mlp_transpose(P->wb[1], h, h, P->wt[0], P->st))) return e;
+  if ((e = dlk::mlp_gemm(P->dA2, B, P->wt[0], h, h, dlk::MLP_EPI_GELU_BWD, nullptr, P->A1, h, nullptr,
+                         P->dA1, h, P->err, P->st)))
+    return e;
+  // layer 1
+  if ((e = dlk::mlp_transpose(P->dA1, B, h, P->dA1t, P->st))) return e;
+  if ((e = dlk::mlp_transpose(P->X, B, P->pk, P->Xt, P->st))) return e;
+  if ((e = dlk::mlp_gemm(P->dA1t, h, P->Xt, P->pk, (int)B, dlk::MLP_EPI_F32, nullptr, nullptr, 0,
+                         P->g[0], nullptr, P->pk, P->err, P->st)))
+    return e;
+  if ((e = dlk::mlp_colsum(P->dA1, B, h, P->g[1], P->st))) return e;
+  if (lr > 0.f) {
+    ++P->step;
+    for (int k = 0; k < 6; ++k)
+      if ((e = dlk::mlp_adam(P->w[k], P->g[k], P->am[k], P->av[k], P->wlen[k], lr, P->step,
+                             (k % 2 == 0) ? P->wb[k / 2] : nullptr, P->st)))
+        return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int dl_proposer_create(dl_proposer** out, int p, int n, int hidden, int64_t batch,
+                                  void* stream) {
+  if (!out || p < 1 || p > DL_MAX_P || n < 64 || n > DL_MAX_N || n % 64 || hidden < 64 ||
+      hidden % 64 || batch < 64 || batch % 64 || !dlk::mlp_gemm_supported())
+    return DL_EINVAL;
+  dl_proposer* P = new dl_proposer();
+  cudaGetDevice(&P->dev);
+  P->p = p;
+  P->pk = (p + 63) / 64 * 64;
+  P->n = n;
+  P->hidden = hidden;
+  P->bmax = batch;
+  P->st = (cudaStream_t)stream;
+  const int64_t h = hidden, B = batch;
+  const int64_t lens[6] = {h * P->pk, h, h * h, h, (int64_t)n * h, n};
+  bool ok = true;
+  for (int k = 0; k < 6 && ok; ++k) {
+    P->wlen[k] = lens[k];
+    ok = dalloc(&P->w[k], lens[k]) && dalloc(&P->g[k], lens[k]) && dalloc(&P->am[k], lens[k]) &&
+         dalloc(&P->av[k], lens[k]);
+    if (ok) ok = cudaMemset(P->w[k], 0, lens[k] * 4) == cudaSuccess &&
+                 cudaMemset(P->am[k], 0, lens[k] * 4) == cudaSuccess &&
+                 cudaMemset(P->av[k], 0, lens[k] * 4) == cudaSuccess;
+  }
+  const size_t b2 = 2;  // BF16 bytes
+  ok = ok && dalloc((uint8_t**)&P->wb[0], lens[0] * b2) && dalloc((uint8_t**)&P->wb[1], lens[2] * b2) &&
+       dalloc((uint8_t**)&P->wb[2], lens[4] * b2) && dalloc((uint8_t**)&P->wt[0], lens[2] * b2) &&
+       dalloc((uint8_t**)&P->wt[1], lens[4] * b2) && dalloc((uint8_t**)&P->X, B * P->pk * b2) &&
+       dalloc(&P->A1, B * h) && dalloc(&P->A2, B * h) && dalloc((uint8_t**)&P->H1, B * h * b2) &&
+       dalloc((uint8_t**)&P->H2, B * h * b2) && dalloc(&P->Z, B * n) &&
+       dalloc((uint8_t**)&P->Zb, B * n * b2) && dalloc(&P->sup, B * kPropMaxS) &&
+       dalloc((uint8_t**)&P->dZ, B * n * b2) && dalloc((uint8_t**)&P->dZt, B * n * b2) &&
+       dalloc((uint8_t**)&P->H2t, B * h * b2) && dalloc((uint8_t**)&P->dA2, B * h * b2) &&
+       dalloc((uint8_t**)&P->dA2t, B * h * b2) && dalloc((uint8_t**)&P->H1t, B * h * b2) &&
+       dalloc((uint8_t**)&P->dA1, B * h * b2) && dalloc((uint8_t**)&P->dA1t, B * h * b2) &&
+       dalloc((uint8_t**)&P->Xt, B * P->pk * b2) && dalloc(&P->loss, 1) && dalloc(&P->err, 1) &&
+       cudaMemset(P->err, 0, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_proposer(P);
+    return DL_ENOMEM;
+  }
+  *out = P;
+  return DL_OK;
+}
+
+extern "C" int dl_proposer_destroy(dl_proposer* P) {
+  free_proposer(P);
+  return DL_OK;
+}
+
+extern "C" int dl_proposer_set_weights(dl_proposer* P, const float* W1, const float* b1,
+                                       const float* W2, const float* b2, const float* W3,
+                                       const float* b3) {
+  if (!P || !W1 || !b1 || !W2 || !b2 || !W3 || !b3) return DL_EINVAL;
+  DevGuard g(P->dev);
+  // W1 arrives hidden x p; store it hidden x pk with zero padding
+  DL_CHECK(cudaMemsetAsync(P->w[0], 0, P->wlen[0] * 4, P->st));
+  DL_CHECK(cudaMemcpy2DAsync(P->w[0], (size_t)P->pk * 4, W1, (size_t)P->p * 4, (size_t)P->p * 4,
+                             (size_t)P->hidden, cudaMemcpyHostToDevice, P->st));
+  const float* src[6] = {nullptr, b1, W2, b2, W3, b3};
+  for (int k = 1; k < 6; ++k)
+    DL_CHECK(cudaMemcpyAsync(P->w[k], src[k], P->wlen[k] * 4, cudaMemcpyHostToDevice, P->st));
+  for (int k = 0; k < 3; ++k) DL_CHECK(dlk::mlp_to_bf16(P->w[2 * k], P->wlen[2 * k], P->wb[k], P->st));
+  for (int k = 0; k < 6; ++k) {
+    DL_CHECK(cudaMemsetAsync(P->am[k], 0, P->wlen[k] * 4, P->st));
+    DL_CHECK(cudaMemsetAsync(P->av[k], 0, P->wlen[k] * 4, P->st));
+  }
+  P->step = 0;
+  DL_CHECK(cudaStreamSynchronize(P->st));
+  return DL_OK;
+}
+
+// which = 0: weights, 1: gradients of the last training step (host FP32, W1 hidden x p).
+extern "C" int dl_proposer_get(dl_proposer* P, int which, float* W1, float* b1, float* W2, float* b2,
+                               float* W3, float* b3) {
+  if (!P || (which != 0 && which != 1) || !W1 || !b1 || !W2 || !b2 || !W3 || !b3) return DL_EINVAL;
+  DevGuard g(P->dev);
+  float** src = which ? P->g : P->w;
+  DL_CHECK(cudaStreamSynchronize(P->st));
+  DL_CHECK(cudaMemcpy2D(W1, (size_t)P->p * 4, src[0], (size_t)P->pk * 4, (size_t)P->p * 4,
+                        (size_t)P->hidden, cudaMemcpyDeviceToHost));
+  float* dst[6] = {nullptr, b1, W2, b2, W3, b3};
+  for (int k = 1; k < 6; ++k)
+    DL_CHECK(cudaMemcpy(dst[k], src[k], P->wlen[k] * 4, cudaMemcpyDeviceToHost));
+  return DL_OK;
+}
+
+extern "C" int dl_proposer_train(dl_proposer* P, const float* Y, int64_t m, const int32_t* sup, int s,
+                                 const int64_t* perm, int64_t batch, float lr, double* mean_loss) {
+  if (!P || !Y || !sup || m < 1 || s < 1 || s > kPropMaxS || batch < 64 || batch > P->bmax ||
+      batch % 64 || ptr_kind(Y) != 1 || ptr_kind(sup) != 1 || (perm && ptr_kind(perm) != 1))
+    return DL_EINVAL;
+  DevGuard g(P->dev);
+  DL_CHECK(cudaMemsetAsync(P->loss, 0, sizeof(double), P->st));
+  int64_t steps = 0;
+  for (int64_t r0 = 0; r0 + batch <= m; r0 += batch, ++steps) {
+    const int64_t tot = batch * P->pk;
+    gather_rows_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, P->st>>>(
+        perm ? Y : Y + r0 * P->p, P->p, P->pk, perm ? perm + r0 : nullptr, batch, perm ? sup : sup + r0 * s,
+        s, (__nv_bfloat16*)P->X, P->sup);
+    DL_CHECK(cudaGetLastError());
+    DL_CHECK(enq_train_step(P, batch, lr));
+  }
+  if (steps == 0) return DL_EINVAL;
+  if (mean_loss) {
+    double h = 0.0;
+    DL_CHECK(cudaMemcpyAsync(&h, P->loss, sizeof(double), cudaMemcpyDeviceToHost, P->st));
+    DL_CHECK(cudaStreamSynchronize(P->st));
+    *mean_loss = h / (double)steps;
+  }
+  int herr = 0;
+  DL_CHECK(cudaMemcpy(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost));
+  return herr ? DL_ETIMEOUT : DL_OK;
+}
+
+extern "C" int dl_proposer_forward(dl_proposer* P, const float* Y, int64_t m, float* logits,
+                                   int32_t* cand, int K) {
+  if (!P || !Y || m < 1 || ptr_kind(Y) != 1 || (!logits && !cand) || (cand && (K < 1 || K > 32)))
+    return DL_EINVAL;
+  DevGuard g(P->dev);
+  for (int64_t r0 = 0; r0 < m; r0 += P->bmax) {
+    const int64_t B = m - r0 < P->bmax ? m - r0 : P->bmax;
+    const int64_t tot = B * P->pk;
+    gather_rows_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, P->st>>>(
+        Y + r0 * P->p, P->p, P->pk, nullptr, B, nullptr, 0, (__nv_bfloat16*)P->X, nullptr);
+    DL_CHECK(cudaGetLastError());
+    if (logits) {
+      DL_CHECK(enq_forward_chunk(P, P->X, B, true));
+      DL_CHECK(cudaMemcpyAsync(logits + r0 * P->n, P->Z, sizeof(float) * B * P->n,
+                               cudaMemcpyDeviceToDevice, P->st));
+    }
+    if (cand) {
+      DL_CHECK(enq_forward_chunk(P, P->X, B, false));
+      DL_CHECK(dlk::mlp_topk(P->Zb, B, P->n, K, cand + r0 * K, P->st));
+    }
+  }
+  DL_CHECK(cudaStreamSynchronize(P->st));
+  return DL_OK;
+}
+
+extern "C" int dl_attach_proposer(dl_ctx* c, dl_proposer* P, int K, int full_every, double tol) {
+  if (!c) return DL_EINVAL;
+  DevGuard g(c->dev);
+  if (!P) {
+    c->prop = nullptr;
+    return DL_OK;
+  }
+  if (P->p != c->p || P->n != c->n || K < c->s_max || K > 32 || full_every < 1 || tol < 0 ||
+      !dlk::omp_restricted_supported(c->n, c->s_max, K))
+    return DL_EINVAL;
+  const size_t mm = (size_t)c->m_max;
+  if (!c->rr_ref) {
+    if (!dalloc(&c->rr_ref, mm) || !dalloc(&c->rr_L, mm) || !dalloc(&c->fb_list, mm) ||
+        !dalloc(&c->fb_count, 1) || !dalloc((uint8_t**)&c->Ybf, mm * P->pk * 2))
+      return DL_ENOMEM;
+    DL_CHECK(cudaMemset(c->fb_count, 0, sizeof(int)));
+  }
+  if (c->cand) cudaFree(c->cand);
+  c->cand = nullptr;
+  if (!dalloc(&c->cand, mm * K)) return DL_ENOMEM;
+  c->prop = P;
+  c->prop_K = K;
+  c->prop_full_every = full_every;
+  c->prop_tol2 = (float)((1.0 + tol) * (1.0 + tol));
+  c->prop_counter = 0;
+  if (c->gexec_learned) cudaGraphExecDestroy(c->gexec_learned);
+  c->gexec_learned = nullptr;
+  c->gkey_seen_l = 0;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->gkey_seen = 0;
+  return DL_OK;
+}
+
+extern "C" int64_t dl_last_fallbacks(dl_ctx* c) {
+  if (!c || !c->fb_count) return c ? 0 : DL_EINVAL;
+  DevGuard g(c->dev);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, c->fb_count, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess)
+    return DL_ECUDA;
+  return h;
 }

@@ -48,7 +48,35 @@ cudaError_t corr_lp(int kind, const void* A, int64_t rows_a, const float* a_inv_
 cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                       int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
                       int* rs_list, int* rs_count, int rs_cap, int warps_per_block,
-                      cudaStream_t st);
+                      float* ores, cudaStream_t st);
+
+// OMP restricted to K ascending candidates per signal (the learned proposer's
+// path) and the full-OMP fallback of listed signals.  ores: residual-energy
+// estimate per signal; ref_res/tol2: fallback when ores > tol2 * ref_res.
+bool omp_restricted_supported(int n, int s, int K);
+cudaError_t omp_restricted(const int32_t* cand, int K, const float* D, const float* G, int n,
+                           const float* Y, int p, int64_t m, int s, int32_t* idx, float* val,
+                           int32_t* cnt, float* ores, const float* ref_res, float tol2, int* fb_list,
+                           int* fb_count, int* err, cudaStream_t st);
+cudaError_t omp_listed(const int* list, const int* count, const float* D, const float* G, int n,
+                       const float* Y, int p, int s, int32_t* idx, float* val, int32_t* cnt,
+                       float* ores, int* err, int* rl, int* rc, int rcap, cudaStream_t st);
+
+// ---- learned proposer (k_mlp.cu) ----------------------------------------------
+enum : int { MLP_EPI_BF16 = 0, MLP_EPI_F32 = 1, MLP_EPI_GELU_FWD = 2, MLP_EPI_GELU_BWD = 3 };
+bool mlp_gemm_supported();
+// C[M x N] = A[M x K] B[N x K]^T, BF16 row-major operands (K % 64 == 0), epilogue op.
+cudaError_t mlp_gemm(const void* A, int64_t M, const void* B, int N, int K, int op, const float* bias,
+                     const float* aux, int64_t ldaux, float* out_f32, void* out_bf16, int64_t ldc,
+                     int* err, cudaStream_t st);
+cudaError_t mlp_transpose(const void* in, int64_t R, int64_t C, void* out, cudaStream_t st);
+cudaError_t mlp_to_bf16(const float* in, int64_t count, void* out, cudaStream_t st);
+cudaError_t mlp_bce_grad(const float* z, int64_t B, int n, const int32_t* sup, int s, void* dz,
+                         double* loss, cudaStream_t st);
+cudaError_t mlp_colsum(const void* in, int64_t R, int C, float* out, cudaStream_t st);
+cudaError_t mlp_adam(float* w, const float* g, float* m, float* v, int64_t count, float lr, int t,
+                     void* wbf, cudaStream_t st);
+cudaError_t mlp_topk(const void* z, int64_t m, int n, int K, int32_t* cand, cudaStream_t st);
 
 // FP64 re-solve (k_resolve.cu): full FP64 OMP of the listed signals, overwriting their slots.
 constexpr int DL_RESOLVE_SMAX = 16;

@@ -1,0 +1,383 @@
+// The learned support proposer: a BF16 MLP p -> 512 -> 512 -> n (GELU, sigmoid
+// outputs) trained with binary cross-entropy on multi-hot OMP supports, and its
+// inference (top-2s candidates per signal).  All products run on one tcgen05
+// GEMM kernel, C = A B^T with BF16 operands stored row-major with K contiguous,
+// FP32 accumulation in TMEM and fused epilogues (bias, GELU, GELU derivative,
+// BF16 or FP32 output).  Backward products that contract over the batch use
+// explicitly transposed BF16 copies, so every operand stays K-major.
+#include "dl_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace dlk {
+namespace {
+
+using namespace tc;
+
+constexpr int GM_THREADS = 128;
+constexpr int GM_TILE_M = 128;
+constexpr int GM_BLOCK_N = 256;
+constexpr int GM_BK = 64;  // BF16 elements per 128-byte chunk
+constexpr int GM_STAGES = 2;
+constexpr size_t GM_A_BYTES = (size_t)GM_TILE_M * 128;   // 16 KB
+constexpr size_t GM_B_BYTES = (size_t)GM_BLOCK_N * 128;  // 32 KB
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) |
+                                ((uint32_t)(GM_BLOCK_N >> 3) << 17) | ((uint32_t)(GM_TILE_M >> 4) << 24);
+
+__device__ __forceinline__ float gelu_f(float a) { return 0.5f * a * (1.f + erff(a * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float a) {
+  return 0.5f * (1.f + erff(a * 0.70710678118654752f)) +
+         a * 0.39894228040143268f * expf(-0.5f * a * a);
+}
+
+struct Epi {
+  int op;                  // MLP_EPI_*
+  const float* bias;       // [N] or null
+  const float* aux;        // GELU_BWD: pre-activation [M x ldaux] (FP32)
+  int64_t ldaux;
+  float* out_f32;          // F32 output (and pre-activation for GELU_FWD), ld = ldc
+  __nv_bfloat16* out_bf16; // BF16 output, ld = ldc
+  int64_t ldc;
+};
+
+// C[M x N] = A[M x K] B[N x K]^T ; one CTA per (128-row tile, 256-column block).
+__global__ void __launch_bounds__(GM_THREADS, 1)
+    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     int64_t M, int N, int K, Epi epi, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* As = base;
+  uint8_t* Bs = base + GM_STAGES * GM_A_BYTES;
+  uint64_t* full = (uint64_t*)(Bs + GM_STAGES * GM_B_BYTES);
+  uint64_t* empty = full + GM_STAGES;
+  uint64_t* done = empty + GM_STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * GM_TILE_M;
+  const int n0 = blockIdx.y * GM_BLOCK_N;
+  const int nk = K / GM_BK;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int q = 0; q < GM_STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(256u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    for (int q = 0; q < GM_STAGES && q < nk; ++q) {
+      mbar_expect_tx(&full[q], (uint32_t)(GM_A_BYTES + GM_B_BYTES));
+      tma_load_2d(As + q * GM_A_BYTES, &tmA, &full[q], q * GM_BK, (int)m0);
+      tma_load_2d(Bs + q * GM_B_BYTES, &tmB, &full[q], q * GM_BK, n0);
+    }
+    for (int kc = 0; kc < nk && ok; ++kc) {
+      const int st = kc % GM_STAGES;
+      const uint32_t ph = (uint32_t)((kc / GM_STAGES) & 1);
+      if (!(ok = mbar_wait(&full[st], ph))) break;
+      tc_fence_after();
+      const uint64_t ad = sw128_desc(As + st * GM_A_BYTES);
+      const uint64_t bd = sw128_desc(Bs + st * GM_B_BYTES);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        mma_f16(tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), kIdescBf16,
+                (kc > 0 || k > 0) ? 1u : 0u);
+      mma_commit(&empty[st]);
+      if (kc + GM_STAGES < nk) {
+        if (!(ok = mbar_wait(&empty[st], ph))) break;
+        const int kn = kc + GM_STAGES;
+        mbar_expect_tx(&full[st], (uint32_t)(GM_A_BYTES + GM_B_BYTES));
+        tma_load_2d(As + st * GM_A_BYTES, &tmA, &full[st], kn * GM_BK, (int)m0);
+        tma_load_2d(Bs + st * GM_B_BYTES, &tmB, &full[st], kn * GM_BK, n0);
+      }
+    }
+    if (ok) {
+      mma_commit(done);
+      ok = mbar_wait(done, 0);
+    }
+    if (!ok) s_fail = 1;
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (!s_fail) {
+    const int64_t row = m0 + warp * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const int ncols = N - n0 < GM_BLOCK_N ? N - n0 : GM_BLOCK_N;
+    for (int c0 = 0; c0 < ncols; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
+      if (row >= M) continue;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int col = n0 + c0 + q;
+        if (col >= N) break;
+        float a = __uint_as_float(r[q]);
+        if (epi.bias) a += epi.bias[col];
+        float o = a;
+        if (epi.op == MLP_EPI_GELU_FWD) {
+          if (epi.out_f32) epi.out_f32[row * epi.ldc + col] = a;
+          o = gelu_f(a);
+        } else if (epi.op == MLP_EPI_GELU_BWD) {
+          o = a * gelu_grad_f(epi.aux[row * epi.ldaux + col]);
+        } else if (epi.op == MLP_EPI_F32) {
+          epi.out_f32[row * epi.ldc + col] = a;
+          continue;
+        }
+        if (epi.out_bf16) epi.out_bf16[row * epi.ldc + col] = __float2bfloat16_rn(o);
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicOr(err, ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u)
+                 : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool map_bf16(CUtensorMap* map, const void* ptr, int64_t rows, int K, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  cuuint32_t box[2] = {(cuuint32_t)GM_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ptr, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// [R x C] BF16 -> [C x R] BF16 through 32 x 32 shared-memory tiles.
+__global__ void transpose_bf16_kernel(const __nv_bfloat16* __restrict__ in, int64_t R, int64_t C,
+                                      __nv_bfloat16* __restrict__ out) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + k, c = c0 + threadIdx.x;
+    if (r < R && c < C) tile[k][threadIdx.x] = in[r * C + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = c0 + k, r = r0 + threadIdx.x;
+    if (r < R && c < C) out[c * R + r] = tile[threadIdx.x][k];
+  }
+}
+
+__global__ void f32_to_bf16_kernel(const float* __restrict__ in, int64_t count,
+                                   __nv_bfloat16* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) out[e] = __float2bfloat16_rn(in[e]);
+}
+
+// dz = (sigmoid(z) - t) / B as BF16, t = 1 on the signal's support; the BCE
+// loss sum(softplus(z) - t z) / B is accumulated into *loss (double).
+__global__ void bce_grad_kernel(const float* __restrict__ z, int64_t B, int n,
+                                const int32_t* __restrict__ sup, int s, __nv_bfloat16* __restrict__ dz,
+                                double* __restrict__ loss) {
+  __shared__ double red[8];
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  if (e < B * n) {
+    const int64_t b = e / n;
+    const int j = (int)(e - b * n);
+    float t = 0.f;
+    for (int q = 0; q < s; ++q)
+      if (sup[b * s + q] == j) t = 1.f;
+    const float zz = z[e];
+    const float sg = 1.f / (1.f + expf(-zz));
+    dz[e] = __float2bfloat16_rn((sg - t) / (float)B);
+    const float sp = zz > 0.f ? zz + log1pf(expf(-zz)) : log1pf(expf(zz));
+    l = (double)(sp - t * zz) / (double)B;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(loss, t);
+  }
+}
+
+// out[c] = sum_r in[r][c]  (BF16 rows, FP32 sums), one thread per column.
+__global__ void colsum_bf16_kernel(const __nv_bfloat16* __restrict__ in, int64_t R, int C,
+                                   float* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  float acc = 0.f;
+  for (int64_t r = 0; r < R; ++r) acc += __bfloat162float(in[r * C + c]);
+  out[c] = acc;
+}
+
+// Adam (Kingma & Ba) on FP32 master weights; refreshes the BF16 copy.
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t count, float lr, float b1, float b2,
+                            float eps, float c1, float c2, __nv_bfloat16* __restrict__ wbf) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  const float gg = g[e];
+  const float mm = b1 * m[e] + (1.f - b1) * gg;
+  const float vv = b2 * v[e] + (1.f - b2) * gg * gg;
+  m[e] = mm;
+  v[e] = vv;
+  const float ww = w[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+  w[e] = ww;
+  if (wbf) wbf[e] = __float2bfloat16_rn(ww);
+}
+
+// Top-K of each row of n logits (one warp per row), indices ascending.
+template <int NT>
+__global__ void topk_kernel(const __nv_bfloat16* __restrict__ z, int64_t m, int n, int K,
+                            int32_t* __restrict__ cand) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= m) return;
+  float v[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int j = 32 * t + lane;
+    v[t] = j < n ? __bfloat162float(z[i * n + j]) : -INFINITY;
+  }
+  int mine = -1;  // lane k < K: the k-th pick
+  for (int k = 0; k < K; ++k) {
+    float bv = -INFINITY;
+    int bt = 0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+      if (v[t] > bv) {
+        bv = v[t];
+        bt = t;
+      }
+    int bj = 32 * bt + lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+      if (ov > bv || (ov == bv && oj < bj)) {
+        bv = ov;
+        bj = oj;
+      }
+    }
+    if (lane == k) mine = bj;
+    if ((bj & 31) == lane) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+        if (t == (bj >> 5)) v[t] = -INFINITY;
+    }
+  }
+  // ascending order of the K picks
+  int rank = 0;
+  for (int q = 0; q < K; ++q) {
+    const int o = __shfl_sync(0xffffffffu, mine, q);
+    if (lane < K && o < mine) ++rank;
+  }
+  if (lane < K) cand[i * K + rank] = mine;
+}
+
+}  // namespace
+
+bool mlp_gemm_supported() { return encode_fn() != nullptr; }
+
+cudaError_t mlp_gemm(const void* A, int64_t M, const void* B, int N, int K, int op, const float* bias,
+                     const float* aux, int64_t ldaux, float* out_f32, void* out_bf16, int64_t ldc,
+                     int* err, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K % GM_BK != 0) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!map_bf16(&ma, A, M, K, GM_TILE_M) || !map_bf16(&mb, B, N, K, GM_BLOCK_N))
+    return cudaErrorInvalidValue;
+  const size_t smem = 1024 + GM_STAGES * (GM_A_BYTES + GM_B_BYTES) + 128;
+  cudaError_t e =
+      cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  Epi epi{op, bias, aux, ldaux, out_f32, (__nv_bfloat16*)out_bf16, ldc};
+  dim3 grid((unsigned)((M + GM_TILE_M - 1) / GM_TILE_M), (unsigned)((N + GM_BLOCK_N - 1) / GM_BLOCK_N));
+  gemm_bf16_kernel<<<grid, GM_THREADS, smem, st>>>(ma, mb, M, N, K, epi, err);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_transpose(const void* in, int64_t R, int64_t C, void* out, cudaStream_t st) {
+  if (R <= 0 || C <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((C + 31) / 32), (unsigned)((R + 31) / 32));
+  transpose_bf16_kernel<<<grid, dim3(32, 8), 0, st>>>((const __nv_bfloat16*)in, R, C,
+                                                       (__nv_bfloat16*)out);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_to_bf16(const float* in, int64_t count, void* out, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  f32_to_bf16_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(in, count, (__nv_bfloat16*)out);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_bce_grad(const float* z, int64_t B, int n, const int32_t* sup, int s, void* dz,
+                         double* loss, cudaStream_t st) {
+  const int64_t tot = B * n;
+  if (tot <= 0) return cudaSuccess;
+  bce_grad_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(z, B, n, sup, s,
+                                                                 (__nv_bfloat16*)dz, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_colsum(const void* in, int64_t R, int C, float* out, cudaStream_t st) {
+  colsum_bf16_kernel<<<(C + 127) / 128, 128, 0, st>>>((const __nv_bfloat16*)in, R, C, out);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_adam(float* w, const float* g, float* m, float* v, int64_t count, float lr, int t,
+                     void* wbf, cudaStream_t st) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+  adam_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(w, g, m, v, count, lr, b1, b2, 1e-8f,
+                                                               c1, c2, (__nv_bfloat16*)wbf);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_topk(const void* z, int64_t m, int n, int K, int32_t* cand, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((m + 7) / 8);
+  const __nv_bfloat16* zz = (const __nv_bfloat16*)z;
+  if (n <= 128) topk_kernel<4><<<blocks, 256, 0, st>>>(zz, m, n, K, cand);
+  else if (n <= 256) topk_kernel<8><<<blocks, 256, 0, st>>>(zz, m, n, K, cand);
+  else if (n <= 512) topk_kernel<16><<<blocks, 256, 0, st>>>(zz, m, n, K, cand);
+  else topk_kernel<32><<<blocks, 256, 0, st>>>(zz, m, n, K, cand);
+  return cudaGetLastError();
+}
+
+}  // namespace dlk

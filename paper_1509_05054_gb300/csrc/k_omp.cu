@@ -100,11 +100,58 @@ struct Take {
   }
 };
 
-template <int NT, int SMAX, bool SMEM_U, bool FULLN>
-__global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
-    const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
-    const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
-    float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err,
+// Gram rows from global memory (L2): pair v of lane l = (G[sel][64v+l], G[sel][64v+32+l]).
+template <bool FULLN>
+struct GramGlobal {
+  const float* __restrict__ G;
+  int n;
+  template <int NV>
+  __device__ __forceinline__ void row(int sel, int lane, float2 (&out)[NV]) const {
+    const float* __restrict__ Gr = G + (size_t)sel * n;  // row sel == column sel (G symmetric)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int j0 = 64 * v + lane, j1 = j0 + 32;
+      out[v].x = (FULLN || j0 < n) ? __ldg(Gr + j0) : 0.f;
+      out[v].y = (FULLN || j1 < n) ? __ldg(Gr + j1) : 0.f;
+    }
+  }
+  __device__ __forceinline__ float diag(int sel) const { return __ldg(G + (size_t)sel * n + sel); }
+};
+
+// Gram entries among K candidate atoms cand[0..K) (ascending) of one signal:
+// element j of "row" sel is G[cand[j]][cand[sel]]; lane l holds candidate l.
+struct GramRestricted {
+  const float* __restrict__ G;
+  int n;
+  const int32_t* __restrict__ cand;
+  int K;
+  template <int NV>
+  __device__ __forceinline__ void row(int sel, int lane, float2 (&out)[NV]) const {
+    const int as = cand[sel];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int j0 = 64 * v + lane, j1 = j0 + 32;
+      out[v].x = j0 < K ? __ldg(G + (size_t)cand[j0] * n + as) : 0.f;
+      out[v].y = j1 < K ? __ldg(G + (size_t)cand[j1] * n + as) : 0.f;
+    }
+  }
+  __device__ __forceinline__ float diag(int sel) const {
+    const int as = cand[sel];
+    return __ldg(G + (size_t)as * n + as);
+  }
+};
+
+// One signal, one warp: the whole OMP of signal i (see the file header).
+// a0row: its correlations (element j, j < n); y: the signal; L, C: this warp's
+// shared-memory Cholesky rows and 1/L_qq; u_s: its shared u vectors (SMEM_U).
+// Outputs slots i*s.. (atom index = idxmap[j] when idxmap is given), the count,
+// and the residual-energy estimate ||y||^2 - sum z^2 in ores[i] when given.
+template <int NT, int SMAX, bool SMEM_U, bool FULLN, class GSrc>
+__device__ __forceinline__ void omp_one(
+    int64_t i, const GSrc& gsrc, float (&L)[SMAX][SMAX], float (&C)[SMAX], float2* u_s,
+    const float* __restrict__ a0row, int n, const float* __restrict__ y, int p, int s,
+    const int32_t* __restrict__ idxmap, int32_t* __restrict__ oidx, float* __restrict__ oval,
+    int32_t* __restrict__ ocnt, float* __restrict__ ores, int* __restrict__ err,
     int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap) {
   static_assert(NT >= 2 && NT % 2 == 0, "alpha is held in float2 pairs");
   constexpr int NV = NT / 2;
@@ -113,24 +160,14 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
   constexpr unsigned TMASK = (1u << TB) - 1u;
   constexpr unsigned VMASK = 0x7FFFFFFFu & ~TMASK;
 
-  extern __shared__ float2 smem_u[];
-  __shared__ float Lsh[OMP_THREADS / 32][SMAX][SMAX];  // per warp: L[j][q] (q < j)
-  __shared__ float Csh[OMP_THREADS / 32][SMAX];        // per warp: c_q = 1/L_qq
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-  if (i >= m) return;
-  float(&L)[SMAX][SMAX] = Lsh[wib];
-  float(&C)[SMAX] = Csh[wib];
-
   float2 u_r[SMEM_U ? 1 : NPHI][SMEM_U ? 1 : NV];
-  float2* u_s = SMEM_U ? smem_u + (size_t)wib * NPHI * NV * 32 : nullptr;
 #define UV(q, v) (*(SMEM_U ? &u_s[((q) * NV + (v)) * 32 + lane] : &u_r[SMEM_U ? 0 : (q)][SMEM_U ? 0 : (v)]))
 
   // ||y||^2 for the residual stop rule and the non-finite check
   float yy = 0.f;
   for (int r = lane; r < p; r += 32) {
-    const float v = Y[i * p + r];
+    const float v = y[r];
     yy = fmaf(v, v, yy);
   }
   yy = warp_sum(yy);
@@ -142,8 +179,8 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const int j0 = 64 * v + lane, j1 = j0 + 32;
-    alpha[v].x = (FULLN || j0 < n) ? A0[i * lda + j0] : qnan;
-    alpha[v].y = (FULLN || j1 < n) ? A0[i * lda + j1] : qnan;
+    alpha[v].x = (FULLN || j0 < n) ? a0row[j0] : qnan;
+    alpha[v].y = (FULLN || j1 < n) ? a0row[j1] : qnan;
   }
 
   float negaw[SMAX];  // -(w_q c_q), broadcast to all lanes
@@ -166,21 +203,15 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     const int lsel = __ffs(ball) - 1;
     const int tsel = NT - 1 - (int)(kbits & TMASK);
     const int sel = 32 * tsel + lsel;
-    const float* __restrict__ Gr = G + (size_t)sel * n;  // row sel == column sel (G symmetric)
-
     // issue the Gram row loads early (needed unless this is the last step)
     const bool need_u = (step + 1 < s) && (step + 1 < SMAX);
     if (need_u) {
+      float2 grow[NV];
+      gsrc.template row<NV>(sel, lane, grow);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const int j0 = 64 * v + lane, j1 = j0 + 32;
-        float2 g;
-        g.x = (FULLN || j0 < n) ? __ldg(Gr + j0) : 0.f;
-        g.y = (FULLN || j1 < n) ? __ldg(Gr + j1) : 0.f;
-        UV(step < NPHI ? step : 0, v) = g;
-      }
+      for (int v = 0; v < NV; ++v) UV(step < NPHI ? step : 0, v) = grow[v];
     }
-    const float gss = __ldg(Gr + sel);
+    const float gss = gsrc.diag(sel);
 
     // alpha[sel] (exact, signed), its masking, and u_q[sel] on the owning lane
     float amine = 0.f;
@@ -272,19 +303,112 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
   }
   const int64_t base = i * s;
   if (lane < k) {
-    oidx[base + rank] = myI;
+    oidx[base + rank] = idxmap ? idxmap[myI] : myI;
     oval[base + rank] = gam;
   } else if (lane < s) {
     oidx[base + lane] = -1;
     oval[base + lane] = 0.f;
   }
-  if (lane == 0) ocnt[i] = k;
+  if (lane == 0) {
+    ocnt[i] = k;
+    if (ores) ores[i] = rr;
+  }
+}
+
+template <int NT, int SMAX, bool SMEM_U, bool FULLN>
+__global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
+    const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
+    const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
+    float* __restrict__ oval, int32_t* __restrict__ ocnt, float* __restrict__ ores,
+    int* __restrict__ err, int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap) {
+  constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
+  extern __shared__ float2 smem_u[];
+  __shared__ float Lsh[OMP_THREADS / 32][SMAX][SMAX];  // per warp: L[j][q] (q < j)
+  __shared__ float Csh[OMP_THREADS / 32][SMAX];        // per warp: c_q = 1/L_qq
+  const int wib = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (i >= m) return;
+  float2* u_s = SMEM_U ? smem_u + (size_t)wib * NPHI * (NT / 2) * 32 : nullptr;
+  const GramGlobal<FULLN> gsrc{G, n};
+  omp_one<NT, SMAX, SMEM_U, FULLN>(i, gsrc, Lsh[wib], Csh[wib], u_s, A0 + i * lda, n, Y + i * p, p,
+                                   s, nullptr, oidx, oval, ocnt, ores, err, rs_list, rs_count,
+                                   rs_cap);
+}
+
+// OMP restricted to K proposed candidates per signal (cand: m x K, ascending):
+// the correlations d_c^T y of the candidates are computed here, the Gram
+// entries come from the full Gram matrix.  Writes the slots (atom indices) and
+// the residual estimate; a signal whose residual energy exceeds `tol2` times its
+// reference residual energy (ref_res from the last full pass) is appended to
+// fb_list for full OMP.
+template <int SMAX>
+__global__ void __launch_bounds__(OMP_THREADS) omp_restricted_kernel(
+    const int32_t* __restrict__ cand, int K, const float* __restrict__ D, const float* __restrict__ G,
+    int n, const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
+    float* __restrict__ oval, int32_t* __restrict__ ocnt, float* __restrict__ ores,
+    const float* __restrict__ ref_res, float tol2, int* __restrict__ fb_list, int* __restrict__ fb_count,
+    int* __restrict__ err) {
+  __shared__ float Lsh[OMP_THREADS / 32][SMAX][SMAX];
+  __shared__ float Csh[OMP_THREADS / 32][SMAX];
+  __shared__ float a0sh[OMP_THREADS / 32][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (i >= m) return;
+  const int32_t* ci = cand + i * K;
+  const float* y = Y + i * p;
+  float a = 0.f;
+  if (lane < K) {
+    const float* dc = D + (size_t)ci[lane] * p;
+    for (int r = 0; r < p; ++r) a = fmaf(dc[r], y[r], a);
+  }
+  a0sh[wib][lane] = a;
+  __syncwarp();
+  const GramRestricted gsrc{G, n, ci, K};
+  omp_one<2, SMAX, false, false>(i, gsrc, Lsh[wib], Csh[wib], nullptr, a0sh[wib], K, y, p, s, ci,
+                                 oidx, oval, ocnt, ores, err, nullptr, nullptr, 0);
+  __syncwarp();
+  if (lane == 0 && fb_count && ores[i] > tol2 * ref_res[i]) {
+    const int pos = atomicAdd(fb_count, 1);
+    if (pos < (int)m) fb_list[pos] = (int)i;
+  }
+}
+
+// Full OMP of the listed signals (the proposer's fallback): one warp computes the
+// signal's correlations D^T y into shared memory, then runs the OMP.
+template <int NT, int SMAX>
+__global__ void __launch_bounds__(OMP_THREADS) omp_listed_kernel(
+    const int* __restrict__ list, const int* __restrict__ count, const float* __restrict__ D,
+    const float* __restrict__ G, int n, const float* __restrict__ Y, int p, int s,
+    int32_t* __restrict__ oidx, float* __restrict__ oval, int32_t* __restrict__ ocnt,
+    float* __restrict__ ores, int* __restrict__ err, int* __restrict__ rs_list,
+    int* __restrict__ rs_count, int rs_cap) {
+  __shared__ float Lsh[OMP_THREADS / 32][SMAX][SMAX];
+  __shared__ float Csh[OMP_THREADS / 32][SMAX];
+  __shared__ float a0sh[OMP_THREADS / 32][32 * NT];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int total = *count;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int e = blockIdx.x * (blockDim.x >> 5) + wib; e < total; e += nw) {
+    const int64_t i = list[e];
+    const float* y = Y + i * p;
+    for (int j = lane; j < n; j += 32) {
+      const float* dj = D + (size_t)j * p;
+      float a = 0.f;
+      for (int r = 0; r < p; ++r) a = fmaf(dj[r], y[r], a);
+      a0sh[wib][j] = a;
+    }
+    __syncwarp();
+    const GramGlobal<false> gsrc{G, n};
+    omp_one<NT, SMAX, false, false>(i, gsrc, Lsh[wib], Csh[wib], nullptr, a0sh[wib], n, y, p, s,
+                                    nullptr, oidx, oval, ocnt, ores, err, rs_list, rs_count, rs_cap);
+    __syncwarp();
+  }
 }
 
 template <int NT, int SMAX, bool SMEM, bool FULLN>
 cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                      int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                     int* rs_list, int* rs_count, int rs_cap, int warps_hint, cudaStream_t st) {
+                     int* rs_list, int* rs_count, int rs_cap, int warps_hint, float* ores, cudaStream_t st) {
   int warps = (warps_hint >= 1 && warps_hint <= OMP_THREADS / 32) ? warps_hint : OMP_THREADS / 32;
   size_t smem = 0;
   if (SMEM) {
@@ -301,7 +425,7 @@ cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const 
   }
   const int64_t blocks = (m + warps - 1) / warps;
   omp_warp_kernel<NT, SMAX, SMEM, FULLN><<<(unsigned)blocks, warps * 32, smem, st>>>(
-      A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rs_list, rs_count, rs_cap);
+      A0, lda, G, n, Y, p, m, s, idx, val, cnt, ores, err, rs_list, rs_count, rs_cap);
   return cudaGetLastError();
 }
 
@@ -314,37 +438,85 @@ constexpr bool fits_regs() {
 template <int NT, int SMAX>
 cudaError_t pick_store(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                        int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                       int* rl, int* rc, int rcap, int wh, cudaStream_t st) {
+                       int* rl, int* rc, int rcap, int wh, float* ores, cudaStream_t st) {
   constexpr bool SM = !fits_regs<NT, SMAX>();
   if (n == 32 * NT)
-    return launch_t<NT, SMAX, SM, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
-  return launch_t<NT, SMAX, SM, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
+    return launch_t<NT, SMAX, SM, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+  return launch_t<NT, SMAX, SM, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
 }
 
 template <int NT>
 cudaError_t pick_s(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                    int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                   int* rl, int* rc, int rcap, int wh, cudaStream_t st) {
-  if (s <= 4) return pick_store<NT, 4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
-  if (s <= 8) return pick_store<NT, 8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
-  if (s <= 12) return pick_store<NT, 12>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
-  return pick_store<NT, 16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
+                   int* rl, int* rc, int rcap, int wh, float* ores, cudaStream_t st) {
+  if (s <= 4) return pick_store<NT, 4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+  if (s <= 8) return pick_store<NT, 8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+  if (s <= 12) return pick_store<NT, 12>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+  return pick_store<NT, 16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
 }
 
 }  // namespace
 
 bool omp_supported(int n, int s) { return n >= 1 && n <= 1024 && s >= 1 && s <= 16; }
 
+bool omp_restricted_supported(int n, int s, int K) {
+  const int nt = (n + 31) / 32;
+  const int sm = s <= 4 ? 4 : s <= 8 ? 8 : 0;
+  return K >= 1 && K <= 32 && s <= K && sm > 0 && (nt <= 2 ? 2 : nt <= 4 ? 4 : nt <= 8 ? 8 : 16) * (sm - 1) <= 128 &&
+         n <= 512;
+}
+
+cudaError_t omp_restricted(const int32_t* cand, int K, const float* D, const float* G, int n,
+                           const float* Y, int p, int64_t m, int s, int32_t* idx, float* val,
+                           int32_t* cnt, float* ores, const float* ref_res, float tol2, int* fb_list,
+                           int* fb_count, int* err, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((m + 3) / 4);
+  if (s <= 4)
+    omp_restricted_kernel<4><<<blocks, OMP_THREADS, 0, st>>>(cand, K, D, G, n, Y, p, m, s, idx, val,
+                                                             cnt, ores, ref_res, tol2, fb_list,
+                                                             fb_count, err);
+  else
+    omp_restricted_kernel<8><<<blocks, OMP_THREADS, 0, st>>>(cand, K, D, G, n, Y, p, m, s, idx, val,
+                                                             cnt, ores, ref_res, tol2, fb_list,
+                                                             fb_count, err);
+  return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t listed_s(const int* list, const int* count, const float* D, const float* G, int n,
+                     const float* Y, int p, int s, int32_t* idx, float* val, int32_t* cnt, float* ores,
+                     int* err, int* rl, int* rc, int rcap, cudaStream_t st) {
+  const unsigned blocks = (unsigned)(num_sms() * 3);
+  if (s <= 4)
+    omp_listed_kernel<NT, 4><<<blocks, OMP_THREADS, 0, st>>>(list, count, D, G, n, Y, p, s, idx, val,
+                                                             cnt, ores, err, rl, rc, rcap);
+  else
+    omp_listed_kernel<NT, 8><<<blocks, OMP_THREADS, 0, st>>>(list, count, D, G, n, Y, p, s, idx, val,
+                                                             cnt, ores, err, rl, rc, rcap);
+  return cudaGetLastError();
+}
+
+cudaError_t omp_listed(const int* list, const int* count, const float* D, const float* G, int n,
+                       const float* Y, int p, int s, int32_t* idx, float* val, int32_t* cnt,
+                       float* ores, int* err, int* rl, int* rc, int rcap, cudaStream_t st) {
+  const int nt = (n + 31) / 32;
+  if (nt <= 2) return listed_s<2>(list, count, D, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
+  if (nt <= 4) return listed_s<4>(list, count, D, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
+  if (nt <= 8) return listed_s<8>(list, count, D, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
+  return listed_s<16>(list, count, D, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
+}
+
 cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                       int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                      int* rl, int* rc, int rcap, int wh, cudaStream_t st) {
+                      int* rl, int* rc, int rcap, int wh, float* ores, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   const int nt = (n + 31) / 32;
-  if (nt <= 2) return pick_s<2>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
-  if (nt <= 4) return pick_s<4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
-  if (nt <= 8) return pick_s<8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
-  if (nt <= 16) return pick_s<16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
-  return pick_s<32>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, st);
+  if (nt <= 2) return pick_s<2>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+  if (nt <= 4) return pick_s<4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+  if (nt <= 8) return pick_s<8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+  if (nt <= 16) return pick_s<16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+  return pick_s<32>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
 }
 
 }  // namespace dlk

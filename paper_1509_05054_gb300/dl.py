@@ -80,8 +80,19 @@ def load(build_if_missing: bool = True):
         lib.dl_batch_kernel_launches.argtypes = [P]
         lib.dl_batch_kernel_launches.restype = i64
         lib.dl_batch_config.argtypes = [P, i32, P]
+        lib.dl_proposer_create.argtypes = [ctypes.POINTER(P), i32, i32, i32, i64, P]
+        lib.dl_proposer_destroy.argtypes = [P]
+        lib.dl_proposer_set_weights.argtypes = [P] + [P] * 6
+        lib.dl_proposer_get.argtypes = [P, i32] + [P] * 6
+        lib.dl_proposer_train.argtypes = [P, P, i64, P, i32, P, i64, ctypes.c_float, P]
+        lib.dl_proposer_forward.argtypes = [P, P, i64, P, P, i32]
+        lib.dl_attach_proposer.argtypes = [P, P, i32, i32, ctypes.c_double]
+        lib.dl_last_fallbacks.argtypes = [P]
+        lib.dl_last_fallbacks.restype = i64
         for name in ("dl_autotune", "dl_get_config", "dl_batch_create", "dl_batch_iterate",
-                     "dl_batch_destroy", "dl_batch_config"):
+                     "dl_batch_destroy", "dl_batch_config", "dl_proposer_create",
+                     "dl_proposer_destroy", "dl_proposer_set_weights", "dl_proposer_get",
+                     "dl_proposer_train", "dl_proposer_forward", "dl_attach_proposer"):
             getattr(lib, name).restype = i32
         for name in ("dl_init", "dl_set_stream", "dl_destroy", "omp_code", "jau_update", "dl_iterate",
                      "dl_sync", "dl_set_profiling", "dl_phase_times", "dl_gram", "dl_correlate",
@@ -247,6 +258,54 @@ def dl_batch_config(batch: int, k: int) -> dict:
     out = np.zeros(4, np.int32)
     _check(load().dl_batch_config(batch, k, out.ctypes.data), "dl_batch_config")
     return dict(zip(("corr_tensor_cores", "omp_warps", "accum_mult", "rows_per_sm"), out.tolist()))
+
+
+def dl_proposer_create(p: int, n: int, hidden: int = 512, batch: int = 4096, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dl_proposer_create(ctypes.byref(h), p, n, hidden, batch, _stream_ptr(stream)),
+           "dl_proposer_create")
+    return h.value
+
+
+def dl_proposer_destroy(prop: int) -> None:
+    load().dl_proposer_destroy(prop)
+
+
+def dl_proposer_set_weights(prop: int, params) -> None:
+    """params: [W1 (h,p), b1, W2 (h,h), b2, W3 (n,h), b3] numpy arrays."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(a, np.float32) for a in params]
+    _check(load().dl_proposer_set_weights(prop, *[a.ctypes.data for a in arrs]),
+           "dl_proposer_set_weights")
+
+
+def dl_proposer_get(prop: int, which: int, shapes):
+    import numpy as np
+    outs = [np.zeros(sh, np.float32) for sh in shapes]
+    _check(load().dl_proposer_get(prop, which, *[a.ctypes.data for a in outs]), "dl_proposer_get")
+    return outs
+
+
+def dl_proposer_train(prop: int, Y, m: int, sup, s: int, perm=None, batch: int = 4096,
+                      lr: float = 1e-3) -> float:
+    import numpy as np
+    loss = np.zeros(1)
+    _check(load().dl_proposer_train(prop, _ptr(Y), m, _ptr(sup), s, _ptr(perm), batch, lr,
+                                    loss.ctypes.data), "dl_proposer_train")
+    return float(loss[0])
+
+
+def dl_proposer_forward(prop: int, Y, m: int, logits=None, cand=None, K: int = 16) -> None:
+    _check(load().dl_proposer_forward(prop, _ptr(Y), m, _ptr(logits), _ptr(cand), K),
+           "dl_proposer_forward")
+
+
+def dl_attach_proposer(ctx: int, prop, K: int = 16, full_every: int = 10, tol: float = 0.01) -> None:
+    _check(load().dl_attach_proposer(ctx, prop, K, full_every, tol), "dl_attach_proposer")
+
+
+def dl_last_fallbacks(ctx: int) -> int:
+    return int(load().dl_last_fallbacks(ctx))
 
 
 class Context:
