@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--forms", default="fp32,bf16,fp8",
                     help="precision forms to time; the reported value is the fastest form whose "
                          "final RMSE is within 1%% of the plain FP32 form")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-proposer measurement")
+    ap.add_argument("--learned-train", type=int, default=1_000_000,
+                    help="training patches for the proposer (5 epochs)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-problems measurement")
     ap.add_argument("--batched-iters", type=int, default=20)
@@ -360,6 +364,9 @@ def run_ours(args):
     batched = None
     if not args.no_batched:
         batched = run_batched(args, dl, torch, st)
+    learned = None
+    if not args.no_learned:
+        learned = run_learned(args, dl, torch, st)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -384,7 +391,7 @@ def run_ours(args):
                     "equal_rmse": f"final relative RMSE after {RMSE_ITERS} iterations within "
                                   f"{100 * EQUAL_RMSE:.0f}% of the plain FP32 form"}),
                 "roofline": roof, "phases_ms": phases, "phase_roofline": per_phase,
-                "forms": forms, "batched": batched,
+                "forms": forms, "batched": batched, "learned": learned,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if pg:
@@ -437,6 +444,86 @@ def run_batched(args, dl, torch, st):
             "shapes": [dict(p=q["p"], n=q["n"], m=q["m"], s=q["s"], cfg=c,
                             final_rmse=float(rm[k, -1, 1]))
                        for k, (q, c) in enumerate(zip(probs, cfgs))]}
+
+
+def run_learned(args, dl, torch, st):
+    """Learned support proposer at p=64, n=512, s=8, m=2e5: plain warm-up, OMP
+    labels of disjoint training patches, 5 epochs of training on the GPU, then 20
+    DL iterations with the proposer (full OMP every 10th) against 20 plain ones
+    from the same dictionary."""
+    Y, D, spec = synth.workload_inputs("patch_n512_m2e5")
+    m, p, n, s = spec["m"], spec["p"], spec["n"], spec["s"]
+    K, full_every, iters, warm = 2 * s, 10, 20, 10
+    mt = args.learned_train
+    t_setup = time.perf_counter()
+    Yd = torch.from_numpy(Y).cuda()
+    ctx = dl.dl_init(p, n, max(m, mt), s, dl.DL_FP32, st)
+    Dw = torch.from_numpy(D).cuda()
+    cp = torch.zeros(max(m, mt) + 1, dtype=torch.int64, device="cuda")
+    ri = torch.zeros(max(m, mt) * s, dtype=torch.int32, device="cuda")
+    v = torch.zeros(max(m, mt) * s, dtype=torch.float32, device="cuda")
+    dl.dl_iterate(ctx, Yd, m, Dw, s, warm, cp, ri, v, np.zeros(2 * warm))
+    Ytr = torch.from_numpy(synth.image_patches(mt, side=8, workload_id=41, first_image=2000)).cuda()
+    dl.omp_code(ctx, Ytr, mt, Dw, s, cp, ri, v)
+    dl.dl_sync(ctx)
+    # slots (mt x s, -1 padded) from the CSC labels
+    colptr = cp[: mt + 1]
+    cnt = colptr[1:] - colptr[:-1]
+    pos = torch.arange(s, device="cuda").unsqueeze(0)
+    gather = (colptr[:-1].unsqueeze(1) + pos).clamp(max=max(int(colptr[-1]) - 1, 0))
+    sup = torch.where(pos < cnt.unsqueeze(1), ri[gather], torch.full_like(gather, -1, dtype=torch.int32))
+    sup = sup.to(torch.int32).contiguous()
+    prop = dl.dl_proposer_create(p, n, 512, 4096, st)
+    dl.dl_proposer_set_weights(prop, synth.proposer_init(p, n, 512, seed=11, positives=s))
+    t0 = time.perf_counter()
+    losses = []
+    for ep in range(5):
+        perm = torch.randperm(mt, device="cuda")
+        losses.append(dl.dl_proposer_train(prop, Ytr, mt, sup, s, perm, 4096, 1e-3))
+    train_s = time.perf_counter() - t0
+    del Ytr, sup
+    dl.dl_destroy(ctx)
+
+    def run(with_prop):
+        c = dl.dl_init(p, n, m, s, dl.DL_FP32, st)
+        if with_prop:
+            dl.dl_attach_proposer(c, prop, K, full_every, 0.01)
+        Dd = Dw.clone()
+        dl.dl_iterate(c, Yd, m, Dd, s, 1, cp, ri, v, None)       # warm the graphs
+        if with_prop:
+            dl.dl_iterate(c, Yd, m, Dd, s, 1, cp, ri, v, None)
+            dl.dl_attach_proposer(c, prop, K, full_every, 0.01)   # restart the full/learned cycle
+        Dd.copy_(Dw)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(iters)]
+        fbs, rm = [], np.zeros(2)
+        for k in range(iters):
+            ev[k][0].record(st)
+            dl.dl_iterate(c, Yd, m, Dd, s, 1, cp, ri, v, None)
+            ev[k][1].record(st)
+            if with_prop and k % full_every:
+                fbs.append(dl.dl_last_fallbacks(c))
+        st.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        Dq = Dd.clone()
+        dl.dl_iterate(c, Yd, m, Dq, s, 1, cp, ri, v, rm)          # error of the final state
+        dl.dl_destroy(c)
+        return m * iters / (ms * 1e-3), ms / iters, float(rm[0]), fbs
+
+    v_plain, ms_plain, r_plain, _ = run(False)
+    v_learn, ms_learn, r_learn, fbs = run(True)
+    dl.dl_proposer_destroy(prop)
+    return {"value": v_learn, "unit": UNIT, "ms_per_iteration": ms_learn, "m": m, "K": K,
+            "full_every": full_every, "iterations": iters, "plain_value": v_plain,
+            "plain_ms_per_iteration": ms_plain, "speedup_vs_plain": v_learn / v_plain,
+            "final_rmse": r_learn, "plain_final_rmse": r_plain,
+            "rmse_vs_plain": r_learn / r_plain - 1.0,
+            "equal_rmse": r_learn <= r_plain * (1 + EQUAL_RMSE),
+            "fallback_fraction": float(np.mean(fbs) / m) if fbs else None,
+            "train": {"patches": mt, "epochs": 5, "batch": 4096, "lr": 1e-3, "seconds": train_s,
+                      "epoch_loss": losses, "warmup_iterations": warm},
+            "setup_s": time.perf_counter() - t_setup}
 
 
 def main():

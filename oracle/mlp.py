@@ -88,18 +88,6 @@ def adam_step(params, grads, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     return params, m, v
 
 
-def init_params(p, n, hidden=512, seed=0, positives=None):
-    """He-style initialisation, N(0, 2/fan_in) weights, zero biases; with
-    `positives` (expected ones per target row, e.g. s) the output bias starts at
-    the log-odds of the base rate, log(s / (n - s))."""
-    g = np.random.default_rng(seed)
-    W1 = g.standard_normal((hidden, p)) * math.sqrt(2.0 / p)
-    W2 = g.standard_normal((hidden, hidden)) * math.sqrt(2.0 / hidden)
-    W3 = g.standard_normal((n, hidden)) * math.sqrt(2.0 / hidden)
-    b3 = np.zeros(n) if positives is None else np.full(n, math.log(positives / (n - positives)))
-    return [W1, np.zeros(hidden), W2, np.zeros(hidden), W3, b3]
-
-
 def multi_hot(idx, cnt, n):
     """(m, s) supports with counts -> (m, n) 0/1 targets."""
     m = idx.shape[0]

@@ -164,6 +164,19 @@ def batched_problems(count: int = 16, m_scale: float = 1.0, seed: int = 5000, dt
     return out
 
 
+def proposer_init(p: int, n: int, hidden: int = 512, seed: int = 0, positives: int | None = None):
+    """Seeded starting weights of the support proposer MLP p -> hidden -> hidden -> n:
+    [W1 (hidden, p), b1, W2 (hidden, hidden), b2, W3 (n, hidden), b3], weights
+    N(0, 2 / fan_in), zero biases; with `positives` (expected ones per target row)
+    the output bias starts at the base-rate log-odds log(positives / (n - positives))."""
+    g = _rng(seed)
+    W1 = g.standard_normal((hidden, p)) * np.sqrt(2.0 / p)
+    W2 = g.standard_normal((hidden, hidden)) * np.sqrt(2.0 / hidden)
+    W3 = g.standard_normal((n, hidden)) * np.sqrt(2.0 / hidden)
+    b3 = np.zeros(n) if positives is None else np.full(n, np.log(positives / (n - positives)))
+    return [W1, np.zeros(hidden), W2, np.zeros(hidden), W3, b3]
+
+
 def workload_inputs(name: str, m: int | None = None, dtype=np.float32):
     """(Y, D_init, spec) for a named workload; m may be reduced for sampling."""
     spec = dict(WORKLOADS[name])

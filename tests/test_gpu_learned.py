@@ -44,7 +44,7 @@ def _rel(a, b):
 
 def test_forward_logits_match_reference_network(dl):
     p, n, h, B = 64, 256, 512, 640
-    params = mlp.init_params(p, n, h, seed=1)
+    params = synth.proposer_init(p, n, h, seed=1)
     params[1] += 0.05
     params[5] -= 0.1
     Y, _, _ = synth.workload_inputs("patch_n256", m=B)
@@ -70,7 +70,7 @@ def test_forward_logits_match_reference_network(dl):
 def test_gradients_match_reference_network(dl):
     """One training step with lr = 0 (gradients only) against oracle/mlp.backward."""
     p, n, h, B = 64, 128, 256, 512
-    params = mlp.init_params(p, n, h, seed=2)
+    params = synth.proposer_init(p, n, h, seed=2)
     g = np.random.default_rng(3)
     Y, _, _ = synth.workload_inputs("patch_n256", m=B)
     s = 6
@@ -113,7 +113,7 @@ def trained(dl):
     p, n, h, s = 64, 256, 512, 6
     Ytr, sup, cnt, Ydl, Dw = _labelled_set(dl, n=n, s=s)
     prop = dl.dl_proposer_create(p, n, h, 1024, torch.cuda.current_stream())
-    dl.dl_proposer_set_weights(prop, mlp.init_params(p, n, h, seed=7, positives=s))
+    dl.dl_proposer_set_weights(prop, synth.proposer_init(p, n, h, seed=7, positives=s))
     Yt, St = torch.from_numpy(Ytr).cuda(), torch.from_numpy(sup).cuda()
     losses = []
     for ep in range(8):
@@ -139,7 +139,7 @@ def test_training_reduces_loss_and_learns_the_supports(dl, trained):
     Yv = trained["Ytr"][-4096:]
     r_trained = _recall(dl, trained["prop"], Yv, trained["sup"][-4096:], trained["cnt"][-4096:])
     fresh = dl.dl_proposer_create(64, trained["n"], trained["h"], 1024, torch.cuda.current_stream())
-    dl.dl_proposer_set_weights(fresh, mlp.init_params(64, trained["n"], trained["h"], seed=7,
+    dl.dl_proposer_set_weights(fresh, synth.proposer_init(64, trained["n"], trained["h"], seed=7,
                                                       positives=trained["s"]))
     r_fresh = _recall(dl, fresh, Yv, trained["sup"][-4096:], trained["cnt"][-4096:])
     dl.dl_proposer_destroy(fresh)
@@ -195,7 +195,7 @@ def test_learned_dl_restricted_omp_parity_and_equal_rmse(dl, trained):
     r_plain, _ = run(None)
     r_learn, fb = run(trained["prop"])
     fresh = dl.dl_proposer_create(64, n, trained["h"], 1024, torch.cuda.current_stream())
-    dl.dl_proposer_set_weights(fresh, mlp.init_params(64, n, trained["h"], seed=7, positives=s))
+    dl.dl_proposer_set_weights(fresh, synth.proposer_init(64, n, trained["h"], seed=7, positives=s))
     _, fb_fresh = run(fresh)
     dl.dl_proposer_destroy(fresh)
     gap = r_learn[-1, 1] / r_plain[-1, 1] - 1
