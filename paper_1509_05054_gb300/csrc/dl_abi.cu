@@ -271,7 +271,7 @@ cudaError_t enq_proposer_forward(dl_proposer* P, const void* Xbf, int64_t m, int
 // Sparse coding with the learned proposer: top-K candidates from the MLP,
 // OMP restricted to them, full OMP for the signals whose residual energy
 // exceeds tol2 times the one of their last full OMP.
-cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
+cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D, int s, bool tc) {
   cudaError_t e = enq_proposer_forward(c->prop, c->Ybf, m, c->prop_K, c->cand, c->st);
   if (e != cudaSuccess) return e;
   mark(c, 2);
@@ -281,8 +281,11 @@ cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D
                           c->scnt, c->rr_L, c->rr_ref, c->prop_tol2, c->fb_list, c->fb_count, c->err,
                           c->st);
   if (e != cudaSuccess) return e;
-  e = dlk::omp_listed(c->fb_list, c->fb_count, D, c->G, c->n, Y, c->p, s, c->sidx, c->sval, c->scnt,
-                      c->rr_ref, c->err, c->rs_list, c->rs_count, (int)c->m_max, c->st);
+  // the fallback signals read their correlations from the tensor-core product of all signals
+  if ((e = enq_corr(c, Y, m, D, tc)) != cudaSuccess) return e;
+  e = dlk::omp_listed(c->fb_list, c->fb_count, c->A0, c->lda, c->G, c->n, Y, c->p, s, c->sidx,
+                      c->sval, c->scnt, c->rr_ref, c->err, c->rs_list, c->rs_count, (int)c->m_max,
+                      c->st);
   if (e != cudaSuccess) return e;
   e = dlk::omp_resolve64(Y, c->p, D, c->n, s, c->rs_list, c->rs_count, (int)c->m_max,
                          c->rs_scratch, c->sidx, c->sval, c->scnt, c->st);
@@ -296,7 +299,7 @@ cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s)
   cudaError_t e = enq_gram(c, D, tc);
   if (e != cudaSuccess) return e;
   mark(c, 1);
-  if (c->prop && c->learned_now) return enq_omp_learned(c, Y, m, D, s);
+  if (c->prop && c->learned_now) return enq_omp_learned(c, Y, m, D, s, tc);
   e = enq_corr(c, Y, m, D, tc);
   if (e != cudaSuccess) return e;
   mark(c, 2);
@@ -353,7 +356,8 @@ int64_t kernels_per_iteration(dl_ctx* c, bool learned, int64_t m) {
                   !getenv("DL_FORCE_SIMT_GEMM");
   int64_t k = (tc ? 2 : 1) /* split + Gram */ + kKernelsScan + kKernelsJau;
   if (learned)
-    k += 4 * proposer_chunks(c->prop, m) /* 3 GEMMs + top-K */ + 3 /* restricted, listed, FP64 */;
+    k += 4 * proposer_chunks(c->prop, m) /* 3 GEMMs + top-K */ + 3 /* restricted, listed, FP64 */ +
+         (c->lp_kind ? 2 : 1) /* correlations for the fallback */;
   else
     k += (c->lp_kind ? 2 : 1) /* correlations */ + 2 /* OMP, FP64 re-solve */;
   return k;

@@ -58,9 +58,10 @@ cudaError_t omp_restricted(const int32_t* cand, int K, const float* D, const flo
                            const float* Y, int p, int64_t m, int s, int32_t* idx, float* val,
                            int32_t* cnt, float* ores, const float* ref_res, float tol2, int* fb_list,
                            int* fb_count, int* err, cudaStream_t st);
-cudaError_t omp_listed(const int* list, const int* count, const float* D, const float* G, int n,
-                       const float* Y, int p, int s, int32_t* idx, float* val, int32_t* cnt,
-                       float* ores, int* err, int* rl, int* rc, int rcap, cudaStream_t st);
+cudaError_t omp_listed(const int* list, const int* count, const float* A0, int64_t lda,
+                       const float* G, int n, const float* Y, int p, int s, int32_t* idx, float* val,
+                       int32_t* cnt, float* ores, int* err, int* rl, int* rc, int rcap,
+                       cudaStream_t st);
 
 // ---- learned proposer (k_mlp.cu) ----------------------------------------------
 enum : int { MLP_EPI_BF16 = 0, MLP_EPI_F32 = 1, MLP_EPI_GELU_FWD = 2, MLP_EPI_GELU_BWD = 3 };

@@ -377,30 +377,22 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_restricted_kernel(
 // signal's correlations D^T y into shared memory, then runs the OMP.
 template <int NT, int SMAX>
 __global__ void __launch_bounds__(OMP_THREADS) omp_listed_kernel(
-    const int* __restrict__ list, const int* __restrict__ count, const float* __restrict__ D,
-    const float* __restrict__ G, int n, const float* __restrict__ Y, int p, int s,
+    const int* __restrict__ list, const int* __restrict__ count, const float* __restrict__ A0,
+    int64_t lda, const float* __restrict__ G, int n, const float* __restrict__ Y, int p, int s,
     int32_t* __restrict__ oidx, float* __restrict__ oval, int32_t* __restrict__ ocnt,
     float* __restrict__ ores, int* __restrict__ err, int* __restrict__ rs_list,
     int* __restrict__ rs_count, int rs_cap) {
   __shared__ float Lsh[OMP_THREADS / 32][SMAX][SMAX];
   __shared__ float Csh[OMP_THREADS / 32][SMAX];
-  __shared__ float a0sh[OMP_THREADS / 32][32 * NT];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int wib = threadIdx.x >> 5;
   const int total = *count;
   const int nw = gridDim.x * (blockDim.x >> 5);
   for (int e = blockIdx.x * (blockDim.x >> 5) + wib; e < total; e += nw) {
     const int64_t i = list[e];
-    const float* y = Y + i * p;
-    for (int j = lane; j < n; j += 32) {
-      const float* dj = D + (size_t)j * p;
-      float a = 0.f;
-      for (int r = 0; r < p; ++r) a = fmaf(dj[r], y[r], a);
-      a0sh[wib][j] = a;
-    }
-    __syncwarp();
     const GramGlobal<false> gsrc{G, n};
-    omp_one<NT, SMAX, false, false>(i, gsrc, Lsh[wib], Csh[wib], nullptr, a0sh[wib], n, y, p, s,
-                                    nullptr, oidx, oval, ocnt, ores, err, rs_list, rs_count, rs_cap);
+    omp_one<NT, SMAX, false, false>(i, gsrc, Lsh[wib], Csh[wib], nullptr, A0 + i * lda, n, Y + i * p,
+                                    p, s, nullptr, oidx, oval, ocnt, ores, err, rs_list, rs_count,
+                                    rs_cap);
     __syncwarp();
   }
 }
@@ -484,27 +476,28 @@ cudaError_t omp_restricted(const int32_t* cand, int K, const float* D, const flo
 }
 
 template <int NT>
-cudaError_t listed_s(const int* list, const int* count, const float* D, const float* G, int n,
-                     const float* Y, int p, int s, int32_t* idx, float* val, int32_t* cnt, float* ores,
-                     int* err, int* rl, int* rc, int rcap, cudaStream_t st) {
+cudaError_t listed_s(const int* list, const int* count, const float* A0, int64_t lda, const float* G,
+                     int n, const float* Y, int p, int s, int32_t* idx, float* val, int32_t* cnt,
+                     float* ores, int* err, int* rl, int* rc, int rcap, cudaStream_t st) {
   const unsigned blocks = (unsigned)(num_sms() * 3);
   if (s <= 4)
-    omp_listed_kernel<NT, 4><<<blocks, OMP_THREADS, 0, st>>>(list, count, D, G, n, Y, p, s, idx, val,
-                                                             cnt, ores, err, rl, rc, rcap);
+    omp_listed_kernel<NT, 4><<<blocks, OMP_THREADS, 0, st>>>(list, count, A0, lda, G, n, Y, p, s, idx,
+                                                             val, cnt, ores, err, rl, rc, rcap);
   else
-    omp_listed_kernel<NT, 8><<<blocks, OMP_THREADS, 0, st>>>(list, count, D, G, n, Y, p, s, idx, val,
-                                                             cnt, ores, err, rl, rc, rcap);
+    omp_listed_kernel<NT, 8><<<blocks, OMP_THREADS, 0, st>>>(list, count, A0, lda, G, n, Y, p, s, idx,
+                                                             val, cnt, ores, err, rl, rc, rcap);
   return cudaGetLastError();
 }
 
-cudaError_t omp_listed(const int* list, const int* count, const float* D, const float* G, int n,
-                       const float* Y, int p, int s, int32_t* idx, float* val, int32_t* cnt,
-                       float* ores, int* err, int* rl, int* rc, int rcap, cudaStream_t st) {
+cudaError_t omp_listed(const int* list, const int* count, const float* A0, int64_t lda,
+                       const float* G, int n, const float* Y, int p, int s, int32_t* idx, float* val,
+                       int32_t* cnt, float* ores, int* err, int* rl, int* rc, int rcap,
+                       cudaStream_t st) {
   const int nt = (n + 31) / 32;
-  if (nt <= 2) return listed_s<2>(list, count, D, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
-  if (nt <= 4) return listed_s<4>(list, count, D, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
-  if (nt <= 8) return listed_s<8>(list, count, D, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
-  return listed_s<16>(list, count, D, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
+  if (nt <= 2) return listed_s<2>(list, count, A0, lda, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
+  if (nt <= 4) return listed_s<4>(list, count, A0, lda, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
+  if (nt <= 8) return listed_s<8>(list, count, A0, lda, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
+  return listed_s<16>(list, count, A0, lda, G, n, Y, p, s, idx, val, cnt, ores, err, rl, rc, rcap, st);
 }
 
 cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
