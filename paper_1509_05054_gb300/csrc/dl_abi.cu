@@ -17,7 +17,8 @@
 // with FP32 masters and Adam state; see k_mlp.cu).
 struct dl_proposer {
   int dev = 0, p = 0, pk = 0, n = 0, hidden = 0;
-  int64_t bmax = 0;        // rows per forward chunk / training batch
+  int64_t bmax = 0;        // rows per training batch
+  int64_t ichunk = 0;      // rows per inference chunk (activations stay in L2)
   cudaStream_t st = nullptr;
   float* w[6] = {};        // W1 (hidden x pk), b1, W2 (hidden x hidden), b2, W3 (n x hidden), b3
   float* g[6] = {};        // gradients of the last training step
@@ -986,7 +987,7 @@ void free_proposer(dl_proposer* P) {
   delete P;
 }
 
-int64_t proposer_chunks(dl_proposer* P, int64_t m) { return P ? (m + P->bmax - 1) / P->bmax : 0; }
+int64_t proposer_chunks(dl_proposer* P, int64_t m) { return P ? (m + P->ichunk - 1) / P->ichunk : 0; }
 
 // rows of Y (FP32, p wide; selected by idx when given) -> BF16 rows pk wide, and
 // their support slots (-1 padded to kPropMaxS) when sup is given.
@@ -1021,8 +1022,8 @@ cudaError_t enq_forward_chunk(dl_proposer* P, const void* X, int64_t B, bool tra
 cudaError_t enq_proposer_forward(dl_proposer* P, const void* Xbf, int64_t m, int K, int32_t* cand,
                                  cudaStream_t st) {
   P->st = st;
-  for (int64_t r0 = 0; r0 < m; r0 += P->bmax) {
-    const int64_t B = m - r0 < P->bmax ? m - r0 : P->bmax;
+  for (int64_t r0 = 0; r0 < m; r0 += P->ichunk) {
+    const int64_t B = m - r0 < P->ichunk ? m - r0 : P->ichunk;
     const void* X = (const __nv_bfloat16*)Xbf + r0 * P->pk;
     cudaError_t e = enq_forward_chunk(P, X, B, false);
     if (e != cudaSuccess) return e;
@@ -1090,8 +1091,9 @@ extern "C" int dl_proposer_create(dl_proposer** out, int p, int n, int hidden, i
   P->n = n;
   P->hidden = hidden;
   P->bmax = batch;
+  P->ichunk = batch > 16384 ? batch : 16384;
   P->st = (cudaStream_t)stream;
-  const int64_t h = hidden, B = batch;
+  const int64_t h = hidden, B = batch, BI = P->ichunk;
   const int64_t lens[6] = {h * P->pk, h, h * h, h, (int64_t)n * h, n};
   bool ok = true;
   for (int k = 0; k < 6 && ok; ++k) {
@@ -1106,9 +1108,9 @@ extern "C" int dl_proposer_create(dl_proposer** out, int p, int n, int hidden, i
   ok = ok && dalloc((uint8_t**)&P->wb[0], lens[0] * b2) && dalloc((uint8_t**)&P->wb[1], lens[2] * b2) &&
        dalloc((uint8_t**)&P->wb[2], lens[4] * b2) && dalloc((uint8_t**)&P->wt[0], lens[2] * b2) &&
        dalloc((uint8_t**)&P->wt[1], lens[4] * b2) && dalloc((uint8_t**)&P->X, B * P->pk * b2) &&
-       dalloc(&P->A1, B * h) && dalloc(&P->A2, B * h) && dalloc((uint8_t**)&P->H1, B * h * b2) &&
-       dalloc((uint8_t**)&P->H2, B * h * b2) && dalloc(&P->Z, B * n) &&
-       dalloc((uint8_t**)&P->Zb, B * n * b2) && dalloc(&P->sup, B * kPropMaxS) &&
+       dalloc(&P->A1, B * h) && dalloc(&P->A2, B * h) && dalloc((uint8_t**)&P->H1, BI * h * b2) &&
+       dalloc((uint8_t**)&P->H2, BI * h * b2) && dalloc(&P->Z, B * n) &&
+       dalloc((uint8_t**)&P->Zb, BI * n * b2) && dalloc(&P->sup, B * kPropMaxS) &&
        dalloc((uint8_t**)&P->dZ, B * n * b2) && dalloc((uint8_t**)&P->dZt, B * n * b2) &&
        dalloc((uint8_t**)&P->H2t, B * h * b2) && dalloc((uint8_t**)&P->dA2, B * h * b2) &&
        dalloc((uint8_t**)&P->dA2t, B * h * b2) && dalloc((uint8_t**)&P->H1t, B * h * b2) &&

@@ -23,7 +23,7 @@ constexpr int GM_THREADS = 128;
 constexpr int GM_TILE_M = 128;
 constexpr int GM_BLOCK_N = 256;
 constexpr int GM_BK = 64;  // BF16 elements per 128-byte chunk
-constexpr int GM_STAGES = 2;
+constexpr int GM_STAGES = 4;
 constexpr size_t GM_A_BYTES = (size_t)GM_TILE_M * 128;   // 16 KB
 constexpr size_t GM_B_BYTES = (size_t)GM_BLOCK_N * 128;  // 32 KB
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) |
@@ -49,6 +49,7 @@ struct Epi {
 __global__ void __launch_bounds__(GM_THREADS, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      int64_t M, int N, int K, Epi epi, int* __restrict__ err) {
+  // blockIdx.z selects a slice of the K chunks (split-K; F32 output accumulated atomically)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* As = base;
@@ -85,34 +86,40 @@ __global__ void __launch_bounds__(GM_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  const int kz = (int)gridDim.z;
+  const int per = (nk + kz - 1) / kz;
+  const int kbeg = (int)blockIdx.z * per;
+  const int kend = kbeg + per < nk ? kbeg + per : nk;
+  const int cnt = kend > kbeg ? kend - kbeg : 0;
   if (threadIdx.x == 0) {
     bool ok = true;
-    for (int q = 0; q < GM_STAGES && q < nk; ++q) {
+    for (int q = 0; q < GM_STAGES && q < cnt; ++q) {
       mbar_expect_tx(&full[q], (uint32_t)(GM_A_BYTES + GM_B_BYTES));
-      tma_load_2d(As + q * GM_A_BYTES, &tmA, &full[q], q * GM_BK, (int)m0);
-      tma_load_2d(Bs + q * GM_B_BYTES, &tmB, &full[q], q * GM_BK, n0);
+      tma_load_2d(As + q * GM_A_BYTES, &tmA, &full[q], (kbeg + q) * GM_BK, (int)m0);
+      tma_load_2d(Bs + q * GM_B_BYTES, &tmB, &full[q], (kbeg + q) * GM_BK, n0);
     }
-    for (int kc = 0; kc < nk && ok; ++kc) {
-      const int st = kc % GM_STAGES;
-      const uint32_t ph = (uint32_t)((kc / GM_STAGES) & 1);
-      if (!(ok = mbar_wait(&full[st], ph))) break;
+    for (int j = 0; j < cnt && ok; ++j) {
+      const int st = j % GM_STAGES;
+      if (!(ok = mbar_wait(&full[st], (uint32_t)((j / GM_STAGES) & 1)))) break;
       tc_fence_after();
       const uint64_t ad = sw128_desc(As + st * GM_A_BYTES);
       const uint64_t bd = sw128_desc(Bs + st * GM_B_BYTES);
 #pragma unroll
       for (int k = 0; k < 4; ++k)
         mma_f16(tmem, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), kIdescBf16,
-                (kc > 0 || k > 0) ? 1u : 0u);
+                (j > 0 || k > 0) ? 1u : 0u);
       mma_commit(&empty[st]);
-      if (kc + GM_STAGES < nk) {
-        if (!(ok = mbar_wait(&empty[st], ph))) break;
-        const int kn = kc + GM_STAGES;
-        mbar_expect_tx(&full[st], (uint32_t)(GM_A_BYTES + GM_B_BYTES));
-        tma_load_2d(As + st * GM_A_BYTES, &tmA, &full[st], kn * GM_BK, (int)m0);
-        tma_load_2d(Bs + st * GM_B_BYTES, &tmB, &full[st], kn * GM_BK, n0);
+      // refill the stage of the previous chunk (its MMAs were issued one step ago)
+      const int jp = j - 1, jn = jp + GM_STAGES;
+      if (jp >= 0 && jn < cnt) {
+        const int ps = jp % GM_STAGES;
+        if (!(ok = mbar_wait(&empty[ps], (uint32_t)((jp / GM_STAGES) & 1)))) break;
+        mbar_expect_tx(&full[ps], (uint32_t)(GM_A_BYTES + GM_B_BYTES));
+        tma_load_2d(As + ps * GM_A_BYTES, &tmA, &full[ps], (kbeg + jn) * GM_BK, (int)m0);
+        tma_load_2d(Bs + ps * GM_B_BYTES, &tmB, &full[ps], (kbeg + jn) * GM_BK, n0);
       }
     }
-    if (ok) {
+    if (ok && cnt > 0) {
       mma_commit(done);
       ok = mbar_wait(done, 0);
     }
@@ -120,31 +127,77 @@ __global__ void __launch_bounds__(GM_THREADS, 1)
   }
   __syncthreads();
   tc_fence_after();
-  if (!s_fail) {
+  if (!s_fail && cnt > 0) {
     const int64_t row = m0 + warp * 32 + lane;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const int ncols = N - n0 < GM_BLOCK_N ? N - n0 : GM_BLOCK_N;
+    const bool split = kz > 1;
     for (int c0 = 0; c0 < ncols; c0 += 16) {
       uint32_t r[16];
       tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
       if (row >= M) continue;
+      const int col0 = n0 + c0;
+      const bool full16 = col0 + 16 <= N && (epi.ldc % 8) == 0;
+      float a[16], o[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const int col = n0 + c0 + q;
-        if (col >= N) break;
-        float a = __uint_as_float(r[q]);
-        if (epi.bias) a += epi.bias[col];
-        float o = a;
-        if (epi.op == MLP_EPI_GELU_FWD) {
-          if (epi.out_f32) epi.out_f32[row * epi.ldc + col] = a;
-          o = gelu_f(a);
-        } else if (epi.op == MLP_EPI_GELU_BWD) {
-          o = a * gelu_grad_f(epi.aux[row * epi.ldaux + col]);
-        } else if (epi.op == MLP_EPI_F32) {
-          epi.out_f32[row * epi.ldc + col] = a;
-          continue;
+        a[q] = __uint_as_float(r[q]);
+        if (epi.bias && !split && col0 + q < N) a[q] += epi.bias[col0 + q];
+      }
+      if (epi.op == MLP_EPI_F32) {
+        float* dst = epi.out_f32 + row * epi.ldc + col0;
+        if (split) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (col0 + q < N) atomicAdd(dst + q, a[q]);
+        } else if (full16) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            ((float4*)dst)[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (col0 + q < N) dst[q] = a[q];
         }
-        if (epi.out_bf16) epi.out_bf16[row * epi.ldc + col] = __float2bfloat16_rn(o);
+        continue;
+      }
+      if (epi.op == MLP_EPI_GELU_FWD) {
+        if (epi.out_f32) {
+          float* pre = epi.out_f32 + row * epi.ldc + col0;
+          if (full16) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              ((float4*)pre)[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (col0 + q < N) pre[q] = a[q];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) o[q] = gelu_f(a[q]);
+      } else if (epi.op == MLP_EPI_GELU_BWD) {
+        const float* aux = epi.aux + row * epi.ldaux + col0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) o[q] = (col0 + q < N) ? a[q] * gelu_grad_f(aux[q]) : 0.f;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) o[q] = a[q];
+      }
+      __nv_bfloat16* dst = epi.out_bf16 + row * epi.ldc + col0;
+      if (full16) {
+        uint32_t w[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(o[2 * q], o[2 * q + 1]);
+          w[q] = *(const uint32_t*)&h2;
+        }
+        ((uint4*)dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        ((uint4*)dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (col0 + q < N) dst[q] = __float2bfloat16_rn(o[q]);
       }
     }
   } else if (threadIdx.x == 0) {
@@ -235,14 +288,17 @@ __global__ void bce_grad_kernel(const float* __restrict__ z, int64_t B, int n,
   }
 }
 
-// out[c] = sum_r in[r][c]  (BF16 rows, FP32 sums), one thread per column.
+// out[c] += sum over a 256-row slice of in[r][c] (BF16 rows, FP32 sums); the
+// caller zeroes out.  grid = (column blocks, row slices).
 __global__ void colsum_bf16_kernel(const __nv_bfloat16* __restrict__ in, int64_t R, int C,
                                    float* __restrict__ out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
+  const int64_t r0 = (int64_t)blockIdx.y * 256;
+  const int64_t r1 = r0 + 256 < R ? r0 + 256 : R;
   float acc = 0.f;
-  for (int64_t r = 0; r < R; ++r) acc += __bfloat162float(in[r * C + c]);
-  out[c] = acc;
+  for (int64_t r = r0; r < r1; ++r) acc += __bfloat162float(in[r * C + c]);
+  atomicAdd(out + c, acc);
 }
 
 // Adam (Kingma & Ba) on FP32 master weights; refreshes the BF16 copy.
@@ -327,8 +383,23 @@ cudaError_t mlp_gemm(const void* A, int64_t M, const void* B, int N, int K, int 
       cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   Epi epi{op, bias, aux, ldaux, out_f32, (__nv_bfloat16*)out_bf16, ldc};
-  dim3 grid((unsigned)((M + GM_TILE_M - 1) / GM_TILE_M), (unsigned)((N + GM_BLOCK_N - 1) / GM_BLOCK_N));
-  gemm_bf16_kernel<<<grid, GM_THREADS, smem, st>>>(ma, mb, M, N, K, epi, err);
+  const unsigned gx = (unsigned)((M + GM_TILE_M - 1) / GM_TILE_M);
+  const unsigned gy = (unsigned)((N + GM_BLOCK_N - 1) / GM_BLOCK_N);
+  // small output grids with long K (weight gradients) split K across CTAs and
+  // accumulate FP32 atomically (bias added by a separate pass is not needed:
+  // those products have no bias)
+  unsigned gz = 1;
+  const int nk = K / GM_BK;
+  if (op == MLP_EPI_F32 && !bias) {
+    const unsigned want = (unsigned)(2 * num_sms()) / (gx * gy);
+    gz = want < 1 ? 1 : want;
+    if (gz > (unsigned)nk / 2) gz = nk / 2 > 0 ? (unsigned)(nk / 2) : 1;
+  }
+  if (gz > 1) {
+    e = cudaMemsetAsync(out_f32, 0, sizeof(float) * (size_t)M * ldc, st);
+    if (e != cudaSuccess) return e;
+  }
+  gemm_bf16_kernel<<<dim3(gx, gy, gz), GM_THREADS, smem, st>>>(ma, mb, M, N, K, epi, err);
   return cudaGetLastError();
 }
 
@@ -356,7 +427,10 @@ cudaError_t mlp_bce_grad(const float* z, int64_t B, int n, const int32_t* sup, i
 }
 
 cudaError_t mlp_colsum(const void* in, int64_t R, int C, float* out, cudaStream_t st) {
-  colsum_bf16_kernel<<<(C + 127) / 128, 128, 0, st>>>((const __nv_bfloat16*)in, R, C, out);
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * (size_t)C, st);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((C + 127) / 128), (unsigned)((R + 255) / 256));
+  colsum_bf16_kernel<<<grid, 128, 0, st>>>((const __nv_bfloat16*)in, R, C, out);
   return cudaGetLastError();
 }
 
