@@ -212,7 +212,7 @@ int64_t dl_last_resolved(dl_ctx* ctx);
 
 /*
  * dl_uses_tensor_cores -- 1 if this context's shape (p % 4 == 0, p <= 64,
- * n <= 512) takes the split-TF32 tcgen05 path for D^T Y and D^T D, 0 if it
+ * n <= 1024) takes the split-TF32 tcgen05 path for D^T Y and D^T D, 0 if it
  * takes the FP32 CUDA-core path.  The environment variable
  * DL_FORCE_SIMT_GEMM forces the CUDA-core path.
  */

@@ -232,7 +232,7 @@ void mark(dl_ctx* c, int k) {
 }
 
 // ---- enqueue helpers (no synchronisation) --------------------------------------
-// The tensor-core path needs p % 4 == 0, p <= 64, n <= 512 and 16-byte aligned operands;
+// The tensor-core path needs p % 4 == 0, p <= 64, n <= 1024 and 16-byte aligned operands;
 // other shapes use the FP32 CUDA-core GEMM.
 bool tc_ok(dl_ctx* c, const float* Y, const float* D) {
   if (getenv("DL_FORCE_SIMT_GEMM") || !c->cfg_corr_tc) return false;

@@ -47,16 +47,23 @@ __device__ double block_sum_d(double v, double* scratch) {
 }
 
 // Pass A: e_i = y_i - D x_i; U[:, j] += x_{j,i} e_i; r_j += x_{j,i}^2;
-// partial ||E||^2 and ||Y||^2.  PL = rows per lane (p <= 32*PL).
-template <int PL, bool SMEM>
-__global__ void __launch_bounds__(ACC_THREADS) accum_kernel(
+// partial ||E||^2 and ||Y||^2.  Eight lanes per signal (four signals per warp):
+// lane g of group q holds rows g + 8((t + q) mod RL), t < RL (p <= 8*RL); the
+// rotation by q puts the four groups' shared-memory atomics on distinct banks.
+// Support slots t and t + 8 live on group lane t % 8.
+template <int RL, bool SMEM>
+__global__ void __launch_bounds__(ACC_THREADS, 1) accum_kernel(
     const float* __restrict__ Y, int p, int64_t m, const float* __restrict__ D, int n, int s,
     const int32_t* __restrict__ idx, const float* __restrict__ val, const int32_t* __restrict__ cnt,
     float* __restrict__ Upart, double* __restrict__ epart, int* __restrict__ err) {
   extern __shared__ float sh[];
   __shared__ double red[ACC_THREADS / 32];
   const int lane = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;
+  const int g = lane & 7, gbase = lane & ~7;
+  const int q = (threadIdx.x >> 3) & 3;
+  int row[RL];
+#pragma unroll
+  for (int t = 0; t < RL; ++t) row[t] = g + 8 * ((t + q) % RL);
   const int np = n * p;
   float* U = SMEM ? sh : Upart;  // atom-major: U[j*p + r]; then r_j at U[np + j]
   if (SMEM) {
@@ -64,39 +71,50 @@ __global__ void __launch_bounds__(ACC_THREADS) accum_kernel(
     __syncthreads();
   }
   float ee = 0.f, yy = 0.f;
-  const int64_t gw = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5);
-  const int64_t stride = (int64_t)gridDim.x * nw;
-  for (int64_t i = gw; i < m; i += stride) {
-    float e[PL];
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
+  const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
+  // every lane of a warp loops the same number of times (shuffles stay converged)
+  const int64_t trips = (m + groups - 1) / groups;
+  for (int64_t k = 0; k < trips; ++k) {
+    const int64_t i = g0 + k * groups;
+    const bool live = i < m;
+    float e[RL];
 #pragma unroll
-    for (int u = 0; u < PL; ++u) {
-      const int r = lane + 32 * u;
-      e[u] = (r < p) ? Y[i * p + r] : 0.f;
-      yy = fmaf(e[u], e[u], yy);
+    for (int t = 0; t < RL; ++t) {
+      const int r = row[t];
+      e[t] = (live && r < p) ? Y[i * p + r] : 0.f;
+      yy = fmaf(e[t], e[t], yy);
     }
-    const int c = cnt[i];
-    const int myj = (lane < c) ? idx[i * s + lane] : 0;
-    const float myx = (lane < c) ? val[i * s + lane] : 0.f;
-    for (int t = 0; t < c; ++t) {
-      const int j = __shfl_sync(FULL, myj, t);
-      const float x = __shfl_sync(FULL, myx, t);
+    const int c = live ? cnt[i] : 0;
+    const int j0 = (g < c) ? idx[i * s + g] : 0;
+    const float x0 = (g < c) ? val[i * s + g] : 0.f;
+    const int j1 = (g + 8 < c) ? idx[i * s + g + 8] : 0;
+    const float x1 = (g + 8 < c) ? val[i * s + g + 8] : 0.f;
+    const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)c);
+    for (int t = 0; t < cmax; ++t) {
+      const int jj = __shfl_sync(0xffffffffu, t < 8 ? j0 : j1, gbase + (t & 7));
+      const float xx = __shfl_sync(0xffffffffu, t < 8 ? x0 : x1, gbase + (t & 7));
+      if (t < c) {
 #pragma unroll
-      for (int u = 0; u < PL; ++u) {
-        const int r = lane + 32 * u;
-        if (r < p) e[u] = fmaf(-x, __ldg(D + (size_t)j * p + r), e[u]);
+        for (int u = 0; u < RL; ++u) {
+          const int r = row[u];
+          if (r < p) e[u] = fmaf(-xx, __ldg(D + (size_t)jj * p + r), e[u]);
+        }
       }
     }
 #pragma unroll
-    for (int u = 0; u < PL; ++u) ee = fmaf(e[u], e[u], ee);
-    for (int t = 0; t < c; ++t) {
-      const int j = __shfl_sync(FULL, myj, t);
-      const float x = __shfl_sync(FULL, myx, t);
+    for (int u = 0; u < RL; ++u) ee = fmaf(e[u], e[u], ee);
+    for (int t = 0; t < cmax; ++t) {
+      const int jj = __shfl_sync(0xffffffffu, t < 8 ? j0 : j1, gbase + (t & 7));
+      const float xx = __shfl_sync(0xffffffffu, t < 8 ? x0 : x1, gbase + (t & 7));
+      if (t < c) {
 #pragma unroll
-      for (int u = 0; u < PL; ++u) {
-        const int r = lane + 32 * u;
-        if (r < p) atomicAdd(&U[(size_t)j * p + r], x * e[u]);
+        for (int u = 0; u < RL; ++u) {
+          const int r = row[u];
+          if (r < p) atomicAdd(&U[(size_t)jj * p + r], xx * e[u]);
+        }
+        if (g == 0) atomicAdd(&U[np + jj], xx * xx);
       }
-      if (lane == 0) atomicAdd(&U[np + j], x * x);
     }
   }
   if (!isfinite(ee) || !isfinite(yy)) atomicOr(err, ERR_NONFINITE);
@@ -165,7 +183,8 @@ __global__ void atoms_kernel(const float* __restrict__ D, int p, int n, const fl
 
 // Pass B: per signal, e = y - D x (old atoms), x_t' = e.d'_{j_t} + c_{j_t} x_t,
 // then ||y - D' x'||^2.  Writes the slots and, optionally, the CSC arrays.
-template <int PL>
+// Eight lanes per signal (four signals per warp), as in pass A.
+template <int RL>
 __global__ void __launch_bounds__(ROW_THREADS) rows_kernel(
     const float* __restrict__ Y, int p, int64_t m, const float* __restrict__ D,
     const float* __restrict__ Dn, const float* __restrict__ C, int s,
@@ -174,58 +193,83 @@ __global__ void __launch_bounds__(ROW_THREADS) rows_kernel(
     float* __restrict__ csc_val, double* __restrict__ epart) {
   __shared__ double red[ROW_THREADS / 32];
   const int lane = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;
+  const int g = lane & 7, gbase = lane & ~7;
   float e2 = 0.f;
-  const int64_t gw = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5);
-  const int64_t stride = (int64_t)gridDim.x * nw;
-  for (int64_t i = gw; i < m; i += stride) {
-    float y[PL], e[PL];
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
+  const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
+  const int64_t trips = (m + groups - 1) / groups;
+  for (int64_t k = 0; k < trips; ++k) {
+    const int64_t i = g0 + k * groups;
+    const bool live = i < m;
+    float y[RL], e[RL];
 #pragma unroll
-    for (int u = 0; u < PL; ++u) {
-      const int r = lane + 32 * u;
-      y[u] = (r < p) ? Y[i * p + r] : 0.f;
+    for (int u = 0; u < RL; ++u) {
+      const int r = g + 8 * u;
+      y[u] = (live && r < p) ? Y[i * p + r] : 0.f;
       e[u] = y[u];
     }
-    const int c = cnt[i];
-    const int myj = (lane < c) ? idx[i * s + lane] : 0;
-    const float myx = (lane < c) ? val[i * s + lane] : 0.f;
-    for (int t = 0; t < c; ++t) {
-      const int j = __shfl_sync(FULL, myj, t);
-      const float x = __shfl_sync(FULL, myx, t);
+    const int c = live ? cnt[i] : 0;
+    const int j0 = (g < c) ? idx[i * s + g] : 0;
+    const float x0 = (g < c) ? val[i * s + g] : 0.f;
+    const int j1 = (g + 8 < c) ? idx[i * s + g + 8] : 0;
+    const float x1 = (g + 8 < c) ? val[i * s + g + 8] : 0.f;
+    const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)c);
+    for (int t = 0; t < cmax; ++t) {
+      const int jj = __shfl_sync(0xffffffffu, t < 8 ? j0 : j1, gbase + (t & 7));
+      const float xx = __shfl_sync(0xffffffffu, t < 8 ? x0 : x1, gbase + (t & 7));
+      if (t < c) {
 #pragma unroll
-      for (int u = 0; u < PL; ++u) {
-        const int r = lane + 32 * u;
-        if (r < p) e[u] = fmaf(-x, __ldg(D + (size_t)j * p + r), e[u]);
+        for (int u = 0; u < RL; ++u) {
+          const int r = g + 8 * u;
+          if (r < p) e[u] = fmaf(-xx, __ldg(D + (size_t)jj * p + r), e[u]);
+        }
       }
     }
-    float newx = 0.f;  // lane t: x_t'
-    for (int t = 0; t < c; ++t) {
-      const int j = __shfl_sync(FULL, myj, t);
-      const float x = __shfl_sync(FULL, myx, t);
+    float nx0 = 0.f, nx1 = 0.f;  // x_t' for the slots held by this lane
+    for (int t = 0; t < cmax; ++t) {
+      const int jj = __shfl_sync(0xffffffffu, t < 8 ? j0 : j1, gbase + (t & 7));
+      const float xx = __shfl_sync(0xffffffffu, t < 8 ? x0 : x1, gbase + (t & 7));
       float dot = 0.f;
+      if (t < c) {
 #pragma unroll
-      for (int u = 0; u < PL; ++u) {
-        const int r = lane + 32 * u;
-        if (r < p) dot = fmaf(e[u], __ldg(Dn + (size_t)j * p + r), dot);
+        for (int u = 0; u < RL; ++u) {
+          const int r = g + 8 * u;
+          if (r < p) dot = fmaf(e[u], __ldg(Dn + (size_t)jj * p + r), dot);
+        }
       }
-      dot = warp_sum(dot);
-      const float xn = fmaf(__ldg(C + j), x, dot);
-      if (lane == t) newx = xn;
-      // residual with the updated atoms: y - D' x'
+      dot += __shfl_xor_sync(0xffffffffu, dot, 4);
+      dot += __shfl_xor_sync(0xffffffffu, dot, 2);
+      dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+      if (t < c) {
+        const float xn = fmaf(__ldg(C + jj), xx, dot);
+        if (g == (t & 7)) {
+          if (t < 8) nx0 = xn;
+          else nx1 = xn;
+        }
+        // residual with the updated atoms: y - D' x'
 #pragma unroll
-      for (int u = 0; u < PL; ++u) {
-        const int r = lane + 32 * u;
-        if (r < p) y[u] = fmaf(-xn, __ldg(Dn + (size_t)j * p + r), y[u]);
+        for (int u = 0; u < RL; ++u) {
+          const int r = g + 8 * u;
+          if (r < p) y[u] = fmaf(-xn, __ldg(Dn + (size_t)jj * p + r), y[u]);
+        }
       }
     }
 #pragma unroll
-    for (int u = 0; u < PL; ++u) e2 = fmaf(y[u], y[u], e2);
-    if (lane < c) {
-      val[i * s + lane] = newx;
+    for (int u = 0; u < RL; ++u) e2 = fmaf(y[u], y[u], e2);
+    if (g < c) {
+      val[i * s + g] = nx0;
       if (csc_val) {
-        const int64_t o = colptr[i] + lane;
-        if (csc_rowidx) csc_rowidx[o] = myj;
-        csc_val[o] = newx;
+        const int64_t o = colptr[i] + g;
+        if (csc_rowidx) csc_rowidx[o] = j0;
+        csc_val[o] = nx0;
+      }
+    }
+    if (g + 8 < c) {
+      val[i * s + g + 8] = nx1;
+      if (csc_val) {
+        const int64_t o = colptr[i] + g + 8;
+        if (csc_rowidx) csc_rowidx[o] = j1;
+        csc_val[o] = nx1;
       }
     }
   }
@@ -413,10 +457,10 @@ int jau_row_blocks_max() { return 8 * num_sms(); }
 cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int n, int s,
                            const int32_t* idx, const float* val, const int32_t* cnt,
                            const JauWork& w, int* err, cudaStream_t st) {
-  if (p <= 32) return accum_t<1>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
-  if (p <= 64) return accum_t<2>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
-  if (p <= 96) return accum_t<3>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
-  return accum_t<4>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
+  if (p <= 32) return accum_t<4>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
+  if (p <= 64) return accum_t<8>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
+  if (p <= 96) return accum_t<12>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
+  return accum_t<16>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
 }
 
 cudaError_t jau_atoms(const float* D, int p, int n, const JauWork& w, cudaStream_t st) {
@@ -436,10 +480,10 @@ cudaError_t jau_rows(const float* Y, int p, int64_t m, const float* D, int n, in
 #define DL_ROWS(PL)                                                                              \
   rows_kernel<PL><<<nb, ROW_THREADS, 0, st>>>(Y, p, m, D, w.Dn, w.C, s, idx, val, cnt, colptr, \
                                               csc_rowidx, csc_val, w.epart_b)
-  if (p <= 32) DL_ROWS(1);
-  else if (p <= 64) DL_ROWS(2);
-  else if (p <= 96) DL_ROWS(3);
-  else DL_ROWS(4);
+  if (p <= 32) DL_ROWS(4);
+  else if (p <= 64) DL_ROWS(8);
+  else if (p <= 96) DL_ROWS(12);
+  else DL_ROWS(16);
 #undef DL_ROWS
   return cudaGetLastError();
 }
