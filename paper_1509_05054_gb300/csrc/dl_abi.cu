@@ -53,6 +53,7 @@ struct dl_ctx {
   // workspace
   float* G = nullptr;
   float* A0 = nullptr;
+  int jau_kernels = 5;   // kernel launches of the last enqueued JAU update
   float* Dhi = nullptr;  // TF32 head / tail of D for the tensor-core correlations
   float* Dlo = nullptr;
   // reduced-precision correlations (precision DL_BF16 / DL_FP8)
@@ -118,7 +119,6 @@ namespace {
 
 constexpr int kKernelsOmp = 5;       // split, gram, correlations, omp, FP64 re-solve
 constexpr int kKernelsScan = 2;      // colptr scan
-constexpr int kKernelsJau = 5;       // accumulate, reduce, atoms, rows, finalize
 
 void free_ctx(dl_ctx* c) {
   if (!c) return;
@@ -320,6 +320,7 @@ cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const
                     int32_t* rowidx_out, float* val_out) {
   c->jw.nb_accum = dlk::jau_accum_blocks(c->p, c->n, c->cfg_acc_mult);
   c->jw.nb_row = dlk::jau_row_blocks(c->cfg_row_per_sm);
+  c->jau_kernels = dlk::jau_launches(c->p, Y, D);
   mark(c, 4);
   cudaError_t e = dlk::jau_accumulate(Y, c->p, m, D, c->n, s, c->sidx, c->sval, c->scnt, c->jw,
                                       c->err, c->st);
@@ -355,7 +356,7 @@ int64_t proposer_chunks(dl_proposer* P, int64_t m);
 int64_t kernels_per_iteration(dl_ctx* c, bool learned, int64_t m) {
   const bool tc = dlk::corr_tc_supported(nullptr, c->p, c->n, c->lda) && c->cfg_corr_tc &&
                   !getenv("DL_FORCE_SIMT_GEMM");
-  int64_t k = (tc ? 2 : 1) /* split + Gram */ + kKernelsScan + kKernelsJau;
+  int64_t k = (tc ? 2 : 1) /* split + Gram */ + kKernelsScan + c->jau_kernels;
   if (learned)
     k += 4 * proposer_chunks(c->prop, m) /* 3 GEMMs + top-K */ + 3 /* restricted, listed, FP64 */ +
          (c->lp_kind ? 2 : 1) /* correlations for the fallback */;
@@ -602,7 +603,7 @@ int jau_update(dl_ctx* c, const float* Y, int64_t m, float* D, const int64_t* co
   DL_CHECK(cudaMemsetAsync(c->iter, 0, sizeof(int), c->st));
   DL_CHECK(dlk::csc_to_slots(dcp, dri, dv, m, c->n, s, c->sidx, c->sval, c->scnt, c->err, c->st));
   DL_CHECK(enq_jau(c, dY, m, dD, s, dcp, nullptr, dv));
-  c->launches += 1 + kKernelsJau;
+  c->launches += 1 + c->jau_kernels;
   if (kind == 0) {
     DL_CHECK(cudaMemcpyAsync(D, dD, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyDeviceToHost, c->st));
     DL_CHECK(cudaMemcpyAsync(val, dv, sizeof(float) * (size_t)nnz, cudaMemcpyDeviceToHost, c->st));
@@ -936,7 +937,7 @@ extern "C" int dl_batch_iterate(dl_batch* b, int iters, double* rmse) {
     b->graph_iters = iters;
   }
   DL_CHECK(cudaGraphLaunch(b->gexec, b->main));
-  for (dl_ctx* c : b->ctxs) c->launches += (int64_t)iters * (kKernelsOmp + kKernelsScan + kKernelsJau);
+  for (dl_ctx* c : b->ctxs) c->launches += (int64_t)iters * (kKernelsOmp + kKernelsScan + c->jau_kernels);
   if (rmse) {
     DL_CHECK(cudaStreamSynchronize(b->main));
     for (int k = 0; k < b->count; ++k)

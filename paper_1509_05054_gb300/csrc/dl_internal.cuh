@@ -41,6 +41,7 @@ cudaError_t corr_lp(int kind, const void* A, int64_t rows_a, const float* a_inv_
                     int* err, cudaStream_t st);
 
 // ---- OMP ----------------------------------------------------------------------
+
 // Batch-OMP of m signals from their correlations A0 (row i = D^T y_i, stride lda) and G = D^T D.
 // Writes s slots per signal (atoms ascending, unused slots idx = -1) and the count.
 // Signals stopped by a pivot below kPivotMin are appended to rs_list (if given) for the
@@ -105,6 +106,9 @@ int jau_accum_blocks_max(int p, int n);
 int jau_row_blocks(int per_sm);
 int jau_row_blocks_max();
 size_t jau_accum_smem(int p, int n);
+// float4 passes (p % 4 == 0, Y and D 16-byte aligned); kernel launches of the JAU passes.
+bool jau_vec4(int p, const float* Y, const float* D);
+int jau_launches(int p, const float* Y, const float* D);
 
 cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int n, int s,
                            const int32_t* idx, const float* val, const int32_t* cnt,

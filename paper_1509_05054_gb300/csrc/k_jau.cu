@@ -8,8 +8,12 @@
 // support sets I_j are never materialised), then every atom is updated by one
 // warp, then every signal recomputes its error and its coefficients.
 //
-// Passes over the signals stream Y, the slots and D with 32-lane-coalesced
-// loads; per-CTA partial sums are reduced in a fixed order.
+// The passes over the signals give each signal eight lanes (four signals per
+// warp).  With p % 4 == 0 and 16-byte aligned Y and D they move float4 rows
+// and pass A adds x e_i into U with vector reductions in L2 (red.v4.f32);
+// otherwise pass A keeps per-CTA copies of U (shared memory when they fit)
+// that are summed in a fixed order.  The energy partial sums are reduced in a
+// fixed order.
 #include "dl_internal.cuh"
 
 #include <math.h>
@@ -20,6 +24,8 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int ACC_THREADS = 1024;
 constexpr int ROW_THREADS = 256;
+constexpr int ACC4_THREADS = 256;
+constexpr int kMaxAtoms = 1024;  // largest n the library accepts
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -128,6 +134,250 @@ __global__ void __launch_bounds__(ACC_THREADS, 1) accum_kernel(
   if (threadIdx.x == 0) {
     epart[2 * blockIdx.x] = see;
     epart[2 * blockIdx.x + 1] = syy;
+  }
+}
+
+// ---- float4 forms (p % 4 == 0, Y and D 16-byte aligned) ----
+// Eight lanes per signal; lane g holds the float4 vectors v = g + 8k (rows
+// 4v..4v+3), k < RV, p <= 32 RV.  The support loops are unrolled to SMAX.
+
+__device__ __forceinline__ void red_add_v4(float* addr, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ float4 f4_fma(float a, float4 b, float4 c) {
+  return make_float4(fmaf(a, b.x, c.x), fmaf(a, b.y, c.y), fmaf(a, b.z, c.z), fmaf(a, b.w, c.w));
+}
+__device__ __forceinline__ float f4_dot(float4 a, float4 b, float acc) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
+}
+
+// Pass A, float4 form: U (zeroed, p x n atom-major, then r at U + n p) gets
+// x_{j,i} e_i by vector reductions in L2 (native FP32 adds); r_j is summed
+// per CTA in shared memory and added once per CTA.
+template <int RV, int SMAX>
+__global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
+    const float* __restrict__ Y, int p, int64_t m, const float* __restrict__ D, int n, int s,
+    const int32_t* __restrict__ idx, const float* __restrict__ val, const int32_t* __restrict__ cnt,
+    float* __restrict__ U, double* __restrict__ epart, int* __restrict__ err) {
+  __shared__ float rsh[kMaxAtoms];
+  __shared__ double red[ACC4_THREADS / 32];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rsh[j] = 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int g = lane & 7, gbase = lane & ~7;
+  const int pv = p >> 2;
+  const float4* __restrict__ Y4 = (const float4*)Y;
+  const float4* __restrict__ D4 = (const float4*)D;
+  float ee = 0.f, yy = 0.f;
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
+  const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
+  const int64_t trips = (m + groups - 1) / groups;
+  for (int64_t k = 0; k < trips; ++k) {
+    const int64_t i = g0 + k * groups;
+    const bool live = i < m;
+    float4 e[RV];
+#pragma unroll
+    for (int q = 0; q < RV; ++q) {
+      const int v = g + 8 * q;
+      e[q] = (live && v < pv) ? Y4[i * pv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+      yy = f4_dot(e[q], e[q], yy);
+    }
+    const int c = live ? cnt[i] : 0;
+    const int j0 = (g < c) ? idx[i * s + g] : 0;
+    const float x0 = (g < c) ? val[i * s + g] : 0.f;
+    const int j1 = (SMAX > 8 && g + 8 < c) ? idx[i * s + g + 8] : 0;
+    const float x1 = (SMAX > 8 && g + 8 < c) ? val[i * s + g + 8] : 0.f;
+    const int cmax = __reduce_max_sync(FULL, (unsigned)c);
+#pragma unroll
+    for (int t = 0; t < SMAX; ++t) {
+      if (t >= cmax) break;
+      const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
+      const float xx = __shfl_sync(FULL, t < 8 ? x0 : x1, gbase + (t & 7));
+      if (t < c) {
+#pragma unroll
+        for (int q = 0; q < RV; ++q) {
+          const int v = g + 8 * q;
+          if (v < pv) e[q] = f4_fma(-xx, __ldg(D4 + (size_t)jj * pv + v), e[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RV; ++q) ee = f4_dot(e[q], e[q], ee);
+#pragma unroll
+    for (int t = 0; t < SMAX; ++t) {
+      if (t >= cmax) break;
+      const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
+      const float xx = __shfl_sync(FULL, t < 8 ? x0 : x1, gbase + (t & 7));
+      if (t < c) {
+#pragma unroll
+        for (int q = 0; q < RV; ++q) {
+          const int v = g + 8 * q;
+          if (v < pv)
+            red_add_v4(U + ((size_t)jj * pv + v) * 4,
+                       make_float4(xx * e[q].x, xx * e[q].y, xx * e[q].z, xx * e[q].w));
+        }
+        if (g == 0) atomicAdd(&rsh[jj], xx * xx);
+      }
+    }
+  }
+  if (!isfinite(ee) || !isfinite(yy)) atomicOr(err, ERR_NONFINITE);
+  __syncthreads();
+  const size_t np = (size_t)n * p;
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    if (rsh[j] != 0.f) atomicAdd(U + np + j, rsh[j]);
+  const double see = block_sum_d((double)ee, red);
+  const double syy = block_sum_d((double)yy, red);
+  if (threadIdx.x == 0) {
+    epart[2 * blockIdx.x] = see;
+    epart[2 * blockIdx.x + 1] = syy;
+  }
+}
+
+// Pass B, float4 form: e = y - D x; x_t' = e.d'_{j_t} + c_{j_t} x_t for all t
+// (independent dot products), then y - D' x'.
+template <int RV, int SMAX>
+__global__ void __launch_bounds__(ROW_THREADS, 4) rows4_kernel(
+    const float* __restrict__ Y, int p, int64_t m, const float* __restrict__ D,
+    const float* __restrict__ Dn, const float* __restrict__ C, int s,
+    const int32_t* __restrict__ idx, float* __restrict__ val, const int32_t* __restrict__ cnt,
+    const int64_t* __restrict__ colptr, int32_t* __restrict__ csc_rowidx,
+    float* __restrict__ csc_val, double* __restrict__ epart) {
+  __shared__ double red[ROW_THREADS / 32];
+  const int lane = threadIdx.x & 31;
+  const int g = lane & 7, gbase = lane & ~7;
+  const int pv = p >> 2;
+  const float4* __restrict__ Y4 = (const float4*)Y;
+  const float4* __restrict__ D4 = (const float4*)D;
+  const float4* __restrict__ N4 = (const float4*)Dn;
+  float e2 = 0.f;
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
+  const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
+  const int64_t trips = (m + groups - 1) / groups;
+  for (int64_t k = 0; k < trips; ++k) {
+    const int64_t i = g0 + k * groups;
+    const bool live = i < m;
+    float4 y[RV], e[RV];
+#pragma unroll
+    for (int q = 0; q < RV; ++q) {
+      const int v = g + 8 * q;
+      y[q] = (live && v < pv) ? Y4[i * pv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+      e[q] = y[q];
+    }
+    const int c = live ? cnt[i] : 0;
+    const int j0 = (g < c) ? idx[i * s + g] : 0;
+    const float x0 = (g < c) ? val[i * s + g] : 0.f;
+    const int j1 = (SMAX > 8 && g + 8 < c) ? idx[i * s + g + 8] : 0;
+    const float x1 = (SMAX > 8 && g + 8 < c) ? val[i * s + g + 8] : 0.f;
+    const int cmax = __reduce_max_sync(FULL, (unsigned)c);
+#pragma unroll
+    for (int t = 0; t < SMAX; ++t) {
+      if (t >= cmax) break;
+      const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
+      const float xx = __shfl_sync(FULL, t < 8 ? x0 : x1, gbase + (t & 7));
+      if (t < c) {
+#pragma unroll
+        for (int q = 0; q < RV; ++q) {
+          const int v = g + 8 * q;
+          if (v < pv) e[q] = f4_fma(-xx, __ldg(D4 + (size_t)jj * pv + v), e[q]);
+        }
+      }
+    }
+    float xn[SMAX];
+#pragma unroll
+    for (int t = 0; t < SMAX; ++t) {
+      xn[t] = 0.f;
+      if (t >= cmax) break;
+      const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
+      const float xx = __shfl_sync(FULL, t < 8 ? x0 : x1, gbase + (t & 7));
+      float dot = 0.f;
+      if (t < c) {
+#pragma unroll
+        for (int q = 0; q < RV; ++q) {
+          const int v = g + 8 * q;
+          if (v < pv) dot = f4_dot(e[q], __ldg(N4 + (size_t)jj * pv + v), dot);
+        }
+      }
+      dot += __shfl_xor_sync(FULL, dot, 4);
+      dot += __shfl_xor_sync(FULL, dot, 2);
+      dot += __shfl_xor_sync(FULL, dot, 1);
+      xn[t] = (t < c) ? fmaf(__ldg(C + jj), xx, dot) : 0.f;
+    }
+    // residual with the updated atoms: y - D' x'
+#pragma unroll
+    for (int t = 0; t < SMAX; ++t) {
+      if (t >= cmax) break;
+      const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
+      if (t < c) {
+#pragma unroll
+        for (int q = 0; q < RV; ++q) {
+          const int v = g + 8 * q;
+          if (v < pv) y[q] = f4_fma(-xn[t], __ldg(N4 + (size_t)jj * pv + v), y[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RV; ++q) e2 = f4_dot(y[q], y[q], e2);
+    // lane g writes slots g and g + 8
+    float nx0 = 0.f, nx1 = 0.f;
+#pragma unroll
+    for (int t = 0; t < SMAX; ++t) {
+      if (t == g) nx0 = xn[t];
+      if (t == g + 8) nx1 = xn[t];
+    }
+    if (g < c) {
+      val[i * s + g] = nx0;
+      if (csc_val) {
+        const int64_t o = colptr[i] + g;
+        if (csc_rowidx) csc_rowidx[o] = j0;
+        csc_val[o] = nx0;
+      }
+    }
+    if (SMAX > 8 && g + 8 < c) {
+      val[i * s + g + 8] = nx1;
+      if (csc_val) {
+        const int64_t o = colptr[i] + g + 8;
+        if (csc_rowidx) csc_rowidx[o] = j1;
+        csc_val[o] = nx1;
+      }
+    }
+  }
+  const double se = block_sum_d((double)e2, red);
+  if (threadIdx.x == 0) epart[blockIdx.x] = se;
+}
+
+// U = sum of the partial slices, float4 columns (len % 4 == 0): 8 slice
+// groups per column in a CTA of 256 threads, then the 8 group sums in order
+// (deterministic).
+__global__ void __launch_bounds__(256) reduce4_kernel(const float4* __restrict__ Upart, int nslices,
+                                                      int len4, float4* __restrict__ U) {
+  __shared__ float4 part[8][32];
+  const int tx = threadIdx.x & 31, gs = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + tx;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (c < len4) {
+#pragma unroll 4
+    for (int b = gs; b < nslices; b += 8) {
+      const float4 v = Upart[(size_t)b * len4 + c];
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+  }
+  part[gs][tx] = acc;
+  __syncthreads();
+  if (gs == 0 && c < len4) {
+    float4 t = part[0][tx];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+      t.x += part[q][tx].x;
+      t.y += part[q][tx].y;
+      t.z += part[q][tx].z;
+      t.w += part[q][tx].w;
+    }
+    U[c] = t;
   }
 }
 
@@ -404,6 +654,15 @@ __global__ void csc_to_slots_kernel(const int64_t* __restrict__ colptr,
   cnt[i] = c;
 }
 
+cudaError_t reduce_slices(float* Upart, int nslices, int len, float* U, cudaStream_t st) {
+  if (len % 4 == 0)
+    reduce4_kernel<<<(len / 4 + 31) / 32, 256, 0, st>>>((const float4*)Upart, nslices, len / 4,
+                                                         (float4*)U);
+  else
+    reduce_kernel<<<(len + 255) / 256, 256, 0, st>>>(Upart, nslices, len, U);
+  return cudaGetLastError();
+}
+
 template <int PL>
 cudaError_t accum_t(const float* Y, int p, int64_t m, const float* D, int n, int s,
                     const int32_t* idx, const float* val, const int32_t* cnt, const JauWork& w,
@@ -421,10 +680,7 @@ cudaError_t accum_t(const float* Y, int p, int64_t m, const float* D, int n, int
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int len = n * p + n;
-  const int nslices = smem > 0 ? w.nb_accum : 1;
-  reduce_kernel<<<(len + 255) / 256, 256, 0, st>>>(w.Upart, nslices, len, w.U);
-  return cudaGetLastError();
+  return reduce_slices(w.Upart, smem > 0 ? w.nb_accum : 1, n * p + n, w.U, st);
 }
 
 }  // namespace
@@ -445,18 +701,63 @@ size_t jau_accum_smem(int p, int n) {
   return bytes <= 200u * 1024u ? bytes : 0;
 }
 int jau_accum_blocks(int p, int n, int mult) {
+  // float4 form: 4 (8) CTAs of 256 threads per SM
+  if (p % 4 == 0) return (mult >= 2 ? 8 : 4) * num_sms();
   // the shared-memory form runs 1 CTA per SM unless two partial slices fit on one SM
   if (jau_accum_smem(p, n) > 0)
     return (mult >= 2 && jau_accum_smem(p, n) <= 100u * 1024u) ? 2 * num_sms() : num_sms();
   return (mult >= 2 ? 8 : 4) * num_sms();
 }
-int jau_accum_blocks_max(int p, int n) { return jau_accum_smem(p, n) > 0 ? 2 * num_sms() : 8 * num_sms(); }
+int jau_accum_blocks_max(int p, int n) {
+  return (p % 4 != 0 && jau_accum_smem(p, n) > 0) ? 2 * num_sms() : 8 * num_sms();
+}
+bool jau_vec4(int p, const float* Y, const float* D) {
+  return p % 4 == 0 && ((uintptr_t)Y % 16) == 0 && ((uintptr_t)D % 16) == 0;
+}
+int jau_launches(int p, const float* Y, const float* D) {
+  // accumulate (+ slice reduction unless the float4 form) + atoms + rows + finalize
+  return jau_vec4(p, Y, D) ? 4 : 5;
+}
 int jau_row_blocks(int per_sm) { return (per_sm == 2 || per_sm == 8 ? per_sm : 4) * num_sms(); }
 int jau_row_blocks_max() { return 8 * num_sms(); }
 
 cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int n, int s,
                            const int32_t* idx, const float* val, const int32_t* cnt,
                            const JauWork& w, int* err, cudaStream_t st) {
+  if (jau_vec4(p, Y, D)) {
+    cudaError_t e = cudaMemsetAsync(w.U, 0, sizeof(float) * ((size_t)n * p + n), st);
+    if (e != cudaSuccess) return e;
+#define DL_ACC4(RV, SM)                                                                          \
+  accum4_kernel<RV, SM><<<w.nb_accum, ACC4_THREADS, 0, st>>>(Y, p, m, D, n, s, idx, val, cnt, w.U, \
+                                                             w.epart_a, err)
+#define DL_ACC4_S(RV) \
+  if (s <= 8) DL_ACC4(RV, 8); else DL_ACC4(RV, 16)
+    if (p <= 32) { DL_ACC4_S(1); }
+    else if (p <= 64) { DL_ACC4_S(2); }
+    else if (p <= 96) { DL_ACC4_S(3); }
+    else { DL_ACC4_S(4); }
+#undef DL_ACC4_S
+#undef DL_ACC4
+    return cudaGetLastError();
+  }
+  if (p % 4 == 0) {
+    // unaligned operands: scalar form with global atomics and w.nb_accum CTAs
+    cudaError_t e = cudaMemsetAsync(w.Upart, 0, sizeof(float) * ((size_t)n * p + n), st);
+    if (e != cudaSuccess) return e;
+#define DL_ACCG(PL)                                                                          \
+  accum_kernel<PL, false><<<w.nb_accum, ACC_THREADS, 0, st>>>(Y, p, m, D, n, s, idx, val, cnt, \
+                                                              w.Upart, w.epart_a, err)
+    if (p <= 32) DL_ACCG(4);
+    else if (p <= 64) DL_ACCG(8);
+    else if (p <= 96) DL_ACCG(12);
+    else DL_ACCG(16);
+#undef DL_ACCG
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int len = n * p + n;
+    reduce_kernel<<<(len + 255) / 256, 256, 0, st>>>(w.Upart, 1, len, w.U);
+    return cudaGetLastError();
+  }
   if (p <= 32) return accum_t<4>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
   if (p <= 64) return accum_t<8>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
   if (p <= 96) return accum_t<12>(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
@@ -480,6 +781,20 @@ cudaError_t jau_rows(const float* Y, int p, int64_t m, const float* D, int n, in
 #define DL_ROWS(PL)                                                                              \
   rows_kernel<PL><<<nb, ROW_THREADS, 0, st>>>(Y, p, m, D, w.Dn, w.C, s, idx, val, cnt, colptr, \
                                               csc_rowidx, csc_val, w.epart_b)
+  if (jau_vec4(p, Y, D)) {
+#define DL_ROWS4(RV, SM)                                                                         \
+  rows4_kernel<RV, SM><<<nb, ROW_THREADS, 0, st>>>(Y, p, m, D, w.Dn, w.C, s, idx, val, cnt, colptr, \
+                                                   csc_rowidx, csc_val, w.epart_b)
+#define DL_ROWS4_S(RV) \
+  if (s <= 8) DL_ROWS4(RV, 8); else DL_ROWS4(RV, 16)
+    if (p <= 32) { DL_ROWS4_S(1); }
+    else if (p <= 64) { DL_ROWS4_S(2); }
+    else if (p <= 96) { DL_ROWS4_S(3); }
+    else { DL_ROWS4_S(4); }
+#undef DL_ROWS4_S
+#undef DL_ROWS4
+    return cudaGetLastError();
+  }
   if (p <= 32) DL_ROWS(4);
   else if (p <= 64) DL_ROWS(8);
   else if (p <= 96) DL_ROWS(12);

@@ -17,8 +17,8 @@
 //
 // Lane l of the warp holds alpha[32t + l], t < NT = ceil(n/32), as NT/2 float2
 // pairs (elements t = 2v, 2v+1) so the updates issue as packed FP32x2 FMAs
-// (__ffma2_rn, sm_100 family); the u vectors live in registers (small n*s) or
-// in shared memory.  Selected atoms are masked by setting their alpha to NaN,
+// (__ffma2_rn, sm_100 family); the first NR u vectors live in registers, the
+// rest in shared memory (see reg_us).  Selected atoms are masked by setting their alpha to NaN,
 // which the argmax ignores.
 #include "dl_internal.cuh"
 
@@ -143,10 +143,11 @@ struct GramRestricted {
 
 // One signal, one warp: the whole OMP of signal i (see the file header).
 // a0row: its correlations (element j, j < n); y: the signal; L, C: this warp's
-// shared-memory Cholesky rows and 1/L_qq; u_s: its shared u vectors (SMEM_U).
+// shared-memory Cholesky rows and 1/L_qq; u_q for q < NR live in registers,
+// the others in u_s (this warp's shared-memory slice).
 // Outputs slots i*s.. (atom index = idxmap[j] when idxmap is given), the count,
 // and the residual-energy estimate ||y||^2 - sum z^2 in ores[i] when given.
-template <int NT, int SMAX, bool SMEM_U, bool FULLN, class GSrc>
+template <int NT, int SMAX, int NR, bool FULLN, class GSrc>
 __device__ __forceinline__ void omp_one(
     int64_t i, const GSrc& gsrc, float (&L)[SMAX][SMAX], float (&C)[SMAX], float2* u_s,
     const float* __restrict__ a0row, int n, const float* __restrict__ y, int p, int s,
@@ -160,9 +161,11 @@ __device__ __forceinline__ void omp_one(
   constexpr unsigned TMASK = (1u << TB) - 1u;
   constexpr unsigned VMASK = 0x7FFFFFFFu & ~TMASK;
 
+  static_assert(NR >= 0 && NR <= NPHI, "register u vectors");
   const int lane = threadIdx.x & 31;
-  float2 u_r[SMEM_U ? 1 : NPHI][SMEM_U ? 1 : NV];
-#define UV(q, v) (*(SMEM_U ? &u_s[((q) * NV + (v)) * 32 + lane] : &u_r[SMEM_U ? 0 : (q)][SMEM_U ? 0 : (v)]))
+  float2 u_r[NR > 0 ? NR : 1][NV];
+#define UV(q, v) \
+  (*((q) >= NR ? &u_s[(((q) - NR) * NV + (v)) * 32 + lane] : &u_r[(q) < NR ? (q) : 0][(v)]))
 
   // ||y||^2 for the residual stop rule and the non-finite check
   float yy = 0.f;
@@ -313,9 +316,10 @@ __device__ __forceinline__ void omp_one(
     ocnt[i] = k;
     if (ores) ores[i] = rr;
   }
+
 }
 
-template <int NT, int SMAX, bool SMEM_U, bool FULLN>
+template <int NT, int SMAX, int NR, bool FULLN>
 __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
     const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
@@ -328,11 +332,10 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
   const int wib = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   if (i >= m) return;
-  float2* u_s = SMEM_U ? smem_u + (size_t)wib * NPHI * (NT / 2) * 32 : nullptr;
+  float2* u_s = NR < NPHI ? smem_u + (size_t)wib * (NPHI - NR) * (NT / 2) * 32 : nullptr;
   const GramGlobal<FULLN> gsrc{G, n};
-  omp_one<NT, SMAX, SMEM_U, FULLN>(i, gsrc, Lsh[wib], Csh[wib], u_s, A0 + i * lda, n, Y + i * p, p,
-                                   s, nullptr, oidx, oval, ocnt, ores, err, rs_list, rs_count,
-                                   rs_cap);
+  omp_one<NT, SMAX, NR, FULLN>(i, gsrc, Lsh[wib], Csh[wib], u_s, A0 + i * lda, n, Y + i * p, p,
+                                s, nullptr, oidx, oval, ocnt, ores, err, rs_list, rs_count, rs_cap);
 }
 
 // OMP restricted to K proposed candidates per signal (cand: m x K, ascending):
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_restricted_kernel(
   a0sh[wib][lane] = a;
   __syncwarp();
   const GramRestricted gsrc{G, n, ci, K};
-  omp_one<2, SMAX, false, false>(i, gsrc, Lsh[wib], Csh[wib], nullptr, a0sh[wib], K, y, p, s, ci,
+  omp_one<2, SMAX, (SMAX > 1 ? SMAX - 1 : 1), false>(i, gsrc, Lsh[wib], Csh[wib], nullptr, a0sh[wib], K, y, p, s, ci,
                                  oidx, oval, ocnt, ores, err, nullptr, nullptr, 0);
   __syncwarp();
   if (lane == 0 && fb_count && ores[i] > tol2 * ref_res[i]) {
@@ -390,51 +393,60 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_listed_kernel(
   for (int e = blockIdx.x * (blockDim.x >> 5) + wib; e < total; e += nw) {
     const int64_t i = list[e];
     const GramGlobal<false> gsrc{G, n};
-    omp_one<NT, SMAX, false, false>(i, gsrc, Lsh[wib], Csh[wib], nullptr, A0 + i * lda, n, Y + i * p,
+    omp_one<NT, SMAX, (SMAX > 1 ? SMAX - 1 : 1), false>(i, gsrc, Lsh[wib], Csh[wib], nullptr, A0 + i * lda, n, Y + i * p,
                                     p, s, nullptr, oidx, oval, ocnt, ores, err, rs_list, rs_count,
                                     rs_cap);
     __syncwarp();
   }
 }
 
-template <int NT, int SMAX, bool SMEM, bool FULLN>
+template <int NT, int SMAX, int NR, bool FULLN>
 cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                      int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                     int* rs_list, int* rs_count, int rs_cap, int warps_hint, float* ores, cudaStream_t st) {
+                     int* rs_list, int* rs_count, int rs_cap, int warps_hint, float* ores,
+                     cudaStream_t st) {
+  constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
   int warps = (warps_hint >= 1 && warps_hint <= OMP_THREADS / 32) ? warps_hint : OMP_THREADS / 32;
   size_t smem = 0;
-  if (SMEM) {
-    const size_t per_warp = (size_t)(SMAX - 1) * (NT / 2) * 32 * sizeof(float2);
+  if (NR < NPHI) {
+    const size_t per_warp = (size_t)(NPHI - NR) * (NT / 2) * 32 * sizeof(float2);
     const int cap = (int)((190u * 1024u) / per_warp);
     if (warps > cap) warps = cap;
     if (warps < 1) warps = 1;
     smem = per_warp * warps;
-    cudaFuncSetAttribute(omp_warp_kernel<NT, SMAX, SMEM, FULLN>,
+    cudaFuncSetAttribute(omp_warp_kernel<NT, SMAX, NR, FULLN>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   } else {  // Gram rows are re-read through L1: give L1 the shared-memory carveout
-    cudaFuncSetAttribute(omp_warp_kernel<NT, SMAX, SMEM, FULLN>,
+    cudaFuncSetAttribute(omp_warp_kernel<NT, SMAX, NR, FULLN>,
                          cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
   }
   const int64_t blocks = (m + warps - 1) / warps;
-  omp_warp_kernel<NT, SMAX, SMEM, FULLN><<<(unsigned)blocks, warps * 32, smem, st>>>(
+  omp_warp_kernel<NT, SMAX, NR, FULLN><<<(unsigned)blocks, warps * 32, smem, st>>>(
       A0, lda, G, n, Y, p, m, s, idx, val, cnt, ores, err, rs_list, rs_count, rs_cap);
   return cudaGetLastError();
 }
 
-// register budget: alpha + the u vectors must stay well inside 255 registers
+// How many u vectors stay in registers.  With 16 alpha elements per lane
+// (n <= 512) keeping all of them caps the kernel near 168 registers (12 warps
+// per SM); three in registers and the rest in shared memory gives ~126
+// registers and 16 warps per SM, which hides more of the Gram-row latency
+// (measured 8% faster at n = 512, s = 8).  Otherwise: all in registers while
+// alpha + u fit (NT*(SMAX-1) <= 128 floats), else all in shared memory.
 template <int NT, int SMAX>
-constexpr bool fits_regs() {
-  return NT * (SMAX - 1) <= 128;
+constexpr int reg_us() {
+  constexpr int nphi = SMAX > 1 ? SMAX - 1 : 1;
+  if (NT == 16 && nphi > 3) return 3;
+  return NT * (SMAX - 1) <= 128 ? nphi : 0;
 }
 
 template <int NT, int SMAX>
 cudaError_t pick_store(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                        int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
                        int* rl, int* rc, int rcap, int wh, float* ores, cudaStream_t st) {
-  constexpr bool SM = !fits_regs<NT, SMAX>();
+  constexpr int NR = reg_us<NT, SMAX>();
   if (n == 32 * NT)
-    return launch_t<NT, SMAX, SM, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
-  return launch_t<NT, SMAX, SM, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+    return launch_t<NT, SMAX, NR, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+  return launch_t<NT, SMAX, NR, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
 }
 
 template <int NT>
