@@ -108,6 +108,9 @@ struct dl_ctx {
   int cfg_acc_mult = 1;   // accumulation CTAs: 1x or 2x the base count
   int cfg_row_per_sm = 4; // row-update CTAs per SM
   int cfg_corr_tc = 1;    // tensor-core correlations when the shape allows
+  // side stream: the colptr scan overlaps the first pass of the atom update
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // optional per-phase timing with CUDA events recorded on the context's stream
   bool prof = false;
   cudaEvent_t ev[9] = {};
@@ -132,6 +135,9 @@ void free_ctx(dl_ctx* c) {
     if (q) cudaFree(q);
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->st2) cudaStreamDestroy(c->st2);
   void* ptrs[] = {c->G, c->A0, c->Dhi, c->Dlo, c->Ylp, c->Ysc, c->Dlp, c->Dsc, c->rs_list,
                   c->rs_count, c->rs_scratch, c->sidx, c->sval, c->scnt, c->bsum, c->err, c->iter, c->rmse,
                   c->jw.Upart, c->jw.U, c->jw.epart_a, c->jw.epart_b, c->jw.Dn, c->jw.C,
@@ -316,8 +322,9 @@ cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s)
   return e;
 }
 
+// join: when given, colptr is produced on the side stream and the row pass waits for it.
 cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const int64_t* colptr,
-                    int32_t* rowidx_out, float* val_out) {
+                    int32_t* rowidx_out, float* val_out, cudaEvent_t join) {
   c->jw.nb_accum = dlk::jau_accum_blocks(c->p, c->n, c->cfg_acc_mult);
   c->jw.nb_row = dlk::jau_row_blocks(c->cfg_row_per_sm);
   c->jau_kernels = dlk::jau_launches(c->p, Y, D);
@@ -329,14 +336,12 @@ cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const
   e = dlk::jau_atoms(D, c->p, c->n, c->jw, c->st);
   if (e != cudaSuccess) return e;
   mark(c, 6);
+  if (join && (e = cudaStreamWaitEvent(c->st, join, 0)) != cudaSuccess) return e;
   e = dlk::jau_rows(Y, c->p, m, D, c->n, s, c->sidx, c->sval, c->scnt, c->jw, colptr, rowidx_out,
                     val_out, c->st);
   if (e != cudaSuccess) return e;
   mark(c, 7);
-  e = dlk::jau_finalize(c->jw, c->rmse, c->iter, c->st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(D, c->jw.Dn, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyDeviceToDevice,
-                      c->st);
+  e = dlk::jau_finalize(c->jw, c->rmse, c->iter, D, c->n, c->p, c->st);
   mark(c, 8);
   return e;
 }
@@ -345,9 +350,13 @@ cudaError_t enq_iteration(dl_ctx* c, const float* Y, int64_t m, float* D, int s,
                           int32_t* rowidx, float* val) {
   cudaError_t e = enq_omp(c, Y, m, D, s);
   if (e != cudaSuccess) return e;
-  e = dlk::counts_to_colptr(c->scnt, m, c->bsum, colptr, c->st);
+  // colptr scan on the side stream, concurrent with the accumulation and the atom update
+  if ((e = cudaEventRecord(c->ev_fork, c->st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(c->st2, c->ev_fork, 0)) != cudaSuccess) return e;
+  e = dlk::counts_to_colptr(c->scnt, m, c->bsum, colptr, c->st2);
   if (e != cudaSuccess) return e;
-  return enq_jau(c, Y, m, D, s, colptr, rowidx, val);
+  if ((e = cudaEventRecord(c->ev_join, c->st2)) != cudaSuccess) return e;
+  return enq_jau(c, Y, m, D, s, colptr, rowidx, val, c->ev_join);
 }
 
 int64_t proposer_chunks(dl_proposer* P, int64_t m);
@@ -417,6 +426,9 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
             dalloc(&c->jw.C, (size_t)n) && dalloc(&c->Dhi, (size_t)n * p) &&
             dalloc(&c->Dlo, (size_t)n * p) && dalloc(&c->rs_list, mm) && dalloc(&c->rs_count, 1) &&
             dalloc(&c->rs_scratch, (size_t)dlk::DL_RESOLVE_WARPS * (dlk::DL_RESOLVE_SMAX + 1) * n);
+  ok = ok && cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
   if (ok && precision != DL_FP32) {
     c->lp_kind = precision == DL_BF16 ? dlk::LP_BF16 : dlk::LP_E4M3;
     const size_t esz = precision == DL_BF16 ? 2 : 1;
@@ -602,7 +614,7 @@ int jau_update(dl_ctx* c, const float* Y, int64_t m, float* D, const int64_t* co
   }
   DL_CHECK(cudaMemsetAsync(c->iter, 0, sizeof(int), c->st));
   DL_CHECK(dlk::csc_to_slots(dcp, dri, dv, m, c->n, s, c->sidx, c->sval, c->scnt, c->err, c->st));
-  DL_CHECK(enq_jau(c, dY, m, dD, s, dcp, nullptr, dv));
+  DL_CHECK(enq_jau(c, dY, m, dD, s, dcp, nullptr, dv, nullptr));
   c->launches += 1 + c->jau_kernels;
   if (kind == 0) {
     DL_CHECK(cudaMemcpyAsync(D, dD, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyDeviceToHost, c->st));

@@ -119,7 +119,9 @@ cudaError_t jau_rows(const float* Y, int p, int64_t m, const float* D, int n, in
                      const int32_t* idx, float* val, const int32_t* cnt, const JauWork& w,
                      const int64_t* colptr, int32_t* csc_rowidx, float* csc_val, cudaStream_t st);
 // rmse_out[2*(*iter)] / [2*(*iter)+1] from the partials, then ++*iter (device counter).
-cudaError_t jau_finalize(const JauWork& w, double* rmse_out, int* iter, cudaStream_t st);
+// RMSE before/after into rmse_out[2*iter..], iter += 1, and D = Dn (updated atoms).
+cudaError_t jau_finalize(const JauWork& w, double* rmse_out, int* iter, float* D, int n, int p,
+                         cudaStream_t st);
 
 // ---- CSC <-> slots --------------------------------------------------------------
 int64_t scan_blocks(int64_t m);

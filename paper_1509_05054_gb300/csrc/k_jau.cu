@@ -529,10 +529,19 @@ __global__ void __launch_bounds__(ROW_THREADS) rows_kernel(
 
 // One block: strided partial sums in a fixed order, then a fixed-order tree.
 constexpr int FIN_THREADS = 256;
+// Block 0: the RMSE before and after the update from the partial sums; the
+// other blocks copy the updated atoms Dn into D.
 __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(
     const double* __restrict__ epa, int na, const double* __restrict__ epb, int nb,
-    double* __restrict__ rmse, int* __restrict__ iter) {
+    double* __restrict__ rmse, int* __restrict__ iter, const float* __restrict__ Dn,
+    float* __restrict__ D, int64_t np) {
   __shared__ double red[FIN_THREADS / 32];
+  if (blockIdx.x > 0) {
+    const int64_t stride = (int64_t)(gridDim.x - 1) * blockDim.x;
+    for (int64_t q = (int64_t)(blockIdx.x - 1) * blockDim.x + threadIdx.x; q < np; q += stride)
+      D[q] = Dn[q];
+    return;
+  }
   double ee = 0.0, yy = 0.0, e2 = 0.0;
   for (int b = threadIdx.x; b < na; b += FIN_THREADS) {
     ee += epa[2 * b];
@@ -803,8 +812,13 @@ cudaError_t jau_rows(const float* Y, int p, int64_t m, const float* D, int n, in
   return cudaGetLastError();
 }
 
-cudaError_t jau_finalize(const JauWork& w, double* rmse_out, int* iter, cudaStream_t st) {
-  finalize_kernel<<<1, FIN_THREADS, 0, st>>>(w.epart_a, w.nb_accum, w.epart_b, w.nb_row, rmse_out, iter);
+cudaError_t jau_finalize(const JauWork& w, double* rmse_out, int* iter, float* D, int n, int p,
+                         cudaStream_t st) {
+  const int64_t np = (int64_t)n * p;
+  int64_t cb = (np + FIN_THREADS - 1) / FIN_THREADS;
+  if (cb > 64) cb = 64;
+  finalize_kernel<<<(unsigned)(1 + cb), FIN_THREADS, 0, st>>>(w.epart_a, w.nb_accum, w.epart_b,
+                                                              w.nb_row, rmse_out, iter, w.Dn, D, np);
   return cudaGetLastError();
 }
 
