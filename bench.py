@@ -155,6 +155,22 @@ def physical_gpu_index(local_rank: int) -> int:
     return local_rank
 
 
+# ---------------------------------------------------------------- ranks
+def max_over_ranks(x, pg=None, device="cuda"):
+    """The maximum of a per-rank float over all ranks (x itself without a group)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # ---------------------------------------------------------------- CPU oracle
 def cpu_oracle_steps(Y, D, s, steps, warmup=0):
     """Time the FP64 oracle's DL iteration (OMP + JAU) on the given signals."""
@@ -253,11 +269,7 @@ def run_ours(args):
         st.synchronize()
         launches = dl.dl_kernel_launches(ctx) - launches0
         barrier()
-        total_ms = sum(a.elapsed_time(b) for a, b in ev)
-        if pg:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), pg)
         # per-phase kernel durations with CUDA events on the context's stream
         dl.dl_set_profiling(ctx, True)
         with torch.cuda.stream(st):
@@ -272,7 +284,7 @@ def run_ours(args):
         rm = np.zeros(2 * RMSE_ITERS)
         dl.dl_iterate(ctx, Yd, m, Dq, s, RMSE_ITERS, colptr, rowidx, val, rm)
         resolved = dl.dl_last_resolved(ctx)
-        return ctx, {"value": world * m * args.steps / (total_ms * 1e-3),
+        return ctx, {"value": job_throughput(world, m * args.steps, total_ms * 1e-3),
                      "ms_per_step": total_ms / args.steps, "gpu_launches": launches,
                      "phases_ms": phases, "rmse": rm.reshape(RMSE_ITERS, 2).tolist(),
                      "final_rmse": float(rm[-1]), "fp64_resolved_last_pass": resolved}
@@ -350,13 +362,9 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             dl.dl_iterate(ctx, Yh, m, Dh, s, 1, cph, rih, vh, rmh)
-        dt = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0, pg)
         nnz = int(cph[m])
-        e2e = {"value": world * m * args.e2e_steps / dt, "unit": UNIT,
+        e2e = {"value": job_throughput(world, m * args.e2e_steps, dt), "unit": UNIT,
                "h2d_bytes_per_step": 4 * m * p + 4 * n * p,
                "d2h_bytes_per_step": 4 * n * p + 8 * (m + 1) + 8 * nnz + 16 + 4,
                "steps": args.e2e_steps}
