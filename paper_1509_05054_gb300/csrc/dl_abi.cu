@@ -54,6 +54,7 @@ struct dl_ctx {
   float* G = nullptr;
   float* A0 = nullptr;
   int jau_kernels = 5;   // kernel launches of the last enqueued JAU update
+  int omp_kernels[2] = {5, 5};  // ... of the last enqueued coding pass (plain, learned)
   float* Dhi = nullptr;  // TF32 head / tail of D for the tensor-core correlations
   float* Dlo = nullptr;
   // reduced-precision correlations (precision DL_BF16 / DL_FP8)
@@ -120,7 +121,6 @@ struct dl_ctx {
 
 namespace {
 
-constexpr int kKernelsOmp = 5;       // split, gram, correlations, omp, FP64 re-solve
 constexpr int kKernelsScan = 2;      // colptr scan
 
 void free_ctx(dl_ctx* c) {
@@ -274,11 +274,14 @@ cudaError_t enq_corr(dl_ctx* c, const float* Y, int64_t m, const float* D, bool 
 
 cudaError_t enq_proposer_forward(dl_proposer* P, const void* Xbf, int64_t m, int K, int32_t* cand,
                                  cudaStream_t st);
+int64_t proposer_chunks(dl_proposer* P, int64_t m);
 
 // Sparse coding with the learned proposer: top-K candidates from the MLP,
 // OMP restricted to them, full OMP for the signals whose residual energy
 // exceeds tol2 times the one of their last full OMP.
 cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D, int s, bool tc) {
+  c->omp_kernels[1] = (tc ? 2 : 1) /* Gram */ + 4 * (int)proposer_chunks(c->prop, m) /* 3 GEMMs +
+      top-K per chunk */ + 3 /* restricted, listed, FP64 */ + (lp_ok(c) ? 2 : 1) /* correlations */;
   cudaError_t e = enq_proposer_forward(c->prop, c->Ybf, m, c->prop_K, c->cand, c->st);
   if (e != cudaSuccess) return e;
   mark(c, 2);
@@ -302,13 +305,24 @@ cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D
 
 cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
   const bool tc = tc_ok(c, Y, D);
+  const bool learned = c->prop && c->learned_now;
   mark(c, 0);
-  cudaError_t e = enq_gram(c, D, tc);
-  if (e != cudaSuccess) return e;
-  mark(c, 1);
-  if (c->prop && c->learned_now) return enq_omp_learned(c, Y, m, D, s, tc);
-  e = enq_corr(c, Y, m, D, tc);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (tc && !learned && !lp_ok(c)) {
+    // one launch computes the Gram matrix and the correlations of all signals
+    if ((e = dlk::split_tf32(D, (int64_t)c->n * c->p, c->Dhi, c->Dlo, c->st)) != cudaSuccess) return e;
+    mark(c, 1);
+    e = dlk::corr_tf32x3_pair(Y, m, c->A0, c->lda, D, c->n, c->G, c->n, c->Dhi, c->Dlo, c->n, c->p,
+                              c->err, c->st);
+    if (e != cudaSuccess) return e;
+    c->omp_kernels[0] = 2 /* split, products */ + 2 /* OMP, FP64 re-solve */;
+  } else {
+    if ((e = enq_gram(c, D, tc)) != cudaSuccess) return e;
+    mark(c, 1);
+    if (learned) return enq_omp_learned(c, Y, m, D, s, tc);
+    if ((e = enq_corr(c, Y, m, D, tc)) != cudaSuccess) return e;
+    c->omp_kernels[0] = (tc ? 2 : 1) + (lp_ok(c) ? 2 : 1) + 2;
+  }
   mark(c, 2);
   e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st);
   if (e != cudaSuccess) return e;
@@ -359,19 +373,10 @@ cudaError_t enq_iteration(dl_ctx* c, const float* Y, int64_t m, float* D, int s,
   return enq_jau(c, Y, m, D, s, colptr, rowidx, val, c->ev_join);
 }
 
-int64_t proposer_chunks(dl_proposer* P, int64_t m);
-
 // Kernels one DL iteration enqueues (the claim behind dl_kernel_launches).
-int64_t kernels_per_iteration(dl_ctx* c, bool learned, int64_t m) {
-  const bool tc = dlk::corr_tc_supported(nullptr, c->p, c->n, c->lda) && c->cfg_corr_tc &&
-                  !getenv("DL_FORCE_SIMT_GEMM");
-  int64_t k = (tc ? 2 : 1) /* split + Gram */ + kKernelsScan + c->jau_kernels;
-  if (learned)
-    k += 4 * proposer_chunks(c->prop, m) /* 3 GEMMs + top-K */ + 3 /* restricted, listed, FP64 */ +
-         (c->lp_kind ? 2 : 1) /* correlations for the fallback */;
-  else
-    k += (c->lp_kind ? 2 : 1) /* correlations */ + 2 /* OMP, FP64 re-solve */;
-  return k;
+// The counts are recorded when the pass is enqueued (eagerly or into a graph).
+int64_t kernels_per_iteration(dl_ctx* c, bool learned) {
+  return c->omp_kernels[learned ? 1 : 0] + kKernelsScan + c->jau_kernels;
 }
 
 int check_common(dl_ctx* c, int64_t m) {
@@ -564,11 +569,12 @@ int omp_code(dl_ctx* c, const float* Y, int64_t m, const float* D, int s, int64_
     dv = c->hval;
   }
   DL_CHECK(enq_convert_y(c, dY, m));
+  if (lp_ok(c)) c->launches += 1;
   c->learned_now = false;
   DL_CHECK(enq_omp(c, dY, m, dD, s));
   DL_CHECK(dlk::counts_to_colptr(c->scnt, m, c->bsum, dcp, c->st));
   DL_CHECK(dlk::slots_to_csc(c->sidx, c->sval, c->scnt, m, s, dcp, dri, dv, c->st));
-  c->launches += kKernelsOmp + kKernelsScan + 1;
+  c->launches += c->omp_kernels[0] + kKernelsScan + 1;
   if (kind == 0) {
     DL_CHECK(cudaMemcpyAsync(colptr, dcp, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyDeviceToHost, c->st));
     DL_CHECK(cudaStreamSynchronize(c->st));
@@ -670,6 +676,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
   const bool can_graph = c->st != nullptr && m > 0;
   DL_CHECK(enq_convert_y(c, dY, m));
   if (c->prop) DL_CHECK(dlk::to_lowp(dlk::LP_BF16, dY, m, c->p, c->Ybf, nullptr, c->st));
+  c->launches += (lp_ok(c) ? 1 : 0) + (c->prop ? 1 : 0);  // the per-call conversions of Y
   for (int it = 0; it < iters; ++it) {
     const bool learned = c->prop && (c->prop_counter % c->prop_full_every) != 0;
     c->learned_now = learned;
@@ -695,7 +702,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
       DL_CHECK(enq_iteration(c, dY, m, dD, s, dcp, dri, dv));
       seen++;
     }
-    c->launches += kernels_per_iteration(c, learned, m);
+    c->launches += kernels_per_iteration(c, learned);
     if (c->prop) c->prop_counter++;
     c->learned_now = false;
     if (c->prof) {
@@ -949,7 +956,7 @@ extern "C" int dl_batch_iterate(dl_batch* b, int iters, double* rmse) {
     b->graph_iters = iters;
   }
   DL_CHECK(cudaGraphLaunch(b->gexec, b->main));
-  for (dl_ctx* c : b->ctxs) c->launches += (int64_t)iters * (kKernelsOmp + kKernelsScan + c->jau_kernels);
+  for (dl_ctx* c : b->ctxs) c->launches += (int64_t)iters * (c->omp_kernels[0] + kKernelsScan + c->jau_kernels);
   if (rmse) {
     DL_CHECK(cudaStreamSynchronize(b->main));
     for (int k = 0; k < b->count; ++k)

@@ -28,6 +28,11 @@ bool corr_tc_supported(const float* A, int p, int n, int64_t ldc);
 cudaError_t split_tf32(const float* B, int64_t count, float* hi, float* lo, cudaStream_t st);
 cudaError_t corr_tf32x3(const float* A, int64_t rows_a, const float* Bhi, const float* Blo, int n,
                         int p, float* C, int64_t ldc, int* err, cudaStream_t st);
+// Two products with the same B in one launch: C0 = A0 B^T and C1 = A1 B^T (A1 may be null).
+cudaError_t corr_tf32x3_pair(const float* A0, int64_t rows0, float* C0, int64_t ldc0,
+                             const float* A1, int64_t rows1, float* C1, int64_t ldc1,
+                             const float* Bhi, const float* Blo, int n, int p, int* err,
+                             cudaStream_t st);
 
 // Reduced-precision correlations (k_corr_lp.cu): operands converted to padded
 // row-major BF16 or E4M3 (+ inverse row scales) buffers, then tcgen05 MMAs.

@@ -2,6 +2,8 @@
 //   C[i][j] = sum_r A[i][r] * B[j][r]
 // with A the signals Y (alpha0 = D^T y for every signal, Algorithm 1 step 1)
 // or the atoms D (the Gram matrix G = D^T D of Batch-OMP), and B the atoms D.
+// One launch can compute two such products with the same B (the correlations
+// of all signals and the Gram matrix of a DL iteration).
 //
 // Split-TF32 ("3xTF32") arithmetic: every operand is split into a TF32 head
 // and a TF32 tail, a = a_hi + a_lo with a_hi = rna_tf32(a), a_lo = a - a_hi;
@@ -9,20 +11,22 @@
 // The dropped A_lo B_lo term and the TF32 rounding of the tails leave a
 // relative error near 2^-21 per product, i.e. FP32 accuracy.
 //
-// The output is a grid of units (128-row tile t, 128-column block nb); the
-// units are dealt to a persistent grid (one CTA per SM) in contiguous ranges,
-// so a CTA walks its tiles block by block.  Warp roles, 256 threads:
-//   * warps 4-7 (producer group): on a tile change, TMA the A tile (128 rows x
-//     64 K, SWIZZLE_128B) and split it in place into A_hi / A_lo; thread 128
-//     keeps a two-slot ring of pre-split B blocks (TMA, one unit ahead) and
-//     issues 3 x (K/8) tcgen05.mma kind::tf32 (M=128, N=128, K=8) per unit
-//     into one of four 128-column TMEM accumulators;
+// Work split: the columns of C are cut into blocks of 128 atoms; CTA c owns
+// block c % nq (nq = ceil(n/128)) and keeps that block's pre-split B (head and
+// tail, 64 KB at p <= 64) resident in shared memory for its whole life; the
+// CTAs owning a block share out the 128-row tiles of A (both products' tiles
+// in one list).  Warp roles, 256 threads:
+//   * warps 4-7 (producer group): thread 128 loads the B block once and keeps
+//     a two-slot ring of A tiles (TMA, SWIZZLE_128B, one tile ahead); the
+//     group splits each tile in place into A_hi / A_lo; thread 128 issues
+//     3 x (K/8) tcgen05.mma kind::tf32 (M=128, N=128, K=8) per tile into one of
+//     four 128-column TMEM accumulators;
 //   * warps 0-3 (epilogue): drain an accumulator with tcgen05.ld (warp w owns
 //     TMEM lanes 32w..32w+31 = rows), stage 32x32 boxes in 128-byte-swizzled
 //     shared memory and write them with TMA stores (two boxes in flight per
 //     warp), then hand the accumulator back.
-// So the stores of one unit overlap the loads and MMAs of the next ones and
-// every global write is a full line.  Every wait on an mbarrier is bounded
+// A tiles stream in while the previous tile multiplies and older tiles drain,
+// and B is read from L2 once per CTA.  Every wait on an mbarrier is bounded
 // (2 s of %globaltimer); on timeout the kernel flags ERR_TIMEOUT, skips the
 // remaining work, frees its TMEM and returns.
 #include "dl_internal.cuh"
@@ -37,59 +41,58 @@ namespace {
 
 constexpr int WS_THREADS = 256;
 constexpr int TILE_M = 128;
-constexpr int UNIT_N = 128;  // columns per unit (MMA N)
-constexpr int KCHUNK = 32;   // floats per 128-byte swizzle row
+constexpr int BLOCK_N = 128;  // atoms per column block (MMA N)
+constexpr int KCHUNK = 32;    // floats per 128-byte swizzle row
 constexpr int TMEM_RING = 4;
-constexpr int BOX = 32;      // TMA store box: 32 rows x 32 floats
+constexpr int BOX = 32;       // TMA store box: 32 rows x 32 floats
 using namespace tc;
 // Instruction descriptor: kind::tf32, A/B TF32 K-major, D FP32, M = 128, N = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(UNIT_N >> 3) << 17) |
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BLOCK_N >> 3) << 17) |
                             ((uint32_t)(TILE_M >> 4) << 24);
 
 struct WsSmem {  // byte offsets from the 1024-aligned base
-  static constexpr size_t chunk_a = (size_t)TILE_M * KCHUNK * 4;  // 16 KB
-  static constexpr size_t chunk_b = (size_t)UNIT_N * KCHUNK * 4;  // 16 KB
-  static constexpr size_t a_hi = 0;
-  static constexpr size_t a_lo = 2 * chunk_a;
-  static constexpr size_t b0 = 4 * chunk_a;          // slot s: hi chunks, then lo chunks
-  static constexpr size_t b_slot = 4 * chunk_b;
-  static constexpr size_t stage = b0 + 2 * b_slot;   // 4 warps x 2 boxes
+  static constexpr size_t chunk = (size_t)TILE_M * KCHUNK * 4;  // 16 KB (= BLOCK_N * KCHUNK * 4)
+  static constexpr size_t b_hi = 0;                  // 2 chunks (K <= 64), then 2 tail chunks
+  static constexpr size_t b_lo = 2 * chunk;
+  static constexpr size_t a0 = 4 * chunk;            // slot s: 2 head chunks, then 2 tail chunks
+  static constexpr size_t a_slot = 4 * chunk;
+  static constexpr size_t stage = a0 + 2 * a_slot;   // 4 warps x 2 boxes
   static constexpr size_t box = (size_t)BOX * BOX * 4;
   static constexpr size_t bars = stage + 8 * box;
-  static constexpr size_t total = bars + 14 * 8 + 16;
+  static constexpr size_t total = bars + 13 * 8 + 16;
   static constexpr size_t dyn = total + 1024;
 };
 static_assert(WsSmem::dyn <= 232448, "shared memory budget");
 
 // barrier indices
-constexpr int B_AFULL = 0, B_AFREE = 1, B_BFULL = 2, B_BFREE = 4, B_TFULL = 6, B_TEMPTY = 10;
+constexpr int B_BFULL = 0, B_AFULL = 1, B_AFREE = 3, B_TFULL = 5, B_TEMPTY = 9;
 
 __device__ __forceinline__ void group_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
+// tiles0 tiles of product 0 (A0 -> C0, rows0 rows), then those of product 1.
 __global__ void __launch_bounds__(WS_THREADS, 1)
-    corr_tf32x3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
-                       const __grid_constant__ CUtensorMap tmBlo, const __grid_constant__ CUtensorMap tmC,
-                       int64_t rows_a, int n, int kb, int64_t units, int* __restrict__ err) {
+    corr_tf32x3_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+                       const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
+                       const __grid_constant__ CUtensorMap tmC0, const __grid_constant__ CUtensorMap tmC1,
+                       int64_t rows0, int64_t rows1, int64_t tiles0, int64_t tiles, int n, int kb,
+                       int nq, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(base + WsSmem::bars);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 14);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 13);
   volatile int* fail = (volatile int*)(tmem_slot + 1);
-  float* Ahi = (float*)(base + WsSmem::a_hi);
-  float* Alo = (float*)(base + WsSmem::a_lo);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int NB = (n + UNIT_N - 1) / UNIT_N;
-  const int64_t ubeg = units * blockIdx.x / gridDim.x;
-  const int nv = (int)(units * (blockIdx.x + 1) / gridDim.x - ubeg);
+  const int blk_n = blockIdx.x % nq;              // this CTA's column block
+  const int64_t gi = blockIdx.x / nq, groups = gridDim.x / nq;
+  const int nitems = gi < tiles ? (int)((tiles - 1 - gi) / groups + 1) : 0;
 
   if (threadIdx.x == 0) {
     *fail = 0;
-    mbar_init(&bars[B_AFULL], 1);
-    mbar_init(&bars[B_AFREE], 1);
+    mbar_init(&bars[B_BFULL], 1);
     for (int q = 0; q < 2; ++q) {
-      mbar_init(&bars[B_BFULL + q], 1);
-      mbar_init(&bars[B_BFREE + q], 1);
+      mbar_init(&bars[B_AFULL + q], 1);
+      mbar_init(&bars[B_AFREE + q], 1);
     }
     for (int q = 0; q < TMEM_RING; ++q) {
       mbar_init(&bars[B_TFULL + q], 1);
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(TMEM_RING * UNIT_N)
+                 "r"(TMEM_RING * BLOCK_N)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -113,67 +116,69 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     // ---------------- producer group ----------------
     const int pt = threadIdx.x - 128;
     const bool leader = pt == 0;
-    auto bslot = [&](int slot) { return base + WsSmem::b0 + slot * WsSmem::b_slot; };
-    auto load_b = [&](int v) {
-      const int slot = v & 1, nb = (int)((ubeg + v) % NB);
-      uint8_t* bs = bslot(slot);
-      mbar_expect_tx(&bars[B_BFULL + slot], (uint32_t)(2 * kb * WsSmem::chunk_b));
-      for (int q = 0; q < kb; ++q) {
-        tma_load_2d(bs + q * WsSmem::chunk_b, &tmBhi, &bars[B_BFULL + slot], q * KCHUNK, nb * UNIT_N);
-        tma_load_2d(bs + (2 + q) * WsSmem::chunk_b, &tmBlo, &bars[B_BFULL + slot], q * KCHUNK,
-                    nb * UNIT_N);
-      }
+    auto aslot = [&](int sl) { return (float*)(base + WsSmem::a0 + sl * WsSmem::a_slot); };
+    auto issue_a = [&](int v) {
+      const int64_t T = gi + (int64_t)v * groups;
+      const bool second = T >= tiles0;
+      const int64_t t = second ? T - tiles0 : T;
+      const int sl = v & 1;
+      float* dst = aslot(sl);
+      mbar_expect_tx(&bars[B_AFULL + sl], (uint32_t)(kb * WsSmem::chunk));
+      for (int q = 0; q < kb; ++q)
+        tma_load_2d(dst + q * TILE_M * KCHUNK, second ? &tmA1 : &tmA0, &bars[B_AFULL + sl],
+                    q * KCHUNK, (int)(t * TILE_M));
     };
-    if (leader && nv > 0) load_b(0);
-    int64_t tcur = -1;
-    int ka = 0;
+    if (leader && nitems > 0) {
+      mbar_expect_tx(&bars[B_BFULL], (uint32_t)(2 * kb * WsSmem::chunk));
+      for (int q = 0; q < kb; ++q) {
+        tma_load_2d(base + WsSmem::b_hi + q * WsSmem::chunk, &tmBhi, &bars[B_BFULL], q * KCHUNK,
+                    blk_n * BLOCK_N);
+        tma_load_2d(base + WsSmem::b_lo + q * WsSmem::chunk, &tmBlo, &bars[B_BFULL], q * KCHUNK,
+                    blk_n * BLOCK_N);
+      }
+      issue_a(0);
+    }
     // No early exit: every thread of the group runs the same iterations and
     // reaches every group_sync(); after a failure the work is skipped.
-    for (int v = 0; v < nv; ++v) {
-      const int64_t u = ubeg + v, t = u / NB;
-      if (t != tcur) {
-        if (leader && !*fail) {
-          if (ka == 0 || mbar_wait(&bars[B_AFREE], (uint32_t)((ka - 1) & 1))) {
-            mbar_expect_tx(&bars[B_AFULL], (uint32_t)(kb * WsSmem::chunk_a));
-            for (int q = 0; q < kb; ++q)
-              tma_load_2d(Ahi + q * TILE_M * KCHUNK, &tmA, &bars[B_AFULL], q * KCHUNK,
-                          (int)(t * TILE_M));
-          } else {
-            *fail = 1;
-          }
-        }
-        if (!*fail && !mbar_wait(&bars[B_AFULL], (uint32_t)(ka & 1))) *fail = 1;
-        if (!*fail) {
-          const int total = kb * TILE_M * KCHUNK;
-          for (int e = pt * 4; e < total; e += 128 * 4) {
-            float4 x = *(float4*)(Ahi + e);
-            float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
-            *(float4*)(Ahi + e) = h;
-            *(float4*)(Alo + e) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-          }
-          fence_async_smem();
-        }
-        group_sync();
-        ++ka;
-        tcur = t;
+    for (int v = 0; v < nitems; ++v) {
+      const int sl = v & 1;
+      // the next tile streams into the other slot once its previous tile's MMAs are done
+      if (leader && !*fail && v + 1 < nitems) {
+        if (v + 1 < 2 || mbar_wait(&bars[B_AFREE + (sl ^ 1)], (uint32_t)(((v + 1) / 2 - 1) & 1)))
+          issue_a(v + 1);
+        else
+          *fail = 1;
       }
+      if (!*fail && !mbar_wait(&bars[B_AFULL + sl], (uint32_t)((v / 2) & 1))) *fail = 1;
+      float* Ahi = aslot(sl);
+      float* Alo = Ahi + 2 * TILE_M * KCHUNK;
+      if (!*fail) {
+        const int total = kb * TILE_M * KCHUNK;
+        for (int e = pt * 4; e < total; e += 128 * 4) {
+          float4 x = *(float4*)(Ahi + e);
+          float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
+          *(float4*)(Ahi + e) = h;
+          *(float4*)(Alo + e) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        }
+        fence_async_smem();
+      }
+      group_sync();
       if (leader && !*fail) {
-        const int blk = v & (TMEM_RING - 1), slot = v & 1;
-        bool ok = v < TMEM_RING ||
-                  mbar_wait(&bars[B_TEMPTY + blk], (uint32_t)(((v / TMEM_RING) - 1) & 1));
-        ok = ok && mbar_wait(&bars[B_BFULL + slot], (uint32_t)((v >> 1) & 1));
+        const int blk = v & (TMEM_RING - 1);
+        bool ok = v > 0 || mbar_wait(&bars[B_BFULL], 0);
+        ok = ok && (v < TMEM_RING ||
+                    mbar_wait(&bars[B_TEMPTY + blk], (uint32_t)(((v / TMEM_RING) - 1) & 1)));
         if (ok) {
           tc_fence_after();
-          const uint32_t dcol = tmem + (uint32_t)(blk * UNIT_N);
-          const uint8_t* bs = bslot(slot);
+          const uint32_t dcol = tmem + (uint32_t)(blk * BLOCK_N);
           uint32_t accum = 0;
           // small terms first: A_hi B_lo, A_lo B_hi, then A_hi B_hi
           for (int pass = 0; pass < 3; ++pass) {
             const float* Ap = pass == 1 ? Alo : Ahi;
-            const uint8_t* Bp = pass == 0 ? bs + 2 * WsSmem::chunk_b : bs;
+            const uint8_t* Bp = base + (pass == 0 ? WsSmem::b_lo : WsSmem::b_hi);
             for (int q = 0; q < kb; ++q) {
               const uint64_t ad = sw128_desc(Ap + q * TILE_M * KCHUNK);
-              const uint64_t bd = sw128_desc(Bp + q * WsSmem::chunk_b);
+              const uint64_t bd = sw128_desc(Bp + q * WsSmem::chunk);
 #pragma unroll
               for (int k = 0; k < KCHUNK / 8; ++k) {
                 // advance 8 TF32 = 32 bytes along K inside the swizzle row
@@ -182,15 +187,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
               }
             }
           }
-          mma_commit(&bars[B_BFREE + slot]);
+          mma_commit(&bars[B_AFREE + sl]);
           mma_commit(&bars[B_TFULL + blk]);
-          if (v + 1 == nv || (u + 1) / NB != t) mma_commit(&bars[B_AFREE]);
-          if (v + 1 < nv) {
-            ok = v < 1 || mbar_wait(&bars[B_BFREE + ((v + 1) & 1)], (uint32_t)(((v - 1) >> 1) & 1));
-            if (ok) load_b(v + 1);
-          }
+        } else {
+          *fail = 1;
         }
-        if (!ok) *fail = 1;
       }
     }
   } else {
@@ -198,10 +199,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     float* stg0 = (float*)(base + WsSmem::stage + (size_t)(2 * warp) * WsSmem::box);
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     int sb = 0;
-    for (int v = 0; v < nv; ++v) {
+    for (int v = 0; v < nitems; ++v) {
       if (__shfl_sync(0xffffffffu, *fail, 0)) continue;
-      const int64_t u = ubeg + v, t = u / NB;
-      const int nb = (int)(u % NB), blk = v & (TMEM_RING - 1);
+      const int64_t T = gi + (int64_t)v * groups;
+      const bool second = T >= tiles0;
+      const int64_t t = second ? T - tiles0 : T;
+      const int64_t rows = second ? rows1 : rows0;
+      const CUtensorMap* tmC = second ? &tmC1 : &tmC0;
+      const int blk = v & (TMEM_RING - 1);
       const bool ok = __all_sync(0xffffffffu,
                                  mbar_wait(&bars[B_TFULL + blk], (uint32_t)((v / TMEM_RING) & 1)));
       if (!ok) {
@@ -210,12 +215,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
       }
       tc_fence_after();
       const int64_t row0 = t * TILE_M + warp * 32;
-      if (row0 < rows_a) {
-        for (int j = 0; j < UNIT_N / BOX; ++j) {
-          const int col0 = nb * UNIT_N + j * BOX;
+      if (row0 < rows) {
+        for (int j = 0; j < BLOCK_N / BOX; ++j) {
+          const int col0 = blk_n * BLOCK_N + j * BOX;
           if (col0 >= n) break;
           uint32_t r[32];
-          tmem_ld32(tmem + lane_base + (uint32_t)(blk * UNIT_N + j * BOX), r);
+          tmem_ld32(tmem + lane_base + (uint32_t)(blk * BLOCK_N + j * BOX), r);
           float* stg = stg0 + sb * (BOX * BOX);
           if (lane == 0) bulk_wait_read<1>();
           __syncwarp();
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
           fence_async_smem();
           __syncwarp();
           if (lane == 0) {
-            tma_store_2d(&tmC, stg, col0, (int)row0);
+            tma_store_2d(tmC, stg, col0, (int)row0);
             bulk_commit();
           }
           sb ^= 1;
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TMEM_RING * UNIT_N)
+                 "r"(TMEM_RING * BLOCK_N)
                  : "memory");
   if (threadIdx.x == 0 && *fail) atomicOr(err, ERR_TIMEOUT);
 }
@@ -317,25 +322,46 @@ cudaError_t split_tf32(const float* B, int64_t count, float* hi, float* lo, cuda
   return cudaGetLastError();
 }
 
-cudaError_t corr_tf32x3(const float* A, int64_t rows_a, const float* Bhi, const float* Blo, int n,
-                        int p, float* C, int64_t ldc, int* err, cudaStream_t st) {
-  if (rows_a <= 0) return cudaSuccess;
-  if (((uintptr_t)C % 16) != 0) return cudaErrorInvalidValue;
-  CUtensorMap ma, mbh, mbl, mc;
-  if (!make_map(&ma, A, rows_a, p, TILE_M) || !make_map(&mbh, Bhi, n, p, UNIT_N) ||
-      !make_map(&mbl, Blo, n, p, UNIT_N) || !make_map_out(&mc, C, rows_a, n, ldc))
+cudaError_t corr_tf32x3_pair(const float* A0, int64_t rows0, float* C0, int64_t ldc0,
+                             const float* A1, int64_t rows1, float* C1, int64_t ldc1,
+                             const float* Bhi, const float* Blo, int n, int p, int* err,
+                             cudaStream_t st) {
+  if (!A1) rows1 = 0;
+  if (rows0 <= 0 && rows1 <= 0) return cudaSuccess;
+  if (rows0 <= 0) return corr_tf32x3_pair(A1, rows1, C1, ldc1, nullptr, 0, nullptr, 0, Bhi, Blo, n,
+                                          p, err, st);
+  if (((uintptr_t)C0 % 16) != 0 || (rows1 > 0 && ((uintptr_t)C1 % 16) != 0))
     return cudaErrorInvalidValue;
+  CUtensorMap ma0, ma1, mbh, mbl, mc0, mc1;
+  if (!make_map(&ma0, A0, rows0, p, TILE_M) || !make_map(&mbh, Bhi, n, p, BLOCK_N) ||
+      !make_map(&mbl, Blo, n, p, BLOCK_N) || !make_map_out(&mc0, C0, rows0, n, ldc0))
+    return cudaErrorInvalidValue;
+  if (rows1 > 0) {
+    if (!make_map(&ma1, A1, rows1, p, TILE_M) || !make_map_out(&mc1, C1, rows1, n, ldc1))
+      return cudaErrorInvalidValue;
+  } else {
+    ma1 = ma0;
+    mc1 = mc0;
+  }
   const int kb = (p + KCHUNK - 1) / KCHUNK;
   cudaError_t e = cudaFuncSetAttribute(corr_tf32x3_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)WsSmem::dyn);
   if (e != cudaSuccess) return e;
-  const int64_t tiles = (rows_a + TILE_M - 1) / TILE_M;
-  const int64_t units = tiles * ((n + UNIT_N - 1) / UNIT_N);
-  const unsigned grid = (unsigned)(units < num_sms() ? units : num_sms());
-  corr_tf32x3_kernel<<<grid, WS_THREADS, WsSmem::dyn, st>>>(ma, mbh, mbl, mc, rows_a, n, kb, units,
-                                                            err);
+  const int64_t tiles0 = (rows0 + TILE_M - 1) / TILE_M;
+  const int64_t tiles = tiles0 + (rows1 + TILE_M - 1) / TILE_M;
+  const int nq = (n + BLOCK_N - 1) / BLOCK_N;
+  int64_t groups = num_sms() / nq;
+  if (groups < 1) groups = 1;
+  if (groups > tiles) groups = tiles;
+  corr_tf32x3_kernel<<<(unsigned)(groups * nq), WS_THREADS, WsSmem::dyn, st>>>(
+      ma0, ma1, mbh, mbl, mc0, mc1, rows0, rows1, tiles0, tiles, n, kb, nq, err);
   return cudaGetLastError();
+}
+
+cudaError_t corr_tf32x3(const float* A, int64_t rows_a, const float* Bhi, const float* Blo, int n,
+                        int p, float* C, int64_t ldc, int* err, cudaStream_t st) {
+  return corr_tf32x3_pair(A, rows_a, C, ldc, nullptr, 0, nullptr, 0, Bhi, Blo, n, p, err, st);
 }
 
 }  // namespace dlk
