@@ -250,7 +250,9 @@ __device__ __forceinline__ void omp_one(
       }
       break;
     }
-    const float ck = __frsqrt_rn(delta);  // c_k = 1 / L_kk, correctly rounded
+    // c_k = 1 / L_kk: rsqrtf refined by one Newton-Raphson step, y + y (1 - d y^2) / 2
+    float ck = rsqrtf(delta);
+    ck = fmaf(0.5f * ck, fmaf(-delta * ck, ck, 1.0f), ck);
     const float zk = asel * ck;
     if (lane == step) {
       invLdiag = ck;
