@@ -421,7 +421,8 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
   c->jw.nb_accum = dlk::jau_accum_blocks_max(p, n);
   c->jw.nb_row = dlk::jau_row_blocks_max();
   const size_t ulen = (size_t)n * p + n;
-  const size_t nslices = dlk::jau_accum_smem(p, n) > 0 ? (size_t)c->jw.nb_accum : 1;
+  size_t nslices = dlk::jau_accum_smem(p, n) > 0 ? (size_t)c->jw.nb_accum : 1;
+  if (nslices < (size_t)dlk::kUCopies) nslices = dlk::kUCopies;
   bool ok = dalloc(&c->G, (size_t)n * n) && dalloc(&c->A0, mm * c->lda) &&
             dalloc(&c->sidx, mm * s_max) && dalloc(&c->sval, mm * s_max) &&
             dalloc(&c->scnt, mm) && dalloc(&c->bsum, (size_t)dlk::scan_blocks(m_max) + 1) &&

@@ -106,6 +106,7 @@ struct JauWork {
 };
 // Grid sizes: mult selects 1x/2x the base CTA count of the accumulation pass
 // and 2/4/8 CTAs per SM for the row pass; *_max give the partial-buffer sizes.
+constexpr int kUCopies = 16;  // copies of U the float4 accumulation spreads its L2 reductions over
 int jau_accum_blocks(int p, int n, int mult);
 int jau_accum_blocks_max(int p, int n);
 int jau_row_blocks(int per_sm);

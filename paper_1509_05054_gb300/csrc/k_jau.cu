@@ -10,9 +10,9 @@
 //
 // The passes over the signals give each signal eight lanes (four signals per
 // warp).  With p % 4 == 0 and 16-byte aligned Y and D they move float4 rows
-// and pass A adds x e_i into U with vector reductions in L2 (red.v4.f32);
-// otherwise pass A keeps per-CTA copies of U (shared memory when they fit)
-// that are summed in a fixed order.  The energy partial sums are reduced in a
+// and pass A adds x e_i into 16 copies of U with vector reductions in L2
+// (red.v4.f32); otherwise pass A keeps per-CTA copies of U (shared memory when
+// they fit).  The copies are summed in a fixed order.  The energy partial sums are reduced in a
 // fixed order.
 #include "dl_internal.cuh"
 
@@ -153,9 +153,12 @@ __device__ __forceinline__ float f4_dot(float4 a, float4 b, float acc) {
   return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
 }
 
-// Pass A, float4 form: U (zeroed, p x n atom-major, then r at U + n p) gets
-// x_{j,i} e_i by vector reductions in L2 (native FP32 adds); r_j is summed
-// per CTA in shared memory and added once per CTA.
+// Pass A, float4 form: CTA b adds x_{j,i} e_i into copy b mod kUCopies of U
+// (zeroed, p x n atom-major, then r at + n p) by vector reductions in L2
+// (native FP32 adds); r_j is summed per CTA in shared memory and added once per
+// CTA.  Spreading the reductions over several copies keeps the L2 lines of
+// frequently used atoms from serialising them; the copies are then summed in a
+// fixed order.
 template <int RV, int SMAX>
 __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
     const float* __restrict__ Y, int p, int64_t m, const float* __restrict__ D, int n, int s,
@@ -170,6 +173,7 @@ __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
   const int pv = p >> 2;
   const float4* __restrict__ Y4 = (const float4*)Y;
   const float4* __restrict__ D4 = (const float4*)D;
+  float* __restrict__ Uc = U + (size_t)(blockIdx.x % kUCopies) * ((size_t)n * p + n);
   float ee = 0.f, yy = 0.f;
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
   const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
@@ -215,7 +219,7 @@ __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
         for (int q = 0; q < RV; ++q) {
           const int v = g + 8 * q;
           if (v < pv)
-            red_add_v4(U + ((size_t)jj * pv + v) * 4,
+            red_add_v4(Uc + ((size_t)jj * pv + v) * 4,
                        make_float4(xx * e[q].x, xx * e[q].y, xx * e[q].z, xx * e[q].w));
         }
         if (g == 0) atomicAdd(&rsh[jj], xx * xx);
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
   __syncthreads();
   const size_t np = (size_t)n * p;
   for (int j = threadIdx.x; j < n; j += blockDim.x)
-    if (rsh[j] != 0.f) atomicAdd(U + np + j, rsh[j]);
+    if (rsh[j] != 0.f) atomicAdd(Uc + np + j, rsh[j]);
   const double see = block_sum_d((double)ee, red);
   const double syy = block_sum_d((double)yy, red);
   if (threadIdx.x == 0) {
@@ -724,8 +728,11 @@ bool jau_vec4(int p, const float* Y, const float* D) {
   return p % 4 == 0 && ((uintptr_t)Y % 16) == 0 && ((uintptr_t)D % 16) == 0;
 }
 int jau_launches(int p, const float* Y, const float* D) {
-  // accumulate (+ slice reduction unless the float4 form) + atoms + rows + finalize
-  return jau_vec4(p, Y, D) ? 4 : 5;
+  // accumulate + slice/copy reduction + atoms + rows + finalize
+  (void)p;
+  (void)Y;
+  (void)D;
+  return 5;
 }
 int jau_row_blocks(int per_sm) { return (per_sm == 2 || per_sm == 8 ? per_sm : 4) * num_sms(); }
 int jau_row_blocks_max() { return 8 * num_sms(); }
@@ -734,11 +741,12 @@ cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int
                            const int32_t* idx, const float* val, const int32_t* cnt,
                            const JauWork& w, int* err, cudaStream_t st) {
   if (jau_vec4(p, Y, D)) {
-    cudaError_t e = cudaMemsetAsync(w.U, 0, sizeof(float) * ((size_t)n * p + n), st);
+    const size_t len = (size_t)n * p + n;
+    cudaError_t e = cudaMemsetAsync(w.Upart, 0, sizeof(float) * len * kUCopies, st);
     if (e != cudaSuccess) return e;
-#define DL_ACC4(RV, SM)                                                                          \
-  accum4_kernel<RV, SM><<<w.nb_accum, ACC4_THREADS, 0, st>>>(Y, p, m, D, n, s, idx, val, cnt, w.U, \
-                                                             w.epart_a, err)
+#define DL_ACC4(RV, SM)                                                                  \
+  accum4_kernel<RV, SM><<<w.nb_accum, ACC4_THREADS, 0, st>>>(Y, p, m, D, n, s, idx, val, cnt, \
+                                                             w.Upart, w.epart_a, err)
 #define DL_ACC4_S(RV) \
   if (s <= 8) DL_ACC4(RV, 8); else DL_ACC4(RV, 16)
     if (p <= 32) { DL_ACC4_S(1); }
@@ -747,7 +755,8 @@ cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int
     else { DL_ACC4_S(4); }
 #undef DL_ACC4_S
 #undef DL_ACC4
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return reduce_slices(w.Upart, kUCopies, (int)len, w.U, st);
   }
   if (p % 4 == 0) {
     // unaligned operands: scalar form with global atomics and w.nb_accum CTAs
