@@ -15,12 +15,12 @@
 // block c % nq (nq = ceil(n/128)) and keeps that block's pre-split B (head and
 // tail, 64 KB at p <= 64) resident in shared memory for its whole life; the
 // CTAs owning a block share out the 128-row tiles of A (both products' tiles
-// in one list).  Warp roles, 256 threads:
-//   * warps 4-7 (producer group): thread 128 loads the B block once and keeps
-//     a two-slot ring of A tiles (TMA, SWIZZLE_128B, one tile ahead); the
-//     group splits each tile in place into A_hi / A_lo; thread 128 issues
-//     3 x (K/8) tcgen05.mma kind::tf32 (M=128, N=128, K=8) per tile into one of
-//     four 128-column TMEM accumulators;
+// in one list).  Warp roles, 256 threads, each waiting only on mbarriers:
+//   * warp 4, one thread: TMA of the B block once, then of the A tiles into a
+//     two-slot ring (SWIZZLE_128B), each as soon as its slot is free;
+//   * warps 6-7: split each arrived tile in place into A_hi / A_lo;
+//   * warp 5, one thread: per split tile, 3 x (K/8) tcgen05.mma kind::tf32
+//     (M=128, N=128, K=8) into one of four 128-column TMEM accumulators;
 //   * warps 0-3 (epilogue): drain an accumulator with tcgen05.ld (warp w owns
 //     TMEM lanes 32w..32w+31 = rows), stage 32x32 boxes in 128-byte-swizzled
 //     shared memory and write them with TMA stores (two boxes in flight per
@@ -59,15 +59,14 @@ struct WsSmem {  // byte offsets from the 1024-aligned base
   static constexpr size_t stage = a0 + 2 * a_slot;   // 4 warps x 2 boxes
   static constexpr size_t box = (size_t)BOX * BOX * 4;
   static constexpr size_t bars = stage + 8 * box;
-  static constexpr size_t total = bars + 13 * 8 + 16;
+  static constexpr size_t total = bars + 15 * 8 + 16;
   static constexpr size_t dyn = total + 1024;
 };
 static_assert(WsSmem::dyn <= 232448, "shared memory budget");
 
 // barrier indices
-constexpr int B_BFULL = 0, B_AFULL = 1, B_AFREE = 3, B_TFULL = 5, B_TEMPTY = 9;
-
-__device__ __forceinline__ void group_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+constexpr int B_BFULL = 0, B_AFULL = 1, B_AFREE = 3, B_ASPLIT = 5, B_TFULL = 7, B_TEMPTY = 11;
+constexpr int kBars = 15;
 
 // tiles0 tiles of product 0 (A0 -> C0, rows0 rows), then those of product 1.
 __global__ void __launch_bounds__(WS_THREADS, 1)
@@ -79,7 +78,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(base + WsSmem::bars);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 13);
+  uint32_t* tmem_slot = (uint32_t*)(bars + kBars);
   volatile int* fail = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -93,6 +92,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     for (int q = 0; q < 2; ++q) {
       mbar_init(&bars[B_AFULL + q], 1);
       mbar_init(&bars[B_AFREE + q], 1);
+      mbar_init(&bars[B_ASPLIT + q], 64);
     }
     for (int q = 0; q < TMEM_RING; ++q) {
       mbar_init(&bars[B_TFULL + q], 1);
@@ -112,23 +112,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp >= 4) {
-    // ---------------- producer group ----------------
-    const int pt = threadIdx.x - 128;
-    const bool leader = pt == 0;
-    auto aslot = [&](int sl) { return (float*)(base + WsSmem::a0 + sl * WsSmem::a_slot); };
-    auto issue_a = [&](int v) {
-      const int64_t T = gi + (int64_t)v * groups;
-      const bool second = T >= tiles0;
-      const int64_t t = second ? T - tiles0 : T;
-      const int sl = v & 1;
-      float* dst = aslot(sl);
-      mbar_expect_tx(&bars[B_AFULL + sl], (uint32_t)(kb * WsSmem::chunk));
-      for (int q = 0; q < kb; ++q)
-        tma_load_2d(dst + q * TILE_M * KCHUNK, second ? &tmA1 : &tmA0, &bars[B_AFULL + sl],
-                    q * KCHUNK, (int)(t * TILE_M));
-    };
-    if (leader && nitems > 0) {
+  auto aslot = [&](int sl) { return (float*)(base + WsSmem::a0 + sl * WsSmem::a_slot); };
+  if (warp == 4) {
+    // ---------------- TMA issuer: the B block once, then the A tiles ----------------
+    if (lane == 0 && nitems > 0) {
       mbar_expect_tx(&bars[B_BFULL], (uint32_t)(2 * kb * WsSmem::chunk));
       for (int q = 0; q < kb; ++q) {
         tma_load_2d(base + WsSmem::b_hi + q * WsSmem::chunk, &tmBhi, &bars[B_BFULL], q * KCHUNK,
@@ -136,63 +123,79 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
         tma_load_2d(base + WsSmem::b_lo + q * WsSmem::chunk, &tmBlo, &bars[B_BFULL], q * KCHUNK,
                     blk_n * BLOCK_N);
       }
-      issue_a(0);
-    }
-    // No early exit: every thread of the group runs the same iterations and
-    // reaches every group_sync(); after a failure the work is skipped.
-    for (int v = 0; v < nitems; ++v) {
-      const int sl = v & 1;
-      // the next tile streams into the other slot once its previous tile's MMAs are done
-      if (leader && !*fail && v + 1 < nitems) {
-        if (v + 1 < 2 || mbar_wait(&bars[B_AFREE + (sl ^ 1)], (uint32_t)(((v + 1) / 2 - 1) & 1)))
-          issue_a(v + 1);
-        else
+      for (int v = 0; v < nitems && !*fail; ++v) {
+        const int sl = v & 1;
+        // the slot is free once the MMAs of the tile two back have completed
+        if (v >= 2 && !mbar_wait(&bars[B_AFREE + sl], (uint32_t)((v / 2 - 1) & 1))) {
           *fail = 1;
-      }
-      if (!*fail && !mbar_wait(&bars[B_AFULL + sl], (uint32_t)((v / 2) & 1))) *fail = 1;
-      float* Ahi = aslot(sl);
-      float* Alo = Ahi + 2 * TILE_M * KCHUNK;
-      if (!*fail) {
-        const int total = kb * TILE_M * KCHUNK;
-        for (int e = pt * 4; e < total; e += 128 * 4) {
-          float4 x = *(float4*)(Ahi + e);
-          float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
-          *(float4*)(Ahi + e) = h;
-          *(float4*)(Alo + e) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          break;
         }
-        fence_async_smem();
+        const int64_t T = gi + (int64_t)v * groups;
+        const bool second = T >= tiles0;
+        const int64_t t = second ? T - tiles0 : T;
+        float* dst = aslot(sl);
+        mbar_expect_tx(&bars[B_AFULL + sl], (uint32_t)(kb * WsSmem::chunk));
+        for (int q = 0; q < kb; ++q)
+          tma_load_2d(dst + q * TILE_M * KCHUNK, second ? &tmA1 : &tmA0, &bars[B_AFULL + sl],
+                      q * KCHUNK, (int)(t * TILE_M));
       }
-      group_sync();
-      if (leader && !*fail) {
-        const int blk = v & (TMEM_RING - 1);
-        bool ok = v > 0 || mbar_wait(&bars[B_BFULL], 0);
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      bool ok = nitems == 0 || mbar_wait(&bars[B_BFULL], 0);
+      for (int v = 0; v < nitems && ok && !*fail; ++v) {
+        const int sl = v & 1, blk = v & (TMEM_RING - 1);
+        ok = mbar_wait(&bars[B_ASPLIT + sl], (uint32_t)((v / 2) & 1));
         ok = ok && (v < TMEM_RING ||
                     mbar_wait(&bars[B_TEMPTY + blk], (uint32_t)(((v / TMEM_RING) - 1) & 1)));
-        if (ok) {
-          tc_fence_after();
-          const uint32_t dcol = tmem + (uint32_t)(blk * BLOCK_N);
-          uint32_t accum = 0;
-          // small terms first: A_hi B_lo, A_lo B_hi, then A_hi B_hi
-          for (int pass = 0; pass < 3; ++pass) {
-            const float* Ap = pass == 1 ? Alo : Ahi;
-            const uint8_t* Bp = base + (pass == 0 ? WsSmem::b_lo : WsSmem::b_hi);
-            for (int q = 0; q < kb; ++q) {
-              const uint64_t ad = sw128_desc(Ap + q * TILE_M * KCHUNK);
-              const uint64_t bd = sw128_desc(Bp + q * WsSmem::chunk);
+        if (!ok) break;
+        tc_fence_after();
+        const float* Ahi = aslot(sl);
+        const float* Alo = Ahi + 2 * TILE_M * KCHUNK;
+        const uint32_t dcol = tmem + (uint32_t)(blk * BLOCK_N);
+        uint32_t accum = 0;
+        // small terms first: A_hi B_lo, A_lo B_hi, then A_hi B_hi
+        for (int pass = 0; pass < 3; ++pass) {
+          const float* Ap = pass == 1 ? Alo : Ahi;
+          const uint8_t* Bp = base + (pass == 0 ? WsSmem::b_lo : WsSmem::b_hi);
+          for (int q = 0; q < kb; ++q) {
+            const uint64_t ad = sw128_desc(Ap + q * TILE_M * KCHUNK);
+            const uint64_t bd = sw128_desc(Bp + q * WsSmem::chunk);
 #pragma unroll
-              for (int k = 0; k < KCHUNK / 8; ++k) {
-                // advance 8 TF32 = 32 bytes along K inside the swizzle row
-                mma_tf32(dcol, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), kIdesc, accum);
-                accum = 1;
-              }
+            for (int k = 0; k < KCHUNK / 8; ++k) {
+              // advance 8 TF32 = 32 bytes along K inside the swizzle row
+              mma_tf32(dcol, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), kIdesc, accum);
+              accum = 1;
             }
           }
-          mma_commit(&bars[B_AFREE + sl]);
-          mma_commit(&bars[B_TFULL + blk]);
-        } else {
-          *fail = 1;
         }
+        mma_commit(&bars[B_AFREE + sl]);
+        mma_commit(&bars[B_TFULL + blk]);
       }
+      if (!ok) *fail = 1;
+    }
+  } else if (warp >= 6) {
+    // ---------------- splitters: A tile -> A_hi / A_lo in place ----------------
+    const int pt = threadIdx.x - 192;  // 0..63
+    for (int v = 0; v < nitems; ++v) {
+      if (*fail) break;
+      const int sl = v & 1;
+      if (!mbar_wait(&bars[B_AFULL + sl], (uint32_t)((v / 2) & 1))) {
+        *fail = 1;
+        break;
+      }
+      float* Ahi = aslot(sl);
+      float* Alo = Ahi + 2 * TILE_M * KCHUNK;
+      const int total = kb * TILE_M * KCHUNK;
+      for (int e = pt * 4; e < total; e += 64 * 4) {
+        float4 x = *(float4*)(Ahi + e);
+        float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
+        *(float4*)(Ahi + e) = h;
+        *(float4*)(Alo + e) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+      }
+      fence_async_smem();
+      mbar_arrive(&bars[B_ASPLIT + sl]);
     }
   } else {
     // ---------------- epilogue warps ----------------
