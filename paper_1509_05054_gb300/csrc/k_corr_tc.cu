@@ -15,10 +15,10 @@
 // block c % nq (nq = ceil(n/128)) and keeps that block's pre-split B (head and
 // tail, 64 KB at p <= 64) resident in shared memory for its whole life; the
 // CTAs owning a block share out the 128-row tiles of A (both products' tiles
-// in one list).  Warp roles, 256 threads, each waiting only on mbarriers:
+// in one list).  Warp roles, 384 threads, each waiting only on mbarriers:
 //   * warp 4, one thread: TMA of the B block once, then of the A tiles into a
 //     two-slot ring (SWIZZLE_128B), each as soon as its slot is free;
-//   * warps 6-7: split each arrived tile in place into A_hi / A_lo;
+//   * warps 6-11: split each arrived tile in place into A_hi / A_lo;
 //   * warp 5, one thread: per split tile, 3 x (K/8) tcgen05.mma kind::tf32
 //     (M=128, N=128, K=8) into one of four 128-column TMEM accumulators;
 //   * warps 0-3 (epilogue): drain an accumulator with tcgen05.ld (warp w owns
@@ -39,7 +39,8 @@
 namespace dlk {
 namespace {
 
-constexpr int WS_THREADS = 256;
+constexpr int WS_THREADS = 384;
+constexpr int SPLIT_THREADS = WS_THREADS - 192;  // warps 6..
 constexpr int TILE_M = 128;
 constexpr int BLOCK_N = 128;  // atoms per column block (MMA N)
 constexpr int KCHUNK = 32;    // floats per 128-byte swizzle row
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     for (int q = 0; q < 2; ++q) {
       mbar_init(&bars[B_AFULL + q], 1);
       mbar_init(&bars[B_AFREE + q], 1);
-      mbar_init(&bars[B_ASPLIT + q], 64);
+      mbar_init(&bars[B_ASPLIT + q], SPLIT_THREADS);
     }
     for (int q = 0; q < TMEM_RING; ++q) {
       mbar_init(&bars[B_TFULL + q], 1);
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     }
   } else if (warp >= 6) {
     // ---------------- splitters: A tile -> A_hi / A_lo in place ----------------
-    const int pt = threadIdx.x - 192;  // 0..63
+    const int pt = threadIdx.x - 192;
     for (int v = 0; v < nitems; ++v) {
       if (*fail) break;
       const int sl = v & 1;
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
       float* Ahi = aslot(sl);
       float* Alo = Ahi + 2 * TILE_M * KCHUNK;
       const int total = kb * TILE_M * KCHUNK;
-      for (int e = pt * 4; e < total; e += 64 * 4) {
+      for (int e = pt * 4; e < total; e += SPLIT_THREADS * 4) {
         float4 x = *(float4*)(Ahi + e);
         float4 h = make_float4(tf32_rna(x.x), tf32_rna(x.y), tf32_rna(x.z), tf32_rna(x.w));
         *(float4*)(Ahi + e) = h;
