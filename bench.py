@@ -317,12 +317,15 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     algo = {
         # FLOP per launch (FFMA = 2, compare = 1) or bytes per launch
-        "omp": ("alu", m * n * s * s, peak_alu_tflops, "TFLOP/s"),
+        # per signal n s(s+1) (alpha and u updates) + 2ns (argmax compares, phi reads)
+        # + s(s+1)(2s+1)/2 (Cholesky rows and solves); FFMA = 2 FLOP
+        "omp": ("alu", m * (n * s * (s + 1) + 2 * n * s + s * (s + 1) * (2 * s + 1) // 2),
+                peak_alu_tflops, "TFLOP/s"),
         "accumulate": ("hbm", m * (4 * p + 8 * s), hbm, "GB/s"),
         "rows": ("hbm", m * (4 * p + 12 * s), hbm, "GB/s"),
     }
-    if best == "fp32":
-        algo["correlations"] = ("tensor", 2.0 * m * n * p,
+    if best == "fp32":  # one launch: the correlations of all signals and the Gram matrix
+        algo["correlations"] = ("tensor", 2.0 * m * n * p + 2.0 * n * n * p,
                                 float(peaks.get("bf16_tflops", 1891.2)) / 2.0, "TFLOP/s")
     else:
         scale = 1.0 if best == "bf16" else 2.0
