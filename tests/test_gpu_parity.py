@@ -352,3 +352,38 @@ def test_correlations_and_gram_are_fp32_accurate(dl, name, m):
     assert errG < 1e-5, (errG, tc)
     if name == "patch_n512":
         assert tc == 1     # p = 64, n = 512 takes the tcgen05 path
+
+
+RAGGED_TC = [
+    # (patch side -> p, n, m, s): a partial last 128-atom block, and eight blocks
+    (8, 200, 1001, 5),
+    (6, 1024, 700, 6),
+]
+
+
+@pytest.mark.parametrize("side,n,m,s", RAGGED_TC)
+def test_tensor_core_products_on_ragged_atom_blocks(dl, side, n, m, s):
+    """Correlations and Gram on the tcgen05 path when n is not a multiple of the
+    kernel's 128-atom column block (n = 200) and when it spans eight blocks
+    (n = 1024, p = 36), through dl_correlate / dl_gram (one product per launch)
+    and through omp_code (both products in one launch), against FP64."""
+    Y = synth.image_patches(m, side=side, workload_id=40 + side, first_image=900)
+    p = side * side
+    D = synth.random_dictionary(p, n, seed=7000 + n, dtype=np.float32)
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    assert dl.dl_uses_tensor_cores(ctx) == 1
+    Yd, Dd = torch.from_numpy(Y).cuda(), torch.from_numpy(D).cuda()
+    A = torch.zeros(m, n, device="cuda")
+    G = torch.zeros(n, n, device="cuda")
+    dl.dl_correlate(ctx, Yd, m, Dd, A)
+    dl.dl_gram(ctx, Dd, G)
+    dl.dl_sync(ctx)
+    Y64, D64 = Y.astype(np.float64), D.astype(np.float64)
+    scale = np.linalg.norm(Y64, axis=1)[:, None] * np.linalg.norm(D64, axis=1)[None, :]
+    assert np.max(np.abs(A.cpu().numpy() - Y64 @ D64.T) / scale) < 1e-5
+    assert np.max(np.abs(G.cpu().numpy() - D64 @ D64.T)) < 1e-5
+    idx_g, val_g, cnt_g = _gpu_omp(dl, Y, D, s, ctx=ctx)
+    dl.dl_destroy(ctx)
+    idx_o, val_o, cnt_o, gaps = oracle.omp(Y64, D64, s, return_gaps=True)
+    same = assert_support_parity(idx_g, cnt_g, idx_o, cnt_o, gaps)
+    np.testing.assert_allclose(val_g[same], val_o[same], rtol=0, atol=5e-4)
