@@ -366,10 +366,11 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             dl.dl_iterate(ctx, Yh, m, Dh, s, 1, cph, rih, vh, rmh)
         dt = max_over_ranks(time.perf_counter() - t0, pg)
-        nnz = int(cph[m])
+        # host buffers: D in; D, colptr, all s*m rowidx/val entries, the RMSE pair and the
+        # device error word out
         e2e = {"value": job_throughput(world, m * args.e2e_steps, dt), "unit": UNIT,
                "h2d_bytes_per_step": 4 * m * p + 4 * n * p,
-               "d2h_bytes_per_step": 4 * n * p + 8 * (m + 1) + 8 * nnz + 16 + 4,
+               "d2h_bytes_per_step": 4 * n * p + 8 * (m + 1) + 8 * m * s + 16 + 4,
                "steps": args.e2e_steps}
 
     batched = None

@@ -26,7 +26,8 @@
  * arguments of one call are device pointers (cudaMalloc, or torch tensors on
  * the context's GPU), or all are host pointers (pageable or pinned); in the
  * host case the call stages them through device buffers owned by the context
- * and copies results back before returning.  `rmse` outputs are always host
+ * and copies results back before returning (all s*m entries of rowidx/val;
+ * those past colptr[m] are unspecified).  `rmse` outputs are always host
  * memory.  The context owns only its workspace (Gram matrix, correlations,
  * per-signal slots, partial sums, staging buffers).
  *

@@ -112,6 +112,9 @@ struct dl_ctx {
   // side stream: the colptr scan overlaps the first pass of the atom update
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // host-buffer calls: the signals arrive in chunks on the side stream
+  static constexpr int kChunks = 4;
+  cudaEvent_t ev_chunk[kChunks] = {};
   // optional per-phase timing with CUDA events recorded on the context's stream
   bool prof = false;
   cudaEvent_t ev[9] = {};
@@ -136,6 +139,8 @@ void free_ctx(dl_ctx* c) {
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  for (cudaEvent_t e : c->ev_chunk)
+    if (e) cudaEventDestroy(e);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->st2) cudaStreamDestroy(c->st2);
   void* ptrs[] = {c->G, c->A0, c->Dhi, c->Dlo, c->Ylp, c->Ysc, c->Dlp, c->Dsc, c->rs_list,
@@ -360,9 +365,69 @@ cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const
   return e;
 }
 
+// Whether a call with host buffers overlaps the upload of Y with the first
+// iteration's coding pass: plain FP32 tensor-core path, at least kChunks x 128 signals.
+bool staged_ok(dl_ctx* c, const float* dY, const float* dD, int64_t m) {
+  return !c->prop && !lp_ok(c) && tc_ok(c, dY, dD) && m >= (int64_t)dl_ctx::kChunks * 128;
+}
+
+// The coding pass with Y still on the host: Y is copied in kChunks pieces on the
+// side stream, and the correlations (the Gram matrix with the first piece), the
+// OMP and the FP64 re-solve of each piece start as soon as it has arrived.
+// dY is the device staging buffer the pieces go to.  Returns the kernel count.
+cudaError_t enq_omp_staged(dl_ctx* c, const float* hostY, const float* dY, int64_t m,
+                           const float* D, int s, int* kernels) {
+  const int64_t p = c->p;
+  const int64_t chunk = ((m + dl_ctx::kChunks - 1) / dl_ctx::kChunks + 127) / 128 * 128;
+  cudaError_t e;
+  int k = 0;
+  mark(c, 0);
+  if ((e = dlk::split_tf32(D, (int64_t)c->n * c->p, c->Dhi, c->Dlo, c->st)) != cudaSuccess) return e;
+  ++k;
+  mark(c, 1);
+  if ((e = cudaEventRecord(c->ev_fork, c->st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(c->st2, c->ev_fork, 0)) != cudaSuccess) return e;
+  int nch = 0;
+  for (int64_t off = 0; off < m; off += chunk, ++nch) {
+    const int64_t mk = off + chunk <= m ? chunk : m - off;
+    e = cudaMemcpyAsync((float*)dY + off * p, hostY + off * p, sizeof(float) * (size_t)(mk * p),
+                        cudaMemcpyHostToDevice, c->st2);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(c->ev_chunk[nch], c->st2)) != cudaSuccess) return e;
+  }
+  mark(c, 2);
+  for (int q = 0; q < nch; ++q) {
+    const int64_t off = q * chunk, mk = off + chunk <= m ? chunk : m - off;
+    const float* Yq = dY + off * p;
+    float* Aq = c->A0 + off * c->lda;
+    if ((e = cudaStreamWaitEvent(c->st, c->ev_chunk[q], 0)) != cudaSuccess) return e;
+    e = q == 0 ? dlk::corr_tf32x3_pair(Yq, mk, Aq, c->lda, D, c->n, c->G, c->n, c->Dhi, c->Dlo,
+                                       c->n, c->p, c->err, c->st)
+               : dlk::corr_tf32x3(Yq, mk, c->Dhi, c->Dlo, c->n, c->p, Aq, c->lda, c->err, c->st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
+    e = dlk::omp_batch(Aq, c->lda, c->G, c->n, Yq, c->p, mk, s, c->sidx + off * s,
+                       c->sval + off * s, c->scnt + off, c->err, c->rs_list, c->rs_count,
+                       (int)c->m_max, c->cfg_omp_warps, nullptr, c->st);
+    if (e != cudaSuccess) return e;
+    e = dlk::omp_resolve64(Yq, c->p, D, c->n, s, c->rs_list, c->rs_count, (int)c->m_max,
+                           c->rs_scratch, c->sidx + off * s, c->sval + off * s, c->scnt + off,
+                           c->st);
+    if (e != cudaSuccess) return e;
+    k += 3;
+  }
+  mark(c, 3);
+  *kernels = k;
+  return cudaSuccess;
+}
+
+// hostY: when given, Y is uploaded into the staging buffer Y by the coding pass
+// itself (enq_omp_staged); staged_kernels then receives that pass's kernel count.
 cudaError_t enq_iteration(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int64_t* colptr,
-                          int32_t* rowidx, float* val) {
-  cudaError_t e = enq_omp(c, Y, m, D, s);
+                          int32_t* rowidx, float* val, const float* hostY = nullptr,
+                          int* staged_kernels = nullptr) {
+  cudaError_t e = hostY ? enq_omp_staged(c, hostY, Y, m, D, s, staged_kernels)
+                        : enq_omp(c, Y, m, D, s);
   if (e != cudaSuccess) return e;
   // colptr scan on the side stream, concurrent with the accumulation and the atom update
   if ((e = cudaEventRecord(c->ev_fork, c->st)) != cudaSuccess) return e;
@@ -435,6 +500,8 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
   ok = ok && cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) == cudaSuccess &&
        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
+  for (cudaEvent_t& e : c->ev_chunk)
+    ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
   if (ok && precision != DL_FP32) {
     c->lp_kind = precision == DL_BF16 ? dlk::LP_BF16 : dlk::LP_E4M3;
     const size_t esz = precision == DL_BF16 ? 2 : 1;
@@ -577,11 +644,11 @@ int omp_code(dl_ctx* c, const float* Y, int64_t m, const float* D, int s, int64_
   DL_CHECK(dlk::slots_to_csc(c->sidx, c->sval, c->scnt, m, s, dcp, dri, dv, c->st));
   c->launches += c->omp_kernels[0] + kKernelsScan + 1;
   if (kind == 0) {
+    // all s*m entries (the caller's capacity), so no synchronisation is needed to learn nnz;
+    // entries past colptr[m] are unspecified
     DL_CHECK(cudaMemcpyAsync(colptr, dcp, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyDeviceToHost, c->st));
-    DL_CHECK(cudaStreamSynchronize(c->st));
-    const int64_t nnz = colptr[m];
-    DL_CHECK(cudaMemcpyAsync(rowidx, dri, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost, c->st));
-    DL_CHECK(cudaMemcpyAsync(val, dv, sizeof(float) * (size_t)nnz, cudaMemcpyDeviceToHost, c->st));
+    DL_CHECK(cudaMemcpyAsync(rowidx, dri, sizeof(int32_t) * (size_t)m * s, cudaMemcpyDeviceToHost, c->st));
+    DL_CHECK(cudaMemcpyAsync(val, dv, sizeof(float) * (size_t)m * s, cudaMemcpyDeviceToHost, c->st));
     return take_device_error(c);
   }
   return DL_OK;
@@ -650,15 +717,18 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
   int64_t* dcp = colptr;
   int32_t* dri = rowidx;
   float* dv = val;
+  bool staged = false;
   if (kind == 0) {
     if ((rc = ensure_staging(c))) return rc;
-    DL_CHECK(cudaMemcpyAsync(c->hY, Y, sizeof(float) * (size_t)m * c->p, cudaMemcpyHostToDevice, c->st));
-    DL_CHECK(cudaMemcpyAsync(c->hD, D, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyHostToDevice, c->st));
     dY = c->hY;
     dD = c->hD;
     dcp = c->hcolptr;
     dri = c->hrowidx;
     dv = c->hval;
+    staged = staged_ok(c, dY, dD, m);
+    if (!staged)
+      DL_CHECK(cudaMemcpyAsync(c->hY, Y, sizeof(float) * (size_t)m * c->p, cudaMemcpyHostToDevice, c->st));
+    DL_CHECK(cudaMemcpyAsync(c->hD, D, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyHostToDevice, c->st));
   }
   DL_CHECK(cudaMemsetAsync(c->iter, 0, sizeof(int), c->st));
   const void* key[5] = {dY, dD, dcp, dri, dv};
@@ -683,6 +753,22 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
     c->learned_now = learned;
     cudaGraphExec_t& gx = learned ? c->gexec_learned : c->gexec;
     int& seen = learned ? c->gkey_seen_l : c->gkey_seen;
+    if (staged && it == 0) {
+      // first iteration of a host-buffer call: upload overlapped with the coding pass
+      int ko = 0;
+      DL_CHECK(enq_iteration(c, dY, m, dD, s, dcp, dri, dv, Y, &ko));
+      c->launches += ko + kKernelsScan + c->jau_kernels;
+      if (c->prof) {
+        DL_CHECK(cudaStreamSynchronize(c->st));
+        for (int k = 0; k < 8; ++k) {
+          float ms = 0.f;
+          DL_CHECK(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+          c->phase_ms[k] += ms;
+        }
+        c->phase_count++;
+      }
+      continue;
+    }
     if (can_graph && seen >= 1 && !gx) {
       cudaGraph_t graph = nullptr;
       DL_CHECK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
@@ -718,11 +804,11 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
   }
   if (kind == 0) {
     DL_CHECK(cudaMemcpyAsync(D, dD, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyDeviceToHost, c->st));
+    // all s*m entries (the caller's capacity), so no synchronisation is needed to learn nnz;
+    // entries past colptr[m] are unspecified
     DL_CHECK(cudaMemcpyAsync(colptr, dcp, sizeof(int64_t) * (size_t)(m + 1), cudaMemcpyDeviceToHost, c->st));
-    DL_CHECK(cudaStreamSynchronize(c->st));
-    const int64_t nnz = colptr[m];
-    DL_CHECK(cudaMemcpyAsync(rowidx, dri, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost, c->st));
-    DL_CHECK(cudaMemcpyAsync(val, dv, sizeof(float) * (size_t)nnz, cudaMemcpyDeviceToHost, c->st));
+    DL_CHECK(cudaMemcpyAsync(rowidx, dri, sizeof(int32_t) * (size_t)m * s, cudaMemcpyDeviceToHost, c->st));
+    DL_CHECK(cudaMemcpyAsync(val, dv, sizeof(float) * (size_t)m * s, cudaMemcpyDeviceToHost, c->st));
   }
   if (rmse)
     DL_CHECK(cudaMemcpyAsync(rmse, c->rmse, sizeof(double) * 2 * (size_t)iters,
