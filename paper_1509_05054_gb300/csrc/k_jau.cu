@@ -296,30 +296,20 @@ __global__ void __launch_bounds__(ROW_THREADS, 4) rows4_kernel(
       const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
       const float xx = __shfl_sync(FULL, t < 8 ? x0 : x1, gbase + (t & 7));
       float dot = 0.f;
-      if (t < c) {
+      float4 dn[RV];
 #pragma unroll
-        for (int q = 0; q < RV; ++q) {
-          const int v = g + 8 * q;
-          if (v < pv) dot = f4_dot(e[q], __ldg(N4 + (size_t)jj * pv + v), dot);
-        }
+      for (int q = 0; q < RV; ++q) {
+        const int v = g + 8 * q;
+        dn[q] = (t < c && v < pv) ? __ldg(N4 + (size_t)jj * pv + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+        dot = f4_dot(e[q], dn[q], dot);
       }
       dot += __shfl_xor_sync(FULL, dot, 4);
       dot += __shfl_xor_sync(FULL, dot, 2);
       dot += __shfl_xor_sync(FULL, dot, 1);
       xn[t] = (t < c) ? fmaf(__ldg(C + jj), xx, dot) : 0.f;
-    }
-    // residual with the updated atoms: y - D' x'
+      // residual with the updated atoms, y - D' x', from the same rows of D'
 #pragma unroll
-    for (int t = 0; t < SMAX; ++t) {
-      if (t >= cmax) break;
-      const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
-      if (t < c) {
-#pragma unroll
-        for (int q = 0; q < RV; ++q) {
-          const int v = g + 8 * q;
-          if (v < pv) y[q] = f4_fma(-xn[t], __ldg(N4 + (size_t)jj * pv + v), y[q]);
-        }
-      }
+      for (int q = 0; q < RV; ++q) y[q] = f4_fma(-xn[t], dn[q], y[q]);
     }
 #pragma unroll
     for (int q = 0; q < RV; ++q) e2 = f4_dot(y[q], y[q], e2);
