@@ -161,6 +161,21 @@ int dl_iterate(dl_ctx* ctx, const float* Y, int64_t m, float* D, int s, int iter
                int64_t* colptr, int32_t* rowidx, float* val, double* rmse);
 
 /*
+ * dl_set_group_size -- group size ntilde of the atom-update stage (Algorithm 1
+ * steps 2-5, Section 3): the atoms are updated in groups of ntilde consecutive
+ * atoms [k*ntilde, (k+1)*ntilde), one group after another; the atoms of one
+ * group are updated from the same error E = Y - D X (Eq. 3, Eq. 5), which for
+ * later groups already includes the atoms and coefficients updated by the
+ * earlier ones.  ntilde = n (the default) is the fully parallel Jacobi form
+ * PAK-SVD; ntilde = 1 the sequential Gauss-Seidel form AK-SVD.  A group size
+ * below n costs one pass over the signals per group and needs the float4 data
+ * path (p % 4 == 0, Y and D 16-byte aligned): jau_update and dl_iterate return
+ * DL_ENOTIMPL otherwise.  Applies to later jau_update / dl_iterate calls.
+ * Returns DL_OK, or DL_EINVAL unless 1 <= ntilde <= n.
+ */
+int dl_set_group_size(dl_ctx* ctx, int ntilde);
+
+/*
  * dl_gram -- G = D^T D (n x n, row-major, device), the Gram matrix Batch-OMP
  * works from (the OMP-Box tool of Section 4).  D and G are device pointers.
  * Asynchronous.  Returns DL_OK, DL_EINVAL or DL_ECUDA.

@@ -54,6 +54,7 @@ struct dl_ctx {
   float* G = nullptr;
   float* A0 = nullptr;
   int jau_kernels = 5;   // kernel launches of the last enqueued JAU update
+  int ntilde = 0;        // group size of the atom update (0 or n: all atoms at once)
   int omp_kernels[2] = {5, 5};  // ... of the last enqueued coding pass (plain, learned)
   float* Dhi = nullptr;  // TF32 head / tail of D for the tensor-core correlations
   float* Dlo = nullptr;
@@ -342,22 +343,47 @@ cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s)
 }
 
 // join: when given, colptr is produced on the side stream and the row pass waits for it.
+// Group size in effect: groups of ntilde consecutive atoms, updated one group
+// after another (Algorithm 1 steps 2-5); ntilde = n is the Jacobi form.
+int group_size(dl_ctx* c) { return c->ntilde > 0 && c->ntilde < c->n ? c->ntilde : c->n; }
+
+// join: when given, colptr is produced on the side stream and the row pass waits for it.
 cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const int64_t* colptr,
                     int32_t* rowidx_out, float* val_out, cudaEvent_t join) {
   c->jw.nb_accum = dlk::jau_accum_blocks(c->p, c->n, c->cfg_acc_mult);
   c->jw.nb_row = dlk::jau_row_blocks(c->cfg_row_per_sm);
-  c->jau_kernels = dlk::jau_launches(c->p, Y, D);
+  const int nt = group_size(c);
+  const int ngroups = (c->n + nt - 1) / nt;
+  // (groups need the float4 passes; the entry points check this before enqueuing)
+  c->jau_kernels = ngroups == 1 ? dlk::jau_launches(c->p, Y, D) : 4 * ngroups + 1;
   mark(c, 4);
-  cudaError_t e = dlk::jau_accumulate(Y, c->p, m, D, c->n, s, c->sidx, c->sval, c->scnt, c->jw,
-                                      c->err, c->st);
-  if (e != cudaSuccess) return e;
-  mark(c, 5);
-  e = dlk::jau_atoms(D, c->p, c->n, c->jw, c->st);
-  if (e != cudaSuccess) return e;
-  mark(c, 6);
-  if (join && (e = cudaStreamWaitEvent(c->st, join, 0)) != cudaSuccess) return e;
-  e = dlk::jau_rows(Y, c->p, m, D, c->n, s, c->sidx, c->sval, c->scnt, c->jw, colptr, rowidx_out,
-                    val_out, c->st);
+  cudaError_t e = cudaSuccess;
+  for (int a0 = 0; a0 < c->n; a0 += nt) {
+    const int a1 = a0 + nt < c->n ? a0 + nt : c->n;
+    c->jw.a0 = ngroups == 1 ? 0 : a0;
+    c->jw.a1 = ngroups == 1 ? 0 : a1;
+    c->jw.energies = a0 == 0;  // the error of the coding pass, before any atom moves
+    e = dlk::jau_accumulate(Y, c->p, m, D, c->n, s, c->sidx, c->sval, c->scnt, c->jw, c->err,
+                            c->st);
+    if (e != cudaSuccess) break;
+    if (a0 == 0) mark(c, 5);
+    if ((e = dlk::jau_atoms(D, c->p, c->n, c->jw, c->st)) != cudaSuccess) break;
+    if (a0 == 0) {
+      mark(c, 6);
+      if (join && (e = cudaStreamWaitEvent(c->st, join, 0)) != cudaSuccess) break;
+    }
+    e = dlk::jau_rows(Y, c->p, m, D, c->n, s, c->sidx, c->sval, c->scnt, c->jw, colptr,
+                      rowidx_out, val_out, c->st);
+    if (e != cudaSuccess) break;
+    // the next group works from the atoms updated so far
+    if (a1 < c->n)
+      e = cudaMemcpyAsync(D + (size_t)a0 * c->p, c->jw.Dn + (size_t)a0 * c->p,
+                          sizeof(float) * (size_t)(a1 - a0) * c->p, cudaMemcpyDeviceToDevice,
+                          c->st);
+    if (e != cudaSuccess) break;
+  }
+  c->jw.a0 = c->jw.a1 = 0;
+  c->jw.energies = true;
   if (e != cudaSuccess) return e;
   mark(c, 7);
   e = dlk::jau_finalize(c->jw, c->rmse, c->iter, D, c->n, c->p, c->st);
@@ -547,6 +573,13 @@ int dl_sync(dl_ctx* c) {
 
 int64_t dl_kernel_launches(dl_ctx* c) { return c ? c->launches : 0; }
 
+int dl_set_group_size(dl_ctx* c, int ntilde) {
+  if (!c || ntilde < 1 || ntilde > c->n) return DL_EINVAL;
+  if (ntilde != c->ntilde) c->gkey_m = -1;  // captured iterations no longer apply
+  c->ntilde = ntilde;
+  return DL_OK;
+}
+
 int dl_set_profiling(dl_ctx* c, int on) {
   if (!c) return DL_EINVAL;
   DevGuard g(c->dev);
@@ -663,6 +696,9 @@ int jau_update(dl_ctx* c, const float* Y, int64_t m, float* D, const int64_t* co
   if (ptr_kind(D) != kind || ptr_kind(colptr) != kind || ptr_kind(rowidx) != kind ||
       ptr_kind(val) != kind)
     return DL_EINVAL;
+  if (group_size(c) < c->n && (c->p % 4 != 0 ||
+                                (kind == 1 && !dlk::jau_vec4(c->p, Y, D))))
+    return DL_ENOTIMPL;
   DevGuard g(c->dev);
   const int s = c->s_max;
   const float* dY = Y;
@@ -710,6 +746,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
       ptr_kind(val) != kind)
     return DL_EINVAL;
   if (iters == 0) return DL_OK;
+  if (kind == 1 && group_size(c) < c->n && !dlk::jau_vec4(c->p, Y, D)) return DL_ENOTIMPL;
   DevGuard g(c->dev);
   if ((rc = ensure_rmse(c, iters))) return rc;
   const float* dY = Y;
@@ -726,6 +763,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
     dri = c->hrowidx;
     dv = c->hval;
     staged = staged_ok(c, dY, dD, m);
+    if (group_size(c) < c->n && !dlk::jau_vec4(c->p, dY, dD)) return DL_ENOTIMPL;
     if (!staged)
       DL_CHECK(cudaMemcpyAsync(c->hY, Y, sizeof(float) * (size_t)m * c->p, cudaMemcpyHostToDevice, c->st));
     DL_CHECK(cudaMemcpyAsync(c->hD, D, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyHostToDevice, c->st));

@@ -103,6 +103,11 @@ struct JauWork {
   float* C;         // [n]   d_j^T d_j'
   int nb_accum;
   int nb_row;
+  // group of atoms [a0, a1) being updated (a1 = 0: all n, the Jacobi form); the
+  // float4 passes then accumulate and update only slots of the group, and
+  // energies selects whether pass A writes the (||E||^2, ||Y||^2) partials
+  int a0 = 0, a1 = 0;
+  bool energies = true;
 };
 // Grid sizes: mult selects 1x/2x the base CTA count of the accumulation pass
 // and 2/4/8 CTAs per SM for the row pass; *_max give the partial-buffer sizes.

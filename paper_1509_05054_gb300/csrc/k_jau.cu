@@ -163,7 +163,8 @@ template <int RV, int SMAX>
 __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
     const float* __restrict__ Y, int p, int64_t m, const float* __restrict__ D, int n, int s,
     const int32_t* __restrict__ idx, const float* __restrict__ val, const int32_t* __restrict__ cnt,
-    float* __restrict__ U, double* __restrict__ epart, int* __restrict__ err) {
+    float* __restrict__ U, double* __restrict__ epart, int* __restrict__ err, int a0, int a1,
+    int energies) {
   __shared__ float rsh[kMaxAtoms];
   __shared__ double red[ACC4_THREADS / 32];
   for (int j = threadIdx.x; j < n; j += blockDim.x) rsh[j] = 0.f;
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
       if (t >= cmax) break;
       const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
       const float xx = __shfl_sync(FULL, t < 8 ? x0 : x1, gbase + (t & 7));
-      if (t < c) {
+      if (t < c && jj >= a0 && jj < a1) {
 #pragma unroll
         for (int q = 0; q < RV; ++q) {
           const int v = g + 8 * q;
@@ -233,21 +234,23 @@ __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
     if (rsh[j] != 0.f) atomicAdd(Uc + np + j, rsh[j]);
   const double see = block_sum_d((double)ee, red);
   const double syy = block_sum_d((double)yy, red);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && energies) {
     epart[2 * blockIdx.x] = see;
     epart[2 * blockIdx.x + 1] = syy;
   }
 }
 
 // Pass B, float4 form: e = y - D x; x_t' = e.d'_{j_t} + c_{j_t} x_t for all t
-// (independent dot products), then y - D' x'.
-template <int RV, int SMAX>
+// (independent dot products), then y - D' x'.  GROUP: only slots whose atom is
+// in [a0, a1) are updated; the others keep x_t and their current atom in the
+// residual.
+template <int RV, int SMAX, bool GROUP>
 __global__ void __launch_bounds__(ROW_THREADS, 4) rows4_kernel(
     const float* __restrict__ Y, int p, int64_t m, const float* __restrict__ D,
     const float* __restrict__ Dn, const float* __restrict__ C, int s,
     const int32_t* __restrict__ idx, float* __restrict__ val, const int32_t* __restrict__ cnt,
     const int64_t* __restrict__ colptr, int32_t* __restrict__ csc_rowidx,
-    float* __restrict__ csc_val, double* __restrict__ epart) {
+    float* __restrict__ csc_val, double* __restrict__ epart, int a0, int a1) {
   __shared__ double red[ROW_THREADS / 32];
   const int lane = threadIdx.x & 31;
   const int g = lane & 7, gbase = lane & ~7;
@@ -255,6 +258,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 4) rows4_kernel(
   const float4* __restrict__ Y4 = (const float4*)Y;
   const float4* __restrict__ D4 = (const float4*)D;
   const float4* __restrict__ N4 = (const float4*)Dn;
+  (void)a0;
+  (void)a1;
   float e2 = 0.f;
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
   const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
@@ -281,10 +286,15 @@ __global__ void __launch_bounds__(ROW_THREADS, 4) rows4_kernel(
       const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
       const float xx = __shfl_sync(FULL, t < 8 ? x0 : x1, gbase + (t & 7));
       if (t < c) {
+        const bool other = GROUP && (jj < a0 || jj >= a1);  // stays: also in the final residual
 #pragma unroll
         for (int q = 0; q < RV; ++q) {
           const int v = g + 8 * q;
-          if (v < pv) e[q] = f4_fma(-xx, __ldg(D4 + (size_t)jj * pv + v), e[q]);
+          if (v < pv) {
+            const float4 d = __ldg(D4 + (size_t)jj * pv + v);
+            e[q] = f4_fma(-xx, d, e[q]);
+            if (other) y[q] = f4_fma(-xx, d, y[q]);
+          }
         }
       }
     }
@@ -295,21 +305,22 @@ __global__ void __launch_bounds__(ROW_THREADS, 4) rows4_kernel(
       if (t >= cmax) break;
       const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
       const float xx = __shfl_sync(FULL, t < 8 ? x0 : x1, gbase + (t & 7));
+      const bool upd = t < c && (!GROUP || (jj >= a0 && jj < a1));
       float dot = 0.f;
       float4 dn[RV];
 #pragma unroll
       for (int q = 0; q < RV; ++q) {
         const int v = g + 8 * q;
-        dn[q] = (t < c && v < pv) ? __ldg(N4 + (size_t)jj * pv + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+        dn[q] = (upd && v < pv) ? __ldg(N4 + (size_t)jj * pv + v) : make_float4(0.f, 0.f, 0.f, 0.f);
         dot = f4_dot(e[q], dn[q], dot);
       }
       dot += __shfl_xor_sync(FULL, dot, 4);
       dot += __shfl_xor_sync(FULL, dot, 2);
       dot += __shfl_xor_sync(FULL, dot, 1);
-      xn[t] = (t < c) ? fmaf(__ldg(C + jj), xx, dot) : 0.f;
+      xn[t] = upd ? fmaf(__ldg(C + jj), xx, dot) : (t < c ? xx : 0.f);
       // residual with the updated atoms, y - D' x', from the same rows of D'
 #pragma unroll
-      for (int q = 0; q < RV; ++q) y[q] = f4_fma(-xn[t], dn[q], y[q]);
+      for (int q = 0; q < RV; ++q) y[q] = f4_fma(upd ? -xn[t] : 0.f, dn[q], y[q]);
     }
 #pragma unroll
     for (int q = 0; q < RV; ++q) e2 = f4_dot(y[q], y[q], e2);
@@ -387,11 +398,12 @@ __global__ void reduce_kernel(const float* __restrict__ Upart, int nslices, int 
 
 // One warp per atom: v = U_j + r_j d_j; d' = v/||v|| (d kept if v = 0); c = d^T d'.
 template <int PL>
+// Atoms a0 <= j < a1.
 __global__ void atoms_kernel(const float* __restrict__ D, int p, int n, const float* __restrict__ U,
-                             float* __restrict__ Dn, float* __restrict__ C) {
+                             float* __restrict__ Dn, float* __restrict__ C, int a0, int a1) {
   const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (j >= n) return;
+  const int j = a0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= a1) return;
   const float rj = U[(size_t)n * p + j];
   float d[PL], v[PL];
   float vv = 0.f;
@@ -736,7 +748,8 @@ cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int
     if (e != cudaSuccess) return e;
 #define DL_ACC4(RV, SM)                                                                  \
   accum4_kernel<RV, SM><<<w.nb_accum, ACC4_THREADS, 0, st>>>(Y, p, m, D, n, s, idx, val, cnt, \
-                                                             w.Upart, w.epart_a, err)
+                                                             w.Upart, w.epart_a, err, w.a0,   \
+                                                             w.a1 > 0 ? w.a1 : n, (int)w.energies)
 #define DL_ACC4_S(RV) \
   if (s <= 8) DL_ACC4(RV, 8); else DL_ACC4(RV, 16)
     if (p <= 32) { DL_ACC4_S(1); }
@@ -773,26 +786,37 @@ cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int
 }
 
 cudaError_t jau_atoms(const float* D, int p, int n, const JauWork& w, cudaStream_t st) {
-  const int blocks = (n + 7) / 8;
-  if (p <= 32) atoms_kernel<1><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C);
-  else if (p <= 64) atoms_kernel<2><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C);
-  else if (p <= 96) atoms_kernel<3><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C);
-  else atoms_kernel<4><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C);
+  const int a0 = w.a0, a1 = w.a1 > 0 ? w.a1 : n;
+  const int blocks = (a1 - a0 + 7) / 8;
+  if (blocks <= 0) return cudaSuccess;
+  if (p <= 32) atoms_kernel<1><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C, a0, a1);
+  else if (p <= 64) atoms_kernel<2><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C, a0, a1);
+  else if (p <= 96) atoms_kernel<3><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C, a0, a1);
+  else atoms_kernel<4><<<blocks, 256, 0, st>>>(D, p, n, w.U, w.Dn, w.C, a0, a1);
   return cudaGetLastError();
 }
 
 cudaError_t jau_rows(const float* Y, int p, int64_t m, const float* D, int n, int s,
                      const int32_t* idx, float* val, const int32_t* cnt, const JauWork& w,
                      const int64_t* colptr, int32_t* csc_rowidx, float* csc_val, cudaStream_t st) {
-  (void)n;
   const int nb = w.nb_row;
+  const int a1 = w.a1 > 0 ? w.a1 : n;
+  const bool grouped = w.a0 > 0 || a1 < n;
 #define DL_ROWS(PL)                                                                              \
   rows_kernel<PL><<<nb, ROW_THREADS, 0, st>>>(Y, p, m, D, w.Dn, w.C, s, idx, val, cnt, colptr, \
                                               csc_rowidx, csc_val, w.epart_b)
   if (jau_vec4(p, Y, D)) {
 #define DL_ROWS4(RV, SM)                                                                         \
-  rows4_kernel<RV, SM><<<nb, ROW_THREADS, 0, st>>>(Y, p, m, D, w.Dn, w.C, s, idx, val, cnt, colptr, \
-                                                   csc_rowidx, csc_val, w.epart_b)
+  do {                                                                                         \
+    if (grouped)                                                                               \
+      rows4_kernel<RV, SM, true><<<nb, ROW_THREADS, 0, st>>>(Y, p, m, D, w.Dn, w.C, s, idx, val, \
+                                                             cnt, colptr, csc_rowidx, csc_val,  \
+                                                             w.epart_b, w.a0, a1);              \
+    else                                                                                       \
+      rows4_kernel<RV, SM, false><<<nb, ROW_THREADS, 0, st>>>(Y, p, m, D, w.Dn, w.C, s, idx,    \
+                                                              val, cnt, colptr, csc_rowidx,     \
+                                                              csc_val, w.epart_b, 0, n);        \
+  } while (0)
 #define DL_ROWS4_S(RV) \
   if (s <= 8) DL_ROWS4(RV, 8); else DL_ROWS4(RV, 16)
     if (p <= 32) { DL_ROWS4_S(1); }

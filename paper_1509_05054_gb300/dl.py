@@ -65,6 +65,7 @@ def load(build_if_missing: bool = True):
         lib.dl_kernel_launches.argtypes = [P]
         lib.dl_kernel_launches.restype = i64
         lib.dl_set_profiling.argtypes = [P, i32]
+        lib.dl_set_group_size.argtypes = [P, i32]
         lib.dl_gram.argtypes = [P, P, P]
         lib.dl_correlate.argtypes = [P, P, i64, P, P]
         lib.dl_uses_tensor_cores.argtypes = [P]
@@ -158,6 +159,10 @@ def dl_kernel_launches(ctx: int) -> int:
 
 
 PHASES = ("gram", "correlations", "omp", "colptr_scan", "accumulate", "atoms", "rows", "finalize")
+
+
+def dl_set_group_size(ctx: int, ntilde: int) -> None:
+    _check(load().dl_set_group_size(ctx, ntilde), "dl_set_group_size")
 
 
 def dl_set_profiling(ctx: int, on: bool) -> None:
