@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-problems measurement")
     ap.add_argument("--batched-iters", type=int, default=20)
+    ap.add_argument("--group-sizes", default="128,32",
+                    help="atom-update group sizes ntilde < n to time beside the Jacobi form "
+                         "(empty: none)")
     ap.add_argument("--m", type=int, default=None,
                     help="override the number of signals (profiling of smaller cases)")
     return ap.parse_args()
@@ -373,6 +376,10 @@ def run_ours(args):
                "d2h_bytes_per_step": 4 * n * p + 8 * (m + 1) + 8 * m * s + 16 + 4,
                "steps": args.e2e_steps}
 
+    groups = None
+    if args.group_sizes:
+        groups = run_groups(args, dl, torch, st, Yd, D0, colptr, rowidx, val, flush, m, p, n, s,
+                            plain_rmse)
     batched = None
     if not args.no_batched:
         batched = run_batched(args, dl, torch, st)
@@ -403,7 +410,7 @@ def run_ours(args):
                     "equal_rmse": f"final relative RMSE after {RMSE_ITERS} iterations within "
                                   f"{100 * EQUAL_RMSE:.0f}% of the plain FP32 form"}),
                 "roofline": roof, "phases_ms": phases, "phase_roofline": per_phase,
-                "forms": forms, "batched": batched, "learned": learned,
+                "forms": forms, "group_size": groups, "batched": batched, "learned": learned,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if pg:
@@ -456,6 +463,43 @@ def run_batched(args, dl, torch, st):
             "shapes": [dict(p=q["p"], n=q["n"], m=q["m"], s=q["s"], cfg=c,
                             final_rmse=float(rm[k, -1, 1]))
                        for k, (q, c) in enumerate(zip(probs, cfgs))]}
+
+
+def run_groups(args, dl, torch, st, Yd, D0, colptr, rowidx, val, flush, m, p, n, s, plain_rmse):
+    """The atom update with group size ntilde < n (groups updated one after
+    another): time per iteration, and the final RMSE after RMSE_ITERS
+    iterations against the Jacobi form's."""
+    out = {}
+    for nt in (int(x) for x in args.group_sizes.split(",") if x):
+        if nt < 1 or nt >= n:
+            continue
+        ctx = dl.dl_init(p, n, m, s, 0, st)
+        dl.dl_set_group_size(ctx, nt)
+        Dd = D0.clone()
+        with torch.cuda.stream(st):
+            for _ in range(3):
+                flush.zero_()
+                dl.dl_iterate(ctx, Yd, m, Dd, s, 1, colptr, rowidx, val, None)
+        st.synchronize()
+        steps = 5
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        with torch.cuda.stream(st):
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(st)
+                dl.dl_iterate(ctx, Yd, m, Dd, s, 1, colptr, rowidx, val, None)
+                ev[k][1].record(st)
+        st.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        Dq = D0.clone()
+        rm = np.zeros(2 * RMSE_ITERS)
+        dl.dl_iterate(ctx, Yd, m, Dq, s, RMSE_ITERS, colptr, rowidx, val, rm)
+        dl.dl_destroy(ctx)
+        out[str(nt)] = {"value": m / (ms * 1e-3), "unit": UNIT, "ms_per_iteration": ms,
+                        "groups": (n + nt - 1) // nt, "final_rmse": float(rm[-1]),
+                        "rmse_vs_jacobi": (float(rm[-1]) / plain_rmse - 1.0) if plain_rmse else None}
+    return out
 
 
 def run_learned(args, dl, torch, st):
