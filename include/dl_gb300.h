@@ -176,6 +176,20 @@ int dl_iterate(dl_ctx* ctx, const float* Y, int64_t m, float* D, int s, int iter
 int dl_set_group_size(dl_ctx* ctx, int ntilde);
 
 /*
+ * dl_set_update_rule -- how the atom-update stage treats each atom j of a group
+ * (Section 3; F = E_{I_j} + d_j x_{j,I_j}, Eq. 3):
+ *   DL_RULE_AKSVD (default)  d_j = F x^T / ||F x^T||, then x_{j,I_j} = F^T d_j
+ *                            (one power step, Eq. 5: PAK-SVD / AK-SVD);
+ *   DL_RULE_SGK              d_j = F x^T / (x x^T), normalised, coefficients
+ *                            unchanged (Eq. 6 and Algorithm 2: P-SGK / SGK).
+ * Both give the same atom direction; SGK leaves X as the coding pass made it.
+ * Applies to later jau_update / dl_iterate calls.  Returns DL_OK or DL_EINVAL.
+ */
+#define DL_RULE_AKSVD 0
+#define DL_RULE_SGK 1
+int dl_set_update_rule(dl_ctx* ctx, int rule);
+
+/*
  * dl_gram -- G = D^T D (n x n, row-major, device), the Gram matrix Batch-OMP
  * works from (the OMP-Box tool of Section 4).  D and G are device pointers.
  * Asynchronous.  Returns DL_OK, DL_EINVAL or DL_ECUDA.

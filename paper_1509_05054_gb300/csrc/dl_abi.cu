@@ -55,6 +55,7 @@ struct dl_ctx {
   float* A0 = nullptr;
   int jau_kernels = 5;   // kernel launches of the last enqueued JAU update
   int ntilde = 0;        // group size of the atom update (0 or n: all atoms at once)
+  int rule = DL_RULE_AKSVD;  // atom update rule
   int omp_kernels[2] = {5, 5};  // ... of the last enqueued coding pass (plain, learned)
   float* Dhi = nullptr;  // TF32 head / tail of D for the tensor-core correlations
   float* Dlo = nullptr;
@@ -363,6 +364,7 @@ cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const
     c->jw.a0 = ngroups == 1 ? 0 : a0;
     c->jw.a1 = ngroups == 1 ? 0 : a1;
     c->jw.energies = a0 == 0;  // the error of the coding pass, before any atom moves
+    c->jw.sgk = c->rule == DL_RULE_SGK;
     e = dlk::jau_accumulate(Y, c->p, m, D, c->n, s, c->sidx, c->sval, c->scnt, c->jw, c->err,
                             c->st);
     if (e != cudaSuccess) break;
@@ -577,6 +579,13 @@ int dl_set_group_size(dl_ctx* c, int ntilde) {
   if (!c || ntilde < 1 || ntilde > c->n) return DL_EINVAL;
   if (ntilde != c->ntilde) c->gkey_m = -1;  // captured iterations no longer apply
   c->ntilde = ntilde;
+  return DL_OK;
+}
+
+int dl_set_update_rule(dl_ctx* c, int rule) {
+  if (!c || (rule != DL_RULE_AKSVD && rule != DL_RULE_SGK)) return DL_EINVAL;
+  if (rule != c->rule) c->gkey_m = -1;  // captured iterations no longer apply
+  c->rule = rule;
   return DL_OK;
 }
 

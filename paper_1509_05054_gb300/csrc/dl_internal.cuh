@@ -108,6 +108,8 @@ struct JauWork {
   // energies selects whether pass A writes the (||E||^2, ||Y||^2) partials
   int a0 = 0, a1 = 0;
   bool energies = true;
+  // SGK rule (Eq. 6, P-SGK): atoms as in AK-SVD, coefficients left as they are
+  bool sgk = false;
 };
 // Grid sizes: mult selects 1x/2x the base CTA count of the accumulation pass
 // and 2/4/8 CTAs per SM for the row pass; *_max give the partial-buffer sizes.

@@ -243,14 +243,14 @@ __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
 // Pass B, float4 form: e = y - D x; x_t' = e.d'_{j_t} + c_{j_t} x_t for all t
 // (independent dot products), then y - D' x'.  GROUP: only slots whose atom is
 // in [a0, a1) are updated; the others keep x_t and their current atom in the
-// residual.
+// residual.  sgk: the coefficients stay (x' = x; SGK rule, Eq. 6).
 template <int RV, int SMAX, bool GROUP>
 __global__ void __launch_bounds__(ROW_THREADS, 4) rows4_kernel(
     const float* __restrict__ Y, int p, int64_t m, const float* __restrict__ D,
     const float* __restrict__ Dn, const float* __restrict__ C, int s,
     const int32_t* __restrict__ idx, float* __restrict__ val, const int32_t* __restrict__ cnt,
     const int64_t* __restrict__ colptr, int32_t* __restrict__ csc_rowidx,
-    float* __restrict__ csc_val, double* __restrict__ epart, int a0, int a1) {
+    float* __restrict__ csc_val, double* __restrict__ epart, int a0, int a1, int sgk) {
   __shared__ double red[ROW_THREADS / 32];
   const int lane = threadIdx.x & 31;
   const int g = lane & 7, gbase = lane & ~7;
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 4) rows4_kernel(
       dot += __shfl_xor_sync(FULL, dot, 4);
       dot += __shfl_xor_sync(FULL, dot, 2);
       dot += __shfl_xor_sync(FULL, dot, 1);
-      xn[t] = upd ? fmaf(__ldg(C + jj), xx, dot) : (t < c ? xx : 0.f);
+      xn[t] = upd && !sgk ? fmaf(__ldg(C + jj), xx, dot) : (t < c ? xx : 0.f);
       // residual with the updated atoms, y - D' x', from the same rows of D'
 #pragma unroll
       for (int q = 0; q < RV; ++q) y[q] = f4_fma(upd ? -xn[t] : 0.f, dn[q], y[q]);
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(ROW_THREADS) rows_kernel(
     const float* __restrict__ Dn, const float* __restrict__ C, int s,
     const int32_t* __restrict__ idx, float* __restrict__ val, const int32_t* __restrict__ cnt,
     const int64_t* __restrict__ colptr, int32_t* __restrict__ csc_rowidx,
-    float* __restrict__ csc_val, double* __restrict__ epart) {
+    float* __restrict__ csc_val, double* __restrict__ epart, int sgk) {
   __shared__ double red[ROW_THREADS / 32];
   const int lane = threadIdx.x & 31;
   const int g = lane & 7, gbase = lane & ~7;
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(ROW_THREADS) rows_kernel(
       dot += __shfl_xor_sync(0xffffffffu, dot, 2);
       dot += __shfl_xor_sync(0xffffffffu, dot, 1);
       if (t < c) {
-        const float xn = fmaf(__ldg(C + jj), xx, dot);
+        const float xn = sgk ? xx : fmaf(__ldg(C + jj), xx, dot);
         if (g == (t & 7)) {
           if (t < 8) nx0 = xn;
           else nx1 = xn;
@@ -804,18 +804,19 @@ cudaError_t jau_rows(const float* Y, int p, int64_t m, const float* D, int n, in
   const bool grouped = w.a0 > 0 || a1 < n;
 #define DL_ROWS(PL)                                                                              \
   rows_kernel<PL><<<nb, ROW_THREADS, 0, st>>>(Y, p, m, D, w.Dn, w.C, s, idx, val, cnt, colptr, \
-                                              csc_rowidx, csc_val, w.epart_b)
+                                              csc_rowidx, csc_val, w.epart_b, (int)w.sgk)
   if (jau_vec4(p, Y, D)) {
 #define DL_ROWS4(RV, SM)                                                                         \
   do {                                                                                         \
     if (grouped)                                                                               \
       rows4_kernel<RV, SM, true><<<nb, ROW_THREADS, 0, st>>>(Y, p, m, D, w.Dn, w.C, s, idx, val, \
                                                              cnt, colptr, csc_rowidx, csc_val,  \
-                                                             w.epart_b, w.a0, a1);              \
+                                                             w.epart_b, w.a0, a1, (int)w.sgk);  \
     else                                                                                       \
       rows4_kernel<RV, SM, false><<<nb, ROW_THREADS, 0, st>>>(Y, p, m, D, w.Dn, w.C, s, idx,    \
                                                               val, cnt, colptr, csc_rowidx,     \
-                                                              csc_val, w.epart_b, 0, n);        \
+                                                              csc_val, w.epart_b, 0, n,         \
+                                                              (int)w.sgk);                      \
   } while (0)
 #define DL_ROWS4_S(RV) \
   if (s <= 8) DL_ROWS4(RV, 8); else DL_ROWS4(RV, 16)

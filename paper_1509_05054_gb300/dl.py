@@ -66,6 +66,7 @@ def load(build_if_missing: bool = True):
         lib.dl_kernel_launches.restype = i64
         lib.dl_set_profiling.argtypes = [P, i32]
         lib.dl_set_group_size.argtypes = [P, i32]
+        lib.dl_set_update_rule.argtypes = [P, i32]
         lib.dl_gram.argtypes = [P, P, P]
         lib.dl_correlate.argtypes = [P, P, i64, P, P]
         lib.dl_uses_tensor_cores.argtypes = [P]
@@ -159,6 +160,13 @@ def dl_kernel_launches(ctx: int) -> int:
 
 
 PHASES = ("gram", "correlations", "omp", "colptr_scan", "accumulate", "atoms", "rows", "finalize")
+
+
+DL_RULE_AKSVD, DL_RULE_SGK = 0, 1
+
+
+def dl_set_update_rule(ctx: int, rule: int) -> None:
+    _check(load().dl_set_update_rule(ctx, rule), "dl_set_update_rule")
 
 
 def dl_set_group_size(ctx: int, ntilde: int) -> None:

@@ -115,3 +115,32 @@ def test_group_size_arguments(dl):
                       cp, ri, v, None)
     assert e.value.status == dl.DL_ENOTIMPL
     dl.dl_destroy(ctx)
+
+
+@pytest.mark.parametrize("ntilde", [256, 64])
+def test_sgk_rule_matches_oracle(dl, ntilde):
+    """P-SGK (Eq. 6, Algorithm 2): atoms from F x^T / (x x^T), normalised, the
+    coefficients left as the coding pass made them."""
+    name, m, s = "patch_n256", 2501, 6
+    Y, D, _ = synth.workload_inputs(name, m=m)
+    Y64, D64 = Y.astype(np.float64), D.astype(np.float64)
+    idx, val, cnt = oracle.omp(Y64, D64, s)
+    val32 = val.astype(np.float32).astype(np.float64)
+    D1_o, val1_o, _ = oracle.atom_update(Y64, D64, idx, val32, cnt, ntilde=ntilde,
+                                         rule=oracle.RULE_SGK)
+    np.testing.assert_array_equal(val1_o, val32)
+    p, n = D.shape[1], D.shape[0]
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    dl.dl_set_group_size(ctx, ntilde)
+    dl.dl_set_update_rule(ctx, dl.DL_RULE_SGK)
+    Dd = torch.from_numpy(D.copy()).cuda()
+    colptr, rowidx, v = _csc(idx, val, cnt, s)
+    rm = np.zeros(2)
+    dl.jau_update(ctx, torch.from_numpy(Y).cuda(), m, Dd, colptr, rowidx, v, rm)
+    with pytest.raises(dl.DLError):
+        dl.dl_set_update_rule(ctx, 7)
+    dl.dl_destroy(ctx)
+    np.testing.assert_allclose(Dd.cpu().numpy(), D1_o, rtol=0, atol=2e-5)
+    _, val1_g, _ = csc_to_slots(colptr.cpu().numpy(), rowidx.cpu().numpy(), v.cpu().numpy(), s)
+    np.testing.assert_allclose(val1_g, val32, rtol=0, atol=1e-7)
+    assert abs(rm[1] - oracle.rmse(Y64, D1_o, idx, val1_o, cnt)) <= 1e-5
