@@ -35,6 +35,7 @@ _lib = None
 
 RULE_AKSVD = 0
 RULE_SGK = 1
+RULE_NSGK = 2  # oracle_dl only: P-NSGK (Eq. 7), see atom_update_nsgk
 
 
 def build(force: bool = False) -> str:
@@ -62,6 +63,8 @@ def _load():
             lib.oracle_error_energy.argtypes = [i32, i64, P, P, i32, P, P, P, P, i32]
             lib.oracle_atom_update.argtypes = [i32, i32, i64, P, P, i32, P, P, P, i32, i32, i32,
                                                P, i32]
+            lib.oracle_atom_update_nsgk.argtypes = [i32, i32, i64, P, P, i32, P, P, P, P, P, P,
+                                                    i32, P, i32]
             lib.oracle_dl.argtypes = [i32, i32, i64, P, P, i32, i32, i32, i32, P, P, P, P, i32]
             lib.oracle_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -153,6 +156,24 @@ def atom_update(Y, D, idx, val, cnt, ntilde: int | None = None, rule: int = RULE
                                n if ntilde is None else int(ntilde), int(rule), int(only_atom),
                                ctypes.cast(ctypes.pointer(unused), ctypes.c_void_p), nthreads)
     return D, val, int(unused.value)
+
+
+def atom_update_nsgk(Y, D, idx, val, cnt, pidx, pval, pcnt, ntilde: int | None = None,
+                     nthreads: int = 0):
+    """P-NSGK atom-update stage (Eq. 7): SGK on Z = Y + D X_prev - D X with the
+    representations X_prev.  Returns (D_new, n_unused); X and X_prev unchanged."""
+    Y = _f64(Y)
+    D = _f64(D).copy()
+    m, p = Y.shape
+    n = D.shape[0]
+    s = idx.shape[1]
+    unused = ctypes.c_int(0)
+    args = [np.ascontiguousarray(idx, np.int32), _f64(val), np.ascontiguousarray(cnt, np.int32),
+            np.ascontiguousarray(pidx, np.int32), _f64(pval), np.ascontiguousarray(pcnt, np.int32)]
+    _load().oracle_atom_update_nsgk(p, n, m, _ptr(Y), _ptr(D), s, *[_ptr(a) for a in args],
+                                    n if ntilde is None else int(ntilde),
+                                    ctypes.cast(ctypes.pointer(unused), ctypes.c_void_p), nthreads)
+    return D, unused.value
 
 
 def jau(Y, D, idx, val, cnt, nthreads: int = 0):

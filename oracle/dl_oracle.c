@@ -407,7 +407,7 @@ static void build_index_sets(int n, int64_t m, int s, const int32_t* idx, const 
     free(fill);
 }
 
-enum { ORACLE_RULE_AKSVD = 0, ORACLE_RULE_SGK = 1 };
+enum { ORACLE_RULE_AKSVD = 0, ORACLE_RULE_SGK = 1, ORACLE_RULE_NSGK = 2 };
 
 /*
  * Atom-update stage with group size ntilde (Algorithm 1 steps 2-5, with the
@@ -496,9 +496,86 @@ int oracle_atom_update(int p, int n, int64_t m, const double* Y, double* D, int 
 }
 
 /*
+ * P-NSGK atom-update stage (Section 3, Eq. 7): SGK with the signal matrix Y
+ * replaced by Z = Y + D X_prev - D X, where D is the dictionary the iteration
+ * started from, X the representations its sparse coding produced and X_prev
+ * those at the beginning of the iteration; the representations entering the
+ * SGK update are X_prev's (supports and values).  For every group of ntilde
+ * consecutive atoms, E = Z - D X_prev with the current D; then for each atom j
+ * of the group, independently, with I_j the signals whose X_prev column uses j,
+ *     F = E_{I_j} + d_j xp_{j,I_j},   d_j = F xp^T / (xp xp^T),  d_j /= ||d_j||
+ * (atoms with an empty I_j, or F xp^T = 0, are left unchanged and counted).
+ * Neither X nor X_prev is modified.  With X_prev = X this is the SGK rule of
+ * oracle_atom_update.
+ */
+int oracle_atom_update_nsgk(int p, int n, int64_t m, const double* Y, double* D, int s,
+                            const int32_t* idx, const double* val, const int32_t* cnt,
+                            const int32_t* pidx, const double* pval, const int32_t* pcnt,
+                            int ntilde, int* unused, int nthreads) {
+    set_threads(nthreads);
+    if (ntilde < 1) ntilde = 1;
+    double* Z = (double*)malloc(sizeof(double) * (size_t)p * m);
+    double* E = (double*)malloc(sizeof(double) * (size_t)p * m);
+    int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t* slots = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m * s + 1));
+    double* Dnew = (double*)malloc(sizeof(double) * (size_t)p * n);
+    /* Z = (Y - D X) + D X_prev, with the entry dictionary */
+    form_error(p, m, Y, D, s, idx, val, cnt, Z);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i) {
+        double* z = Z + (size_t)i * p;
+        for (int u = 0; u < pcnt[i]; ++u) {
+            const double* d = D + (size_t)pidx[(size_t)i * s + u] * p;
+            double x = pval[(size_t)i * s + u];
+            for (int q = 0; q < p; ++q) z[q] += d[q] * x;
+        }
+    }
+    build_index_sets(n, m, s, pidx, pcnt, start, slots);
+    int n_unused = 0;
+    for (int g0 = 0; g0 < n; g0 += ntilde) {
+        int g1 = g0 + ntilde < n ? g0 + ntilde : n;
+        form_error(p, m, Z, D, s, pidx, pval, pcnt, E);   /* E = Z - D X_prev */
+        memcpy(Dnew, D, sizeof(double) * (size_t)p * n);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : n_unused)
+        for (int j = g0; j < g1; ++j) {
+            int64_t nI = start[j + 1] - start[j];
+            if (nI == 0) { n_unused++; continue; }
+            const double* dj = D + (size_t)j * p;
+            double* g = (double*)calloc((size_t)p, sizeof(double));
+            double xx = 0.0;
+            for (int64_t c = 0; c < nI; ++c) {
+                int64_t sl = slots[start[j] + c];
+                int64_t i = sl / s;
+                double x = pval[sl];
+                xx += x * x;
+                for (int q = 0; q < p; ++q) g[q] += (E[(size_t)i * p + q] + dj[q] * x) * x;
+            }
+            double gn = 0.0;
+            if (xx > 0.0) for (int q = 0; q < p; ++q) g[q] /= xx;
+            for (int q = 0; q < p; ++q) gn += g[q] * g[q];
+            double* dn = Dnew + (size_t)j * p;
+            if (gn > 0.0) {
+                double inv = 1.0 / sqrt(gn);
+                for (int q = 0; q < p; ++q) dn[q] = g[q] * inv;
+            } else {
+                n_unused++;
+                for (int q = 0; q < p; ++q) dn[q] = dj[q];
+            }
+            free(g);
+        }
+        memcpy(D, Dnew, sizeof(double) * (size_t)p * n);
+    }
+    if (unused) *unused = n_unused;
+    free(Z); free(E); free(start); free(slots); free(Dnew);
+    return 0;
+}
+
+/*
  * The DL iteration of Algorithm 1, repeated `iters` times: OMP with the
  * current D (step 1), then the atom-update stage with group size ntilde and
- * the chosen rule. rmse[2*k] is ||Y - D^(k) X^(k)||_F / ||Y||_F right after
+ * the chosen rule (AK-SVD, SGK, or P-NSGK with the representations of the
+ * previous iteration; the first iteration, having none, uses its own and so is
+ * P-SGK). rmse[2*k] is ||Y - D^(k) X^(k)||_F / ||Y||_F right after
  * sparse coding, rmse[2*k+1] the same with the updated D and (for AK-SVD)
  * updated X at the end of the iteration (Section 4.2 computes the errors at
  * the end of an iteration). On return idx/val/cnt hold the last X.
@@ -507,13 +584,37 @@ int oracle_dl(int p, int n, int64_t m, const double* Y, double* D, int s, int it
               int ntilde, int rule, int32_t* idx, double* val, int32_t* cnt, double* rmse,
               int nthreads) {
     double e2[2];
+    /* P-NSGK keeps the representations the iteration started from; the first
+       iteration has none and uses its own (it is then P-SGK) */
+    int32_t* pidx = NULL;
+    double* pval = NULL;
+    int32_t* pcnt = NULL;
+    if (rule == ORACLE_RULE_NSGK) {
+        pidx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m * s + 1));
+        pval = (double*)malloc(sizeof(double) * (size_t)(m * s + 1));
+        pcnt = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    }
     for (int it = 0; it < iters; ++it) {
         oracle_omp(p, n, m, Y, D, s, idx, val, cnt, NULL, nthreads);
         oracle_error_energy(p, m, Y, D, s, idx, val, cnt, e2, nthreads);
         if (rmse) rmse[2 * it] = e2[1] > 0 ? sqrt(e2[0] / e2[1]) : 0.0;
-        oracle_atom_update(p, n, m, Y, D, s, idx, val, cnt, ntilde, rule, -1, NULL, nthreads);
+        if (rule == ORACLE_RULE_NSGK) {
+            if (it == 0) {
+                memcpy(pidx, idx, sizeof(int32_t) * (size_t)(m * s));
+                memcpy(pval, val, sizeof(double) * (size_t)(m * s));
+                memcpy(pcnt, cnt, sizeof(int32_t) * (size_t)m);
+            }
+            oracle_atom_update_nsgk(p, n, m, Y, D, s, idx, val, cnt, pidx, pval, pcnt, ntilde,
+                                    NULL, nthreads);
+            memcpy(pidx, idx, sizeof(int32_t) * (size_t)(m * s));
+            memcpy(pval, val, sizeof(double) * (size_t)(m * s));
+            memcpy(pcnt, cnt, sizeof(int32_t) * (size_t)m);
+        } else {
+            oracle_atom_update(p, n, m, Y, D, s, idx, val, cnt, ntilde, rule, -1, NULL, nthreads);
+        }
         oracle_error_energy(p, m, Y, D, s, idx, val, cnt, e2, nthreads);
         if (rmse) rmse[2 * it + 1] = e2[1] > 0 ? sqrt(e2[0] / e2[1]) : 0.0;
     }
+    free(pidx); free(pval); free(pcnt);
     return 0;
 }

@@ -377,3 +377,63 @@ def test_table1_dictionary_recovery(s):
         se = 100.0 * np.std(res) / np.sqrt(len(res))
         tol = max(4.0, 3.0 * se)
         assert abs(mean - table[snr]) <= tol, (s, snr, mean, table[snr], tol)
+
+
+def _two_codings(seed):
+    """One problem coded twice: X from D0, X_prev from a perturbed dictionary
+    (different supports and values on many signals)."""
+    Y, D, idx, val, cnt = _sparse_problem(seed)
+    g = _rng(seed + 5)
+    Dp = _unit_rows(D + 0.2 * g.standard_normal(D.shape))
+    pidx, pval, pcnt = oracle.omp(Y, Dp, idx.shape[1])
+    assert np.mean(np.any(pidx != idx, axis=1)) > 0.2
+    return Y, D, idx, val, cnt, pidx, pval, pcnt
+
+
+@pytest.mark.parametrize("ntilde", [None, 7, 1])
+def test_nsgk_is_sgk_on_the_modified_signals(ntilde):
+    """P-NSGK (Eq. 7) = the SGK update (Eq. 6, pinned on its own) applied to the
+    signals Z = Y + D X_prev - D X with the representations X_prev, for any group
+    size: Z is formed here with dense products, independently of the oracle."""
+    Y, D, idx, val, cnt, pidx, pval, pcnt = _two_codings(41)
+    n = D.shape[0]
+    X = oracle.slots_to_dense(idx, val, cnt, n)
+    Xp = oracle.slots_to_dense(pidx, pval, pcnt, n)
+    Z = Y + (D.T @ Xp).T - (D.T @ X).T
+    A, _ = oracle.atom_update_nsgk(Y, D, idx, val, cnt, pidx, pval, pcnt, ntilde=ntilde)
+    B, vB, _ = oracle.atom_update(Z, D, pidx, pval, pcnt, ntilde=ntilde, rule=oracle.RULE_SGK)
+    np.testing.assert_allclose(A, B, rtol=0, atol=1e-11)
+    assert np.max(np.abs(A - D)) > 1e-3
+
+
+def test_nsgk_with_unchanged_representations_is_sgk():
+    """X_prev = X makes Z = Y: P-NSGK reduces to P-SGK (Section 3)."""
+    Y, D, idx, val, cnt = _sparse_problem(42)
+    A, _ = oracle.atom_update_nsgk(Y, D, idx, val, cnt, idx, val, cnt)
+    B, _, _ = oracle.atom_update(Y, D, idx, val, cnt, rule=oracle.RULE_SGK)
+    np.testing.assert_allclose(A, B, rtol=0, atol=1e-12)
+
+
+def test_nsgk_fixed_point_on_exact_representations():
+    """Y = D X_prev exactly and X = X_prev: F = d_j xp_j is rank one, so every
+    used atom is its own least-squares fit and stays (Eq. 6)."""
+    g = _rng(43)
+    p, n, m, s = 10, 25, 300, 3
+    D = _unit_rows(g.standard_normal((n, p)))
+    rows, vals = synth.sparse_codes(n, m, s, 77)
+    Y = np.einsum("ms,msp->mp", vals, D[rows])
+    cnt = np.full(m, s, np.int32)
+    A, unused = oracle.atom_update_nsgk(Y, D, rows, vals, cnt, rows, vals, cnt)
+    np.testing.assert_allclose(A, D, rtol=0, atol=1e-12)
+
+
+def test_dl_nsgk_first_iteration_is_sgk():
+    """The first P-NSGK iteration has no earlier representations and uses its
+    own: identical to a P-SGK iteration; the second differs."""
+    Y, D, idx, val, cnt = _sparse_problem(44)
+    a = oracle.dl(Y, D, 3, 1, rule=oracle.RULE_NSGK)
+    b = oracle.dl(Y, D, 3, 1, rule=oracle.RULE_SGK)
+    np.testing.assert_allclose(a[0], b[0], rtol=0, atol=1e-12)
+    a2 = oracle.dl(Y, D, 3, 2, rule=oracle.RULE_NSGK)
+    b2 = oracle.dl(Y, D, 3, 2, rule=oracle.RULE_SGK)
+    assert np.max(np.abs(a2[0] - b2[0])) > 1e-6
