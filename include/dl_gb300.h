@@ -181,12 +181,24 @@ int dl_set_group_size(dl_ctx* ctx, int ntilde);
  *   DL_RULE_AKSVD (default)  d_j = F x^T / ||F x^T||, then x_{j,I_j} = F^T d_j
  *                            (one power step, Eq. 5: PAK-SVD / AK-SVD);
  *   DL_RULE_SGK              d_j = F x^T / (x x^T), normalised, coefficients
- *                            unchanged (Eq. 6 and Algorithm 2: P-SGK / SGK).
- * Both give the same atom direction; SGK leaves X as the coding pass made it.
- * Applies to later jau_update / dl_iterate calls.  Returns DL_OK or DL_EINVAL.
+ *                            unchanged (Eq. 6 and Algorithm 2: P-SGK / SGK);
+ *   DL_RULE_NSGK             P-NSGK (Eq. 7): the SGK update with Y replaced by
+ *                            Z = Y + D X_prev - D X and the representations
+ *                            taken from X_prev, the X the previous iteration
+ *                            ended with (stored by the context).  The first
+ *                            P-NSGK iteration after this call, or after a
+ *                            dl_iterate on other signals or sizes, has no
+ *                            X_prev and uses its own X (it is then P-SGK).
+ *                            Needs the float4 data path like group sizes < n
+ *                            (DL_ENOTIMPL otherwise) and allocates the stored
+ *                            representations on first use (DL_ENOMEM).
+ * AK-SVD and SGK give the same atom direction; SGK and P-NSGK leave X as the
+ * coding pass made it.  Applies to later jau_update / dl_iterate calls.
+ * Returns DL_OK, DL_EINVAL or DL_ENOMEM.
  */
 #define DL_RULE_AKSVD 0
 #define DL_RULE_SGK 1
+#define DL_RULE_NSGK 2
 int dl_set_update_rule(dl_ctx* ctx, int rule);
 
 /*

@@ -56,6 +56,13 @@ struct dl_ctx {
   int jau_kernels = 5;   // kernel launches of the last enqueued JAU update
   int ntilde = 0;        // group size of the atom update (0 or n: all atoms at once)
   int rule = DL_RULE_AKSVD;  // atom update rule
+  // P-NSGK: the representations of the previous iteration (slots), a device
+  // flag telling whether they exist yet, and the dictionary an iteration starts from
+  int32_t* pidx = nullptr;
+  float* pval = nullptr;
+  int32_t* pcnt = nullptr;
+  int* pvalid = nullptr;
+  float* D0 = nullptr;
   int omp_kernels[2] = {5, 5};  // ... of the last enqueued coding pass (plain, learned)
   float* Dhi = nullptr;  // TF32 head / tail of D for the tensor-core correlations
   float* Dlo = nullptr;
@@ -148,7 +155,8 @@ void free_ctx(dl_ctx* c) {
   void* ptrs[] = {c->G, c->A0, c->Dhi, c->Dlo, c->Ylp, c->Ysc, c->Dlp, c->Dsc, c->rs_list,
                   c->rs_count, c->rs_scratch, c->sidx, c->sval, c->scnt, c->bsum, c->err, c->iter, c->rmse,
                   c->jw.Upart, c->jw.U, c->jw.epart_a, c->jw.epart_b, c->jw.Dn, c->jw.C,
-                  c->hY, c->hD, c->hcolptr, c->hrowidx, c->hval};
+                  c->hY, c->hD, c->hcolptr, c->hrowidx, c->hval, c->pidx, c->pval, c->pcnt,
+                  c->pvalid, c->D0};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   cudaSetDevice(prev);
@@ -355,6 +363,17 @@ cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const
   c->jw.nb_row = dlk::jau_row_blocks(c->cfg_row_per_sm);
   const int nt = group_size(c);
   const int ngroups = (c->n + nt - 1) / nt;
+  const bool nsgk = c->rule == DL_RULE_NSGK;
+  c->jw.nsgk = nsgk;
+  c->jw.pidx = c->pidx;
+  c->jw.pval = c->pval;
+  c->jw.pcnt = c->pcnt;
+  c->jw.pvalid = c->pvalid;
+  c->jw.D0 = c->D0;
+  cudaError_t e0;
+  if (nsgk && (e0 = cudaMemcpyAsync(c->D0, D, sizeof(float) * (size_t)c->n * c->p,
+                                    cudaMemcpyDeviceToDevice, c->st)) != cudaSuccess)
+    return e0;
   // (groups need the float4 passes; the entry points check this before enqueuing)
   c->jau_kernels = ngroups == 1 ? dlk::jau_launches(c->p, Y, D) : 4 * ngroups + 1;
   mark(c, 4);
@@ -364,7 +383,7 @@ cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const
     c->jw.a0 = ngroups == 1 ? 0 : a0;
     c->jw.a1 = ngroups == 1 ? 0 : a1;
     c->jw.energies = a0 == 0;  // the error of the coding pass, before any atom moves
-    c->jw.sgk = c->rule == DL_RULE_SGK;
+    c->jw.sgk = c->rule != DL_RULE_AKSVD;  // SGK and P-NSGK leave the coefficients
     e = dlk::jau_accumulate(Y, c->p, m, D, c->n, s, c->sidx, c->sval, c->scnt, c->jw, c->err,
                             c->st);
     if (e != cudaSuccess) break;
@@ -386,7 +405,19 @@ cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const
   }
   c->jw.a0 = c->jw.a1 = 0;
   c->jw.energies = true;
+  c->jw.nsgk = false;
   if (e != cudaSuccess) return e;
+  if (nsgk) {  // this iteration's representations are the next one's previous ones
+    const size_t ms = (size_t)m * s;
+    if ((e = cudaMemcpyAsync(c->pidx, c->sidx, sizeof(int32_t) * ms, cudaMemcpyDeviceToDevice,
+                             c->st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->pval, c->sval, sizeof(float) * ms, cudaMemcpyDeviceToDevice,
+                             c->st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->pcnt, c->scnt, sizeof(int32_t) * (size_t)m,
+                             cudaMemcpyDeviceToDevice, c->st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->pvalid, 1, sizeof(int), c->st)) != cudaSuccess)
+      return e;
+  }
   mark(c, 7);
   e = dlk::jau_finalize(c->jw, c->rmse, c->iter, D, c->n, c->p, c->st);
   mark(c, 8);
@@ -583,7 +614,20 @@ int dl_set_group_size(dl_ctx* c, int ntilde) {
 }
 
 int dl_set_update_rule(dl_ctx* c, int rule) {
-  if (!c || (rule != DL_RULE_AKSVD && rule != DL_RULE_SGK)) return DL_EINVAL;
+  if (!c || (rule != DL_RULE_AKSVD && rule != DL_RULE_SGK && rule != DL_RULE_NSGK))
+    return DL_EINVAL;
+  DevGuard g(c->dev);
+  if (rule == DL_RULE_NSGK) {
+    const size_t ms = (size_t)c->m_max * c->s_max;
+    if (!c->pvalid && !(dalloc(&c->pidx, ms) && dalloc(&c->pval, ms) &&
+                        dalloc(&c->pcnt, (size_t)c->m_max) && dalloc(&c->pvalid, 1) &&
+                        dalloc(&c->D0, (size_t)c->n * c->p))) {
+      cudaGetLastError();
+      return DL_ENOMEM;
+    }
+    // the first P-NSGK iteration has no previous representations
+    DL_CHECK(cudaMemsetAsync(c->pvalid, 0, sizeof(int), c->st));
+  }
   if (rule != c->rule) c->gkey_m = -1;  // captured iterations no longer apply
   c->rule = rule;
   return DL_OK;
@@ -705,8 +749,8 @@ int jau_update(dl_ctx* c, const float* Y, int64_t m, float* D, const int64_t* co
   if (ptr_kind(D) != kind || ptr_kind(colptr) != kind || ptr_kind(rowidx) != kind ||
       ptr_kind(val) != kind)
     return DL_EINVAL;
-  if (group_size(c) < c->n && (c->p % 4 != 0 ||
-                                (kind == 1 && !dlk::jau_vec4(c->p, Y, D))))
+  if ((group_size(c) < c->n || c->rule == DL_RULE_NSGK) &&
+      (c->p % 4 != 0 || (kind == 1 && !dlk::jau_vec4(c->p, Y, D))))
     return DL_ENOTIMPL;
   DevGuard g(c->dev);
   const int s = c->s_max;
@@ -755,7 +799,9 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
       ptr_kind(val) != kind)
     return DL_EINVAL;
   if (iters == 0) return DL_OK;
-  if (kind == 1 && group_size(c) < c->n && !dlk::jau_vec4(c->p, Y, D)) return DL_ENOTIMPL;
+  if (kind == 1 && (group_size(c) < c->n || c->rule == DL_RULE_NSGK) &&
+      !dlk::jau_vec4(c->p, Y, D))
+    return DL_ENOTIMPL;
   DevGuard g(c->dev);
   if ((rc = ensure_rmse(c, iters))) return rc;
   const float* dY = Y;
@@ -772,7 +818,8 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
     dri = c->hrowidx;
     dv = c->hval;
     staged = staged_ok(c, dY, dD, m);
-    if (group_size(c) < c->n && !dlk::jau_vec4(c->p, dY, dD)) return DL_ENOTIMPL;
+    if ((group_size(c) < c->n || c->rule == DL_RULE_NSGK) && !dlk::jau_vec4(c->p, dY, dD))
+      return DL_ENOTIMPL;
     if (!staged)
       DL_CHECK(cudaMemcpyAsync(c->hY, Y, sizeof(float) * (size_t)m * c->p, cudaMemcpyHostToDevice, c->st));
     DL_CHECK(cudaMemcpyAsync(c->hD, D, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyHostToDevice, c->st));
@@ -790,6 +837,8 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
     c->gkey_m = m;
     c->gkey_s = s;
     c->gkey_seen = 0;
+    // other signals or sizes: the stored P-NSGK representations do not apply
+    if (c->pvalid) DL_CHECK(cudaMemsetAsync(c->pvalid, 0, sizeof(int), c->st));
   }
   const bool can_graph = c->st != nullptr && m > 0;
   DL_CHECK(enq_convert_y(c, dY, m));

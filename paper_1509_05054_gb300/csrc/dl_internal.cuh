@@ -110,6 +110,14 @@ struct JauWork {
   bool energies = true;
   // SGK rule (Eq. 6, P-SGK): atoms as in AK-SVD, coefficients left as they are
   bool sgk = false;
+  // P-NSGK (Eq. 7, float4 form): previous representations (slots), whether they
+  // exist yet (device flag), and the dictionary the iteration started from
+  bool nsgk = false;
+  const int32_t* pidx = nullptr;
+  const float* pval = nullptr;
+  const int32_t* pcnt = nullptr;
+  const int* pvalid = nullptr;
+  const float* D0 = nullptr;
 };
 // Grid sizes: mult selects 1x/2x the base CTA count of the accumulation pass
 // and 2/4/8 CTAs per SM for the row pass; *_max give the partial-buffer sizes.

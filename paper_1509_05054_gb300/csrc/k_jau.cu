@@ -159,12 +159,19 @@ __device__ __forceinline__ float f4_dot(float4 a, float4 b, float acc) {
 // CTA.  Spreading the reductions over several copies keeps the L2 lines of
 // frequently used atoms from serialising them; the copies are then summed in a
 // fixed order.
-template <int RV, int SMAX>
+// NS (P-NSGK, Eq. 7): the error is that of Z = Y + D0 Xp - D0 X against the
+// current atoms and the previous representations Xp, e = y - D0 x + (D0 - D) xp
+// (D0: the dictionary the iteration started from; equal to D before any group
+// has moved), and U, r are accumulated over Xp's supports and values.  *pvalid
+// == 0 means there are no previous representations yet: Xp = X.
+template <int RV, int SMAX, bool NS>
 __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
     const float* __restrict__ Y, int p, int64_t m, const float* __restrict__ D, int n, int s,
     const int32_t* __restrict__ idx, const float* __restrict__ val, const int32_t* __restrict__ cnt,
     float* __restrict__ U, double* __restrict__ epart, int* __restrict__ err, int a0, int a1,
-    int energies) {
+    int energies, const float* __restrict__ D0, const int32_t* __restrict__ pidx,
+    const float* __restrict__ pval, const int32_t* __restrict__ pcnt,
+    const int* __restrict__ pvalid, int moved) {
   __shared__ float rsh[kMaxAtoms];
   __shared__ double red[ACC4_THREADS / 32];
   for (int j = threadIdx.x; j < n; j += blockDim.x) rsh[j] = 0.f;
@@ -173,7 +180,12 @@ __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
   const int g = lane & 7, gbase = lane & ~7;
   const int pv = p >> 2;
   const float4* __restrict__ Y4 = (const float4*)Y;
-  const float4* __restrict__ D4 = (const float4*)D;
+  const float4* __restrict__ D4 = (const float4*)(NS ? D0 : D);
+  const float4* __restrict__ Dc4 = (const float4*)D;
+  const bool have_prev = NS && *pvalid != 0;
+  const int32_t* __restrict__ sidx = have_prev ? pidx : idx;
+  const float* __restrict__ sval = have_prev ? pval : val;
+  const int32_t* __restrict__ scnt = have_prev ? pcnt : cnt;
   float* __restrict__ Uc = U + (size_t)(blockIdx.x % kUCopies) * ((size_t)n * p + n);
   float ee = 0.f, yy = 0.f;
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
@@ -210,12 +222,41 @@ __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
     }
 #pragma unroll
     for (int q = 0; q < RV; ++q) ee = f4_dot(e[q], e[q], ee);
+    // the slots whose contributions are accumulated: X, or Xp for P-NSGK
+    int sc = c, sj0 = j0, sj1 = j1, scmax = cmax;
+    float sx0 = x0, sx1 = x1;
+    if (NS) {
+      sc = live ? scnt[i] : 0;
+      sj0 = (g < sc) ? sidx[i * s + g] : 0;
+      sx0 = (g < sc) ? sval[i * s + g] : 0.f;
+      sj1 = (SMAX > 8 && g + 8 < sc) ? sidx[i * s + g + 8] : 0;
+      sx1 = (SMAX > 8 && g + 8 < sc) ? sval[i * s + g + 8] : 0.f;
+      scmax = __reduce_max_sync(FULL, (unsigned)sc);
+      if (moved) {  // e += (D0 - D) xp for the atoms earlier groups have moved
+#pragma unroll
+        for (int t = 0; t < SMAX; ++t) {
+          if (t >= scmax) break;
+          const int jj = __shfl_sync(FULL, t < 8 ? sj0 : sj1, gbase + (t & 7));
+          const float xx = __shfl_sync(FULL, t < 8 ? sx0 : sx1, gbase + (t & 7));
+          if (t < sc) {
+#pragma unroll
+            for (int q = 0; q < RV; ++q) {
+              const int v = g + 8 * q;
+              if (v < pv) {
+                e[q] = f4_fma(xx, __ldg(D4 + (size_t)jj * pv + v), e[q]);
+                e[q] = f4_fma(-xx, __ldg(Dc4 + (size_t)jj * pv + v), e[q]);
+              }
+            }
+          }
+        }
+      }
+    }
 #pragma unroll
     for (int t = 0; t < SMAX; ++t) {
-      if (t >= cmax) break;
-      const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
-      const float xx = __shfl_sync(FULL, t < 8 ? x0 : x1, gbase + (t & 7));
-      if (t < c && jj >= a0 && jj < a1) {
+      if (t >= scmax) break;
+      const int jj = __shfl_sync(FULL, t < 8 ? sj0 : sj1, gbase + (t & 7));
+      const float xx = __shfl_sync(FULL, t < 8 ? sx0 : sx1, gbase + (t & 7));
+      if (t < sc && jj >= a0 && jj < a1) {
 #pragma unroll
         for (int q = 0; q < RV; ++q) {
           const int v = g + 8 * q;
@@ -747,9 +788,16 @@ cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int
     cudaError_t e = cudaMemsetAsync(w.Upart, 0, sizeof(float) * len * kUCopies, st);
     if (e != cudaSuccess) return e;
 #define DL_ACC4(RV, SM)                                                                  \
-  accum4_kernel<RV, SM><<<w.nb_accum, ACC4_THREADS, 0, st>>>(Y, p, m, D, n, s, idx, val, cnt, \
-                                                             w.Upart, w.epart_a, err, w.a0,   \
-                                                             w.a1 > 0 ? w.a1 : n, (int)w.energies)
+  do {                                                                                       \
+    if (w.nsgk)                                                                              \
+      accum4_kernel<RV, SM, true><<<w.nb_accum, ACC4_THREADS, 0, st>>>(                     \
+          Y, p, m, D, n, s, idx, val, cnt, w.Upart, w.epart_a, err, w.a0, w.a1 > 0 ? w.a1 : n, \
+          (int)w.energies, w.D0, w.pidx, w.pval, w.pcnt, w.pvalid, w.a0 > 0 ? 1 : 0);         \
+    else                                                                                     \
+      accum4_kernel<RV, SM, false><<<w.nb_accum, ACC4_THREADS, 0, st>>>(                    \
+          Y, p, m, D, n, s, idx, val, cnt, w.Upart, w.epart_a, err, w.a0, w.a1 > 0 ? w.a1 : n, \
+          (int)w.energies, D, idx, val, cnt, nullptr, 0);                                     \
+  } while (0)
 #define DL_ACC4_S(RV) \
   if (s <= 8) DL_ACC4(RV, 8); else DL_ACC4(RV, 16)
     if (p <= 32) { DL_ACC4_S(1); }

@@ -162,7 +162,7 @@ def dl_kernel_launches(ctx: int) -> int:
 PHASES = ("gram", "correlations", "omp", "colptr_scan", "accumulate", "atoms", "rows", "finalize")
 
 
-DL_RULE_AKSVD, DL_RULE_SGK = 0, 1
+DL_RULE_AKSVD, DL_RULE_SGK, DL_RULE_NSGK = 0, 1, 2
 
 
 def dl_set_update_rule(ctx: int, rule: int) -> None:

@@ -144,3 +144,40 @@ def test_sgk_rule_matches_oracle(dl, ntilde):
     _, val1_g, _ = csc_to_slots(colptr.cpu().numpy(), rowidx.cpu().numpy(), v.cpu().numpy(), s)
     np.testing.assert_allclose(val1_g, val32, rtol=0, atol=1e-7)
     assert abs(rm[1] - oracle.rmse(Y64, D1_o, idx, val1_o, cnt)) <= 1e-5
+
+
+@pytest.mark.parametrize("ntilde", [256, 64])
+def test_nsgk_dl_iterate_matches_oracle(dl, ntilde):
+    """P-NSGK (Eq. 7) over three iterations: each GPU atom update against the
+    oracle's, given the GPU's own dictionary, representations X^(k) and the
+    previous iteration's X^(k-1) (the first iteration uses its own X)."""
+    name, m, s = "patch_n256", 3001, 6
+    Y, D, _ = synth.workload_inputs(name, m=m)
+    Y64 = Y.astype(np.float64)
+    p, n = D.shape[1], D.shape[0]
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    dl.dl_set_group_size(ctx, ntilde)
+    dl.dl_set_update_rule(ctx, dl.DL_RULE_NSGK)
+    Yd, Dd = torch.from_numpy(Y).cuda(), torch.from_numpy(D.copy()).cuda()
+    cp, ri, v = (torch.zeros(m + 1, dtype=torch.int64, device="cuda"),
+                 torch.zeros(m * s, dtype=torch.int32, device="cuda"),
+                 torch.zeros(m * s, dtype=torch.float32, device="cuda"))
+    prev = None
+    for k in range(3):
+        Dk = Dd.cpu().numpy().astype(np.float64)
+        rm = np.zeros(2)
+        dl.dl_iterate(ctx, Yd, m, Dd, s, 1, cp, ri, v, rm)
+        idx_g, val_g, cnt_g = csc_to_slots(cp.cpu().numpy(), ri.cpu().numpy(), v.cpu().numpy(), s)
+        idx_o, _, cnt_o, gaps = oracle.omp(Y64, Dk, s, return_gaps=True)
+        assert_support_parity(idx_g, cnt_g, idx_o, cnt_o, gaps)
+        val64 = val_g.astype(np.float64)
+        pi, pv, pc = prev if prev is not None else (idx_g, val64, cnt_g)
+        D1_o, _ = oracle.atom_update_nsgk(Y64, Dk, idx_g, val64, cnt_g, pi, pv, pc, ntilde=ntilde)
+        np.testing.assert_allclose(Dd.cpu().numpy(), D1_o, rtol=0, atol=2e-5)
+        assert abs(rm[1] - oracle.rmse(Y64, D1_o, idx_g, val64, cnt_g)) <= 1e-5
+        if k == 1:   # from the second iteration on, P-NSGK is not P-SGK
+            D1_s, _, _ = oracle.atom_update(Y64, Dk, idx_g, val64, cnt_g, ntilde=ntilde,
+                                            rule=oracle.RULE_SGK)
+            assert np.max(np.abs(D1_o - D1_s)) > 1e-4
+        prev = (idx_g, val64, cnt_g)
+    dl.dl_destroy(ctx)
