@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--group-sizes", default="128,32",
                     help="atom-update group sizes ntilde < n to time beside the Jacobi form "
                          "(empty: none)")
+    ap.add_argument("--no-rules", dest="rules", action="store_false",
+                    help="skip timing the P-SGK and P-NSGK atom-update rules")
     ap.add_argument("--m", type=int, default=None,
                     help="override the number of signals (profiling of smaller cases)")
     return ap.parse_args()
@@ -376,10 +378,10 @@ def run_ours(args):
                "d2h_bytes_per_step": 4 * n * p + 8 * (m + 1) + 8 * m * s + 16 + 4,
                "steps": args.e2e_steps}
 
-    groups = None
-    if args.group_sizes:
-        groups = run_groups(args, dl, torch, st, Yd, D0, colptr, rowidx, val, flush, m, p, n, s,
-                            plain_rmse)
+    variants = None
+    if args.group_sizes or args.rules:
+        variants = run_variants(args, dl, torch, st, Yd, D0, colptr, rowidx, val, flush, m, p, n,
+                                s, plain_rmse)
     batched = None
     if not args.no_batched:
         batched = run_batched(args, dl, torch, st)
@@ -410,7 +412,7 @@ def run_ours(args):
                     "equal_rmse": f"final relative RMSE after {RMSE_ITERS} iterations within "
                                   f"{100 * EQUAL_RMSE:.0f}% of the plain FP32 form"}),
                 "roofline": roof, "phases_ms": phases, "phase_roofline": per_phase,
-                "forms": forms, "group_size": groups, "batched": batched, "learned": learned,
+                "forms": forms, "atom_update_variants": variants, "batched": batched, "learned": learned,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if pg:
@@ -465,16 +467,21 @@ def run_batched(args, dl, torch, st):
                        for k, (q, c) in enumerate(zip(probs, cfgs))]}
 
 
-def run_groups(args, dl, torch, st, Yd, D0, colptr, rowidx, val, flush, m, p, n, s, plain_rmse):
-    """The atom update with group size ntilde < n (groups updated one after
-    another): time per iteration, and the final RMSE after RMSE_ITERS
-    iterations against the Jacobi form's."""
+def run_variants(args, dl, torch, st, Yd, D0, colptr, rowidx, val, flush, m, p, n, s,
+                 plain_rmse):
+    """Other forms of the atom-update stage beside the Jacobi PAK-SVD: group sizes
+    ntilde < n (groups updated one after another) and the P-SGK and P-NSGK rules
+    (Section 3): time per iteration, and the final RMSE after RMSE_ITERS iterations
+    against the Jacobi PAK-SVD form's."""
+    variants = [(f"ntilde={int(x)}", int(x), 0) for x in args.group_sizes.split(",")
+                if x and 1 <= int(x) < n]
+    if args.rules:
+        variants += [("P-SGK", n, 1), ("P-NSGK", n, 2)]
     out = {}
-    for nt in (int(x) for x in args.group_sizes.split(",") if x):
-        if nt < 1 or nt >= n:
-            continue
+    for name, nt, rule in variants:
         ctx = dl.dl_init(p, n, m, s, 0, st)
         dl.dl_set_group_size(ctx, nt)
+        dl.dl_set_update_rule(ctx, rule)
         Dd = D0.clone()
         with torch.cuda.stream(st):
             for _ in range(3):
@@ -492,13 +499,15 @@ def run_groups(args, dl, torch, st, Yd, D0, colptr, rowidx, val, flush, m, p, n,
                 ev[k][1].record(st)
         st.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        dl.dl_set_update_rule(ctx, rule)   # a fresh start for the RMSE run
         Dq = D0.clone()
         rm = np.zeros(2 * RMSE_ITERS)
         dl.dl_iterate(ctx, Yd, m, Dq, s, RMSE_ITERS, colptr, rowidx, val, rm)
         dl.dl_destroy(ctx)
-        out[str(nt)] = {"value": m / (ms * 1e-3), "unit": UNIT, "ms_per_iteration": ms,
-                        "groups": (n + nt - 1) // nt, "final_rmse": float(rm[-1]),
-                        "rmse_vs_jacobi": (float(rm[-1]) / plain_rmse - 1.0) if plain_rmse else None}
+        out[name] = {"value": m / (ms * 1e-3), "unit": UNIT, "ms_per_iteration": ms,
+                     "groups": (n + nt - 1) // nt, "rule": ["PAK-SVD", "P-SGK", "P-NSGK"][rule],
+                     "final_rmse": float(rm[-1]),
+                     "rmse_vs_pak_svd": (float(rm[-1]) / plain_rmse - 1.0) if plain_rmse else None}
     return out
 
 
