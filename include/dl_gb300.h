@@ -314,6 +314,20 @@ int dl_batch_create(dl_batch** out, const dl_problem* problems, int count, int p
  */
 int dl_batch_iterate(dl_batch* batch, int iters, double* rmse);
 
+/*
+ * dl_batch_set_update_rule / dl_batch_set_group_size -- dl_set_update_rule and
+ * dl_set_group_size applied to every problem of the batch (e.g. the P-NSGK and
+ * P-SGK rows of the dictionary-recovery experiment, Section 4.1, as one batch).
+ * The next dl_batch_iterate captures its graph again.  The P-NSGK previous
+ * representations of each problem persist across dl_batch_iterate calls and
+ * are dropped by the next dl_batch_set_update_rule.  dl_batch_iterate returns
+ * DL_ENOTIMPL when a group size below n or P-NSGK is set for a problem without
+ * the float4 data path (p % 4 == 0, Y and D 16-byte aligned).  Return as the
+ * single-context calls (DL_EINVAL for a group size above some problem's n).
+ */
+int dl_batch_set_update_rule(dl_batch* batch, int rule);
+int dl_batch_set_group_size(dl_batch* batch, int ntilde);
+
 /* dl_batch_destroy -- free the batch's contexts, streams and graph. */
 int dl_batch_destroy(dl_batch* batch);
 

@@ -544,7 +544,7 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
   const size_t mm = (size_t)m_max;
   c->jw.nb_accum = dlk::jau_accum_blocks_max(p, n);
   c->jw.nb_row = dlk::jau_row_blocks_max();
-  const size_t ulen = (size_t)n * p + n;
+  const size_t ulen = dlk::jau_ulen(p, n);
   size_t nslices = dlk::jau_accum_smem(p, n) > 0 ? (size_t)c->jw.nb_accum : 1;
   if (nslices < (size_t)dlk::kUCopies) nslices = dlk::kUCopies;
   bool ok = dalloc(&c->G, (size_t)n * n) && dalloc(&c->A0, mm * c->lda) &&
@@ -1118,8 +1118,13 @@ extern "C" int dl_batch_iterate(dl_batch* b, int iters, double* rmse) {
   if (!b || iters < 0) return DL_EINVAL;
   if (iters == 0) return DL_OK;
   DevGuard g(b->dev);
-  for (dl_ctx* c : b->ctxs)
+  for (int k = 0; k < b->count; ++k) {
+    dl_ctx* c = b->ctxs[k];
+    if ((group_size(c) < c->n || c->rule == DL_RULE_NSGK) &&
+        !dlk::jau_vec4(c->p, b->probs[k].Y, b->probs[k].D))
+      return DL_ENOTIMPL;
     if (int rc = ensure_rmse(c, iters)) return rc;
+  }
   if (!b->gexec || b->graph_iters != iters) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
@@ -1148,6 +1153,26 @@ extern "C" int dl_batch_iterate(dl_batch* b, int iters, double* rmse) {
     for (dl_ctx* c : b->ctxs)
       if (int rc = take_device_error(c)) return rc;
   }
+  return DL_OK;
+}
+
+extern "C" int dl_batch_set_update_rule(dl_batch* b, int rule) {
+  if (!b) return DL_EINVAL;
+  for (dl_ctx* c : b->ctxs)
+    if (int rc = dl_set_update_rule(c, rule)) return rc;
+  for (dl_ctx* c : b->ctxs) DL_CHECK(cudaStreamSynchronize(c->st));  // the flag resets
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  return DL_OK;
+}
+
+extern "C" int dl_batch_set_group_size(dl_batch* b, int ntilde) {
+  if (!b) return DL_EINVAL;
+  for (dl_ctx* c : b->ctxs)
+    if (ntilde < 1 || ntilde > c->n) return DL_EINVAL;
+  for (dl_ctx* c : b->ctxs) dl_set_group_size(c, ntilde);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
   return DL_OK;
 }
 

@@ -122,6 +122,11 @@ struct JauWork {
 // Grid sizes: mult selects 1x/2x the base CTA count of the accumulation pass
 // and 2/4/8 CTAs per SM for the row pass; *_max give the partial-buffer sizes.
 constexpr int kUCopies = 16;  // copies of U the float4 accumulation spreads its L2 reductions over
+// Floats per copy of U (n p atom sums, then n row energies), padded to a
+// multiple of 4 so that every copy, and with p % 4 == 0 every atom row in it,
+// starts on a 16-byte boundary for the float4 reductions; U and each slice of
+// the partial buffer are allocated with this length.
+__host__ __device__ inline size_t jau_ulen(int p, int n) { return ((size_t)n * p + n + 3) / 4 * 4; }
 int jau_accum_blocks(int p, int n, int mult);
 int jau_accum_blocks_max(int p, int n);
 int jau_row_blocks(int per_sm);

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
   const int32_t* __restrict__ sidx = have_prev ? pidx : idx;
   const float* __restrict__ sval = have_prev ? pval : val;
   const int32_t* __restrict__ scnt = have_prev ? pcnt : cnt;
-  float* __restrict__ Uc = U + (size_t)(blockIdx.x % kUCopies) * ((size_t)n * p + n);
+  float* __restrict__ Uc = U + (size_t)(blockIdx.x % kUCopies) * jau_ulen(p, n);
   float ee = 0.f, yy = 0.f;
   const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 3);
   const int64_t g0 = (int64_t)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 3);
@@ -784,7 +784,7 @@ cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int
                            const int32_t* idx, const float* val, const int32_t* cnt,
                            const JauWork& w, int* err, cudaStream_t st) {
   if (jau_vec4(p, Y, D)) {
-    const size_t len = (size_t)n * p + n;
+    const size_t len = jau_ulen(p, n);
     cudaError_t e = cudaMemsetAsync(w.Upart, 0, sizeof(float) * len * kUCopies, st);
     if (e != cudaSuccess) return e;
 #define DL_ACC4(RV, SM)                                                                  \

@@ -67,6 +67,8 @@ def load(build_if_missing: bool = True):
         lib.dl_set_profiling.argtypes = [P, i32]
         lib.dl_set_group_size.argtypes = [P, i32]
         lib.dl_set_update_rule.argtypes = [P, i32]
+        lib.dl_batch_set_update_rule.argtypes = [P, i32]
+        lib.dl_batch_set_group_size.argtypes = [P, i32]
         lib.dl_gram.argtypes = [P, P, P]
         lib.dl_correlate.argtypes = [P, P, i64, P, P]
         lib.dl_uses_tensor_cores.argtypes = [P]
@@ -98,7 +100,8 @@ def load(build_if_missing: bool = True):
             getattr(lib, name).restype = i32
         for name in ("dl_init", "dl_set_stream", "dl_destroy", "omp_code", "jau_update", "dl_iterate",
                      "dl_sync", "dl_set_profiling", "dl_phase_times", "dl_gram", "dl_correlate",
-                     "dl_uses_tensor_cores", "dl_correlate_noalloc"):
+                     "dl_uses_tensor_cores", "dl_correlate_noalloc", "dl_set_group_size",
+                     "dl_set_update_rule", "dl_batch_set_update_rule", "dl_batch_set_group_size"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -256,6 +259,14 @@ def dl_batch_create(problems, precision: int = DL_FP32, autotune: bool = True, s
 
 def dl_batch_iterate(batch: int, iters: int, rmse=None) -> None:
     _check(load().dl_batch_iterate(batch, iters, _ptr(rmse)), "dl_batch_iterate")
+
+
+def dl_batch_set_update_rule(batch: int, rule: int) -> None:
+    _check(load().dl_batch_set_update_rule(batch, rule), "dl_batch_set_update_rule")
+
+
+def dl_batch_set_group_size(batch: int, ntilde: int) -> None:
+    _check(load().dl_batch_set_group_size(batch, ntilde), "dl_batch_set_group_size")
 
 
 def dl_batch_destroy(batch: int) -> None:

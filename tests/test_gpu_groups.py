@@ -181,3 +181,45 @@ def test_nsgk_dl_iterate_matches_oracle(dl, ntilde):
             assert np.max(np.abs(D1_o - D1_s)) > 1e-4
         prev = (idx_g, val64, cnt_g)
     dl.dl_destroy(ctx)
+
+
+@pytest.mark.parametrize("rule,ntilde", [(0, 50), (0, 16), (1, 50), (2, 50), (2, 16)])
+def test_recovery_shape_iterations_match_oracle(dl, rule, ntilde):
+    """The dictionary-recovery shape of Section 4.1 (p=20, n=50, m=1500, s=3):
+    n p + n = 1050 is not a multiple of 4, so the float4 accumulation's copies
+    of U sit at a padded stride, and n % 4 != 0 sends both products to the
+    CUDA-core GEMM.  Three iterations of each rule, each atom update against
+    the oracle's from the GPU's own dictionary and representations."""
+    p, n, m, s = 20, 50, 1500, 3
+    Y, _, _, _ = synth.recovery_problem(p, n, m, s, 20.0, seed=10000)
+    D = synth.dictionary_from_signals(Y, n, seed=20000)
+    Y, D = Y.astype(np.float32), D.astype(np.float32)
+    Y64 = Y.astype(np.float64)
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    dl.dl_set_group_size(ctx, ntilde)
+    dl.dl_set_update_rule(ctx, rule)
+    Yd, Dd = torch.from_numpy(Y).cuda(), torch.from_numpy(D.copy()).cuda()
+    cp, ri, v = (torch.zeros(m + 1, dtype=torch.int64, device="cuda"),
+                 torch.zeros(m * s, dtype=torch.int32, device="cuda"),
+                 torch.zeros(m * s, dtype=torch.float32, device="cuda"))
+    prev = None
+    for k in range(3):
+        Dk = Dd.cpu().numpy().astype(np.float64)
+        rm = np.zeros(2)
+        dl.dl_iterate(ctx, Yd, m, Dd, s, 1, cp, ri, v, rm)
+        idx_g, val_g, cnt_g = csc_to_slots(cp.cpu().numpy(), ri.cpu().numpy(), v.cpu().numpy(), s)
+        idx_o, val_o, cnt_o, gaps = oracle.omp(Y64, Dk, s, return_gaps=True)
+        assert_support_parity(idx_g, cnt_g, idx_o, cnt_o, gaps)
+        assert abs(rm[0] - oracle.rmse(Y64, Dk, idx_o, val_o, cnt_o)) <= 1e-4
+        if rule == dl.DL_RULE_NSGK:
+            # the coding pass's X (the GPU's slots hold it: P-NSGK leaves X)
+            val64 = val_g.astype(np.float64)
+            pi, pv, pc = prev if prev is not None else (idx_g, val64, cnt_g)
+            D1_o, _ = oracle.atom_update_nsgk(Y64, Dk, idx_g, val64, cnt_g, pi, pv, pc,
+                                              ntilde=ntilde)
+            prev = (idx_g, val64, cnt_g)
+        else:
+            D1_o, _, _ = oracle.atom_update(Y64, Dk, idx_o, val_o, cnt_o, ntilde=ntilde,
+                                            rule=rule)
+        np.testing.assert_allclose(Dd.cpu().numpy(), D1_o, rtol=0, atol=5e-5)
+    dl.dl_destroy(ctx)
