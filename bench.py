@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-problems measurement")
     ap.add_argument("--batched-iters", type=int, default=20)
+    ap.add_argument("--table1", action="store_true",
+                    help="also run the dictionary-recovery experiment of Table 1 (P-SGK and "
+                         "P-NSGK rows, 50 runs per cell) as batches of 200 problems")
     ap.add_argument("--group-sizes", default="128,32",
                     help="atom-update group sizes ntilde < n to time beside the Jacobi form "
                          "(empty: none)")
@@ -385,6 +388,7 @@ def run_ours(args):
     batched = None
     if not args.no_batched:
         batched = run_batched(args, dl, torch, st)
+    table1 = run_table1(dl, torch, st) if args.table1 else None
     learned = None
     if not args.no_learned:
         learned = run_learned(args, dl, torch, st)
@@ -412,7 +416,8 @@ def run_ours(args):
                     "equal_rmse": f"final relative RMSE after {RMSE_ITERS} iterations within "
                                   f"{100 * EQUAL_RMSE:.0f}% of the plain FP32 form"}),
                 "roofline": roof, "phases_ms": phases, "phase_roofline": per_phase,
-                "forms": forms, "atom_update_variants": variants, "batched": batched, "learned": learned,
+                "forms": forms, "atom_update_variants": variants, "batched": batched, "table1": table1,
+                "learned": learned,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if pg:
@@ -465,6 +470,73 @@ def run_batched(args, dl, torch, st):
             "shapes": [dict(p=q["p"], n=q["n"], m=q["m"], s=q["s"], cfg=c,
                             final_rmse=float(rm[k, -1, 1]))
                        for k, (q, c) in enumerate(zip(probs, cfgs))]}
+
+
+def run_table1(dl, torch, st):
+    """Dictionary recovery (Section 4.1, Table 1): p=20, n=50, m=1500, s in
+    {3, 4, 5}, SNR 10/20/30/inf dB, 50 runs per cell, 9 s^2 iterations from n
+    random data vectors, ntilde = n.  One batch of 200 problems per s (one graph
+    launch per s^2 iterations); percentages of recovered atoms (an atom counts
+    when some learned atom has 1 - |d0^T d| < 0.01) beside the paper's."""
+    snrs, runs, p, n, m = (10.0, 20.0, 30.0, None), 50, 20, 50, 1500
+    golden = os.path.join(ROOT, "tests", "golden")
+    rows = {"P-SGK": (dl.DL_RULE_SGK, "table1_recovery_psgk.txt"),
+            "P-NSGK": (dl.DL_RULE_NSGK, "table1_recovery_pnsgk.txt")}
+    out = {"unit": "% recovered atoms", "columns_snr_db": ["10", "20", "30", "inf"]}
+    total_ms, total_pi = 0.0, 0
+    for name, (rule, fname) in rows.items():
+        paper = {}
+        for line in open(os.path.join(golden, fname)):
+            v = line.split()
+            if v and not line.startswith("#"):
+                paper[int(v[0])] = [float(x) for x in v[1:]]
+        out[name] = {"gpu": {}, "paper": paper}
+    for s in (3, 4, 5):
+        cells, dev = [], []
+        for snr in snrs:
+            for r in range(runs):
+                Y, D0, _, _ = synth.recovery_problem(p, n, m, s, snr, seed=10000 + 97 * r)
+                Dinit = synth.dictionary_from_signals(Y, n, seed=20000 + r)
+                cells.append((snr, D0, torch.from_numpy(Dinit.astype(np.float32)).cuda()))
+                dev.append(dict(p=p, n=n, s=s, m=m, Y=torch.from_numpy(Y.astype(np.float32)).cuda(),
+                                D=torch.from_numpy(Dinit.astype(np.float32)).cuda(),
+                                colptr=torch.zeros(m + 1, dtype=torch.int64, device="cuda"),
+                                rowidx=torch.zeros(m * s, dtype=torch.int32, device="cuda"),
+                                val=torch.zeros(m * s, dtype=torch.float32, device="cuda")))
+        b = dl.dl_batch_create(dev, autotune=False, stream=st)
+        try:
+            for name, (rule, _) in rows.items():
+                for (_, _, Dinit), d in zip(cells, dev):
+                    d["D"].copy_(Dinit)
+                torch.cuda.synchronize()
+                dl.dl_batch_set_update_rule(b, rule)
+                dl.dl_batch_iterate(b, s * s, None)      # capture
+                for (_, _, Dinit), d in zip(cells, dev):
+                    d["D"].copy_(Dinit)
+                dl.dl_batch_set_update_rule(b, rule)      # drops the stored representations
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for _ in range(9):
+                    dl.dl_batch_iterate(b, s * s, None)
+                e1.record(st)
+                st.synchronize()
+                total_ms += e0.elapsed_time(e1)
+                total_pi += len(dev) * 9 * s * s
+                pct = []
+                for snr in snrs:
+                    res = []
+                    for (c_snr, D0, _), d in zip(cells, dev):
+                        if c_snr == snr:
+                            c = np.abs(D0 @ d["D"].cpu().numpy().astype(np.float64).T)
+                            res.append(np.mean((1.0 - c.max(axis=1)) < 0.01))
+                    pct.append(round(100.0 * float(np.mean(res)), 2))
+                out[name]["gpu"][s] = pct
+        finally:
+            dl.dl_batch_destroy(b)
+    out["problem_iterations_per_s"] = total_pi / (total_ms * 1e-3)
+    out["gpu_ms"] = total_ms
+    return out
 
 
 def run_variants(args, dl, torch, st, Yd, D0, colptr, rowidx, val, flush, m, p, n, s,
