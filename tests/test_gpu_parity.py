@@ -127,6 +127,33 @@ def test_jau_update_matches_oracle_from_identical_x(dl, name, m, s):
     assert abs(rm[1] - rho_after) <= 1e-4
 
 
+# (p, n, m, s): p % 4 == 0 (float4 passes) with n p + n = n (p + 1) not a multiple
+# of 4 (n mod 4 = 1, 2, 3), so the copies of U sit at a padded stride
+UNALIGNED_U = [(20, 37, 1501, 3), (16, 51, 999, 4), (64, 129, 2003, 6), (36, 203, 1777, 5)]
+
+
+@pytest.mark.parametrize("p,n,m,s", UNALIGNED_U)
+def test_jau_update_with_unaligned_atom_sums(dl, p, n, m, s):
+    """The atom update (Eq. 3, 5) from an identical X for every residue of n p + n
+    mod 4: atoms within 1e-5 of the oracle's, RMSE pair close."""
+    Y, _, _, _ = synth.recovery_problem(p, n, m, s, 20.0, seed=300 + n)
+    D = synth.dictionary_from_signals(Y, n, seed=400 + n)
+    Y, D = Y.astype(np.float32), D.astype(np.float32)
+    Y64, D64 = Y.astype(np.float64), D.astype(np.float64)
+    idx, val, cnt = oracle.omp(Y64, D64, s)
+    val32 = val.astype(np.float32).astype(np.float64)
+    D1_o, val1_o, _ = oracle.jau(Y64, D64, idx, val32, cnt)
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    Dd = torch.from_numpy(D.copy()).cuda()
+    colptr, rowidx, v = _to_csc_tensors(idx, val, cnt, s)
+    rm = np.zeros(2)
+    dl.jau_update(ctx, torch.from_numpy(Y).cuda(), m, Dd, colptr, rowidx, v, rm)
+    dl.dl_destroy(ctx)
+    np.testing.assert_allclose(Dd.cpu().numpy(), D1_o, rtol=0, atol=1e-5)
+    assert abs(rm[0] - oracle.rmse(Y64, D64, idx, val32, cnt)) <= 1e-5
+    assert abs(rm[1] - oracle.rmse(Y64, D1_o, idx, val1_o, cnt)) <= 1e-4
+
+
 def test_dl_iterate_teacher_forced(dl):
     """Each GPU iteration vs the oracle started from the GPU's own D^(k) (the JAU
     trajectory is erratic, so free-running FP32 and FP64 runs may part ways)."""
