@@ -122,7 +122,7 @@ struct dl_ctx {
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // host-buffer calls: the signals arrive in chunks on the side stream
-  static constexpr int kChunks = 4;
+  static constexpr int kChunks = 3;
   cudaEvent_t ev_chunk[kChunks] = {};
   // optional per-phase timing with CUDA events recorded on the context's stream
   bool prof = false;
@@ -430,6 +430,28 @@ bool staged_ok(dl_ctx* c, const float* dY, const float* dD, int64_t m) {
   return !c->prop && !lp_ok(c) && tc_ok(c, dY, dD) && m >= (int64_t)dl_ctx::kChunks * 128;
 }
 
+// Piece q of the staged coding pass covers signals [off[q], off[q+1]).  Each
+// piece is kGrow times the one before it: uploading a signal takes about a
+// third of the time its correlations and OMP take (p=64, n=512: ~1.3 against
+// ~3.9 ns), so piece q+1 arrives while piece q is being coded and only the
+// first, small piece is waited for.  Boundaries are multiples of 128 signals
+// (row tiles); trailing pieces may be empty.
+constexpr double kGrow = 2.5;
+void staged_pieces(int64_t m, int64_t (&off)[dl_ctx::kChunks + 1]) {
+  double w = 1.0, total = 0.0;
+  for (int q = 0; q < dl_ctx::kChunks; ++q, w *= kGrow) total += w;
+  double acc = 0.0;
+  w = 1.0;
+  off[0] = 0;
+  for (int q = 0; q < dl_ctx::kChunks; ++q, w *= kGrow) {
+    acc += w;
+    int64_t b = q + 1 == dl_ctx::kChunks ? m : ((int64_t)(m * (acc / total)) + 127) / 128 * 128;
+    if (b > m) b = m;
+    if (b < off[q]) b = off[q];
+    off[q + 1] = b;
+  }
+}
+
 // The coding pass with Y still on the host: Y is copied in kChunks pieces on the
 // side stream, and the correlations (the Gram matrix with the first piece), the
 // OMP and the FP64 re-solve of each piece start as soon as it has arrived.
@@ -437,7 +459,8 @@ bool staged_ok(dl_ctx* c, const float* dY, const float* dD, int64_t m) {
 cudaError_t enq_omp_staged(dl_ctx* c, const float* hostY, const float* dY, int64_t m,
                            const float* D, int s, int* kernels) {
   const int64_t p = c->p;
-  const int64_t chunk = ((m + dl_ctx::kChunks - 1) / dl_ctx::kChunks + 127) / 128 * 128;
+  int64_t offs[dl_ctx::kChunks + 1];
+  staged_pieces(m, offs);
   cudaError_t e;
   int k = 0;
   mark(c, 0);
@@ -446,24 +469,27 @@ cudaError_t enq_omp_staged(dl_ctx* c, const float* hostY, const float* dY, int64
   mark(c, 1);
   if ((e = cudaEventRecord(c->ev_fork, c->st)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(c->st2, c->ev_fork, 0)) != cudaSuccess) return e;
-  int nch = 0;
-  for (int64_t off = 0; off < m; off += chunk, ++nch) {
-    const int64_t mk = off + chunk <= m ? chunk : m - off;
+  for (int q = 0; q < dl_ctx::kChunks; ++q) {
+    const int64_t off = offs[q], mk = offs[q + 1] - offs[q];
+    if (mk <= 0) continue;
     e = cudaMemcpyAsync((float*)dY + off * p, hostY + off * p, sizeof(float) * (size_t)(mk * p),
                         cudaMemcpyHostToDevice, c->st2);
     if (e != cudaSuccess) return e;
-    if ((e = cudaEventRecord(c->ev_chunk[nch], c->st2)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(c->ev_chunk[q], c->st2)) != cudaSuccess) return e;
   }
   mark(c, 2);
-  for (int q = 0; q < nch; ++q) {
-    const int64_t off = q * chunk, mk = off + chunk <= m ? chunk : m - off;
+  bool first = true;
+  for (int q = 0; q < dl_ctx::kChunks; ++q) {
+    const int64_t off = offs[q], mk = offs[q + 1] - offs[q];
+    if (mk <= 0) continue;
     const float* Yq = dY + off * p;
     float* Aq = c->A0 + off * c->lda;
     if ((e = cudaStreamWaitEvent(c->st, c->ev_chunk[q], 0)) != cudaSuccess) return e;
-    e = q == 0 ? dlk::corr_tf32x3_pair(Yq, mk, Aq, c->lda, D, c->n, c->G, c->n, c->Dhi, c->Dlo,
+    e = first ? dlk::corr_tf32x3_pair(Yq, mk, Aq, c->lda, D, c->n, c->G, c->n, c->Dhi, c->Dlo,
                                        c->n, c->p, c->err, c->st)
                : dlk::corr_tf32x3(Yq, mk, c->Dhi, c->Dlo, c->n, c->p, Aq, c->lda, c->err, c->st);
     if (e != cudaSuccess) return e;
+    first = false;
     if ((e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
     e = dlk::omp_batch(Aq, c->lda, c->G, c->n, Yq, c->p, mk, s, c->sidx + off * s,
                        c->sval + off * s, c->scnt + off, c->err, c->rs_list, c->rs_count,
