@@ -216,15 +216,16 @@ __device__ __forceinline__ void omp_one(
     const int lsel = __ffs(ball) - 1;
     const int tsel = NT - 1 - (int)(kbits & TMASK);
     const int sel = 32 * tsel + lsel;
-    // issue the Gram row loads early (needed unless this is the last step)
+    // issue the Gram loads early: the diagonal first (the pivot needs it before
+    // the row is used), then the row (needed unless this is the last step)
     const bool need_u = (step + 1 < s) && (step + 1 < SMAX);
+    const float gss = gsrc.diag(sel);
     if (need_u) {
       float2 grow[NV];
       gsrc.template row<NV>(sel, lane, grow);
 #pragma unroll
       for (int v = 0; v < NV; ++v) UV(step < NPHI ? step : 0, v) = grow[v];
     }
-    const float gss = gsrc.diag(sel);
 
     // alpha[sel] (exact, signed), its masking, and u_q[sel] on the owning lane
     float amine = 0.f;
