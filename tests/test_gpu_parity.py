@@ -15,7 +15,7 @@ import pytest
 import oracle
 from paper_1509_05054_gb300 import synth
 
-from _common import assert_support_parity, csc_to_slots
+from _common import assert_support_parity, compare_supports, csc_to_slots
 
 pytestmark = pytest.mark.gpu
 
@@ -152,6 +152,41 @@ def test_jau_update_with_unaligned_atom_sums(dl, p, n, m, s):
     np.testing.assert_allclose(Dd.cpu().numpy(), D1_o, rtol=0, atol=1e-5)
     assert abs(rm[0] - oracle.rmse(Y64, D64, idx, val32, cnt)) <= 1e-5
     assert abs(rm[1] - oracle.rmse(Y64, D1_o, idx, val1_o, cnt)) <= 1e-4
+
+
+# (p, n, m, s) at the library's limits: n = DL_MAX_N and s = DL_MAX_S with the
+# tensor-core correlations (p = 64) and with the CUDA-core ones (p = DL_MAX_P)
+MAX_SIZES = [(64, 1024, 641, 16), (128, 1024, 515, 16), (128, 37, 300, 16)]
+
+
+@pytest.mark.parametrize("p,n,m,s", MAX_SIZES)
+def test_maximum_sizes_match_oracle(dl, p, n, m, s):
+    """OMP (Algorithm 1 step 1) and the atom update (Eq. 3, 5) at the largest n,
+    s and p: the coding's error no worse than the oracle's and supports equal on
+    98% of the signals, mismatches (FP32 against FP64 over 16 steps) explained
+    by near-ties but for 0.5%; the update from the GPU's own X against the
+    oracle's from the same X."""
+    Y, _, _, _ = synth.recovery_problem(p, n, m, s, 30.0, seed=500 + p + n)
+    D = synth.random_dictionary(p, n, seed=600 + p + n, dtype=np.float32)
+    Y = Y.astype(np.float32)
+    Y64, D64 = Y.astype(np.float64), D.astype(np.float64)
+    idx_g, val_g, cnt_g = _gpu_omp(dl, Y, D, s)
+    idx_o, val_o, cnt_o, gaps = oracle.omp(Y64, D64, s, return_gaps=True)
+    ndiff, nbad, _ = compare_supports(idx_g, cnt_g, idx_o, cnt_o, gaps)
+    assert ndiff <= 0.02 * m and nbad <= 0.005 * m, (ndiff, nbad)
+    assert (oracle.rmse(Y64, D64, idx_g, val_g.astype(np.float64), cnt_g)
+            <= oracle.rmse(Y64, D64, idx_o, val_o, cnt_o) + 1e-4)
+    val64 = val_g.astype(np.float64)
+    D1_o, val1_o, _ = oracle.jau(Y64, D64, idx_g, val64, cnt_g)
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    Dd = torch.from_numpy(D.copy()).cuda()
+    colptr, rowidx, v = _to_csc_tensors(idx_g, val_g, cnt_g, s)
+    rm = np.zeros(2)
+    dl.jau_update(ctx, torch.from_numpy(Y).cuda(), m, Dd, colptr, rowidx, v, rm)
+    dl.dl_destroy(ctx)
+    np.testing.assert_allclose(Dd.cpu().numpy(), D1_o, rtol=0, atol=2e-5)
+    assert abs(rm[0] - oracle.rmse(Y64, D64, idx_g, val64, cnt_g)) <= 1e-4
+    assert abs(rm[1] - oracle.rmse(Y64, D1_o, idx_g, val1_o, cnt_g)) <= 1e-4
 
 
 def test_dl_iterate_teacher_forced(dl):
