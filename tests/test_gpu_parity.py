@@ -189,6 +189,45 @@ def test_maximum_sizes_match_oracle(dl, p, n, m, s):
     assert abs(rm[1] - oracle.rmse(Y64, D1_o, idx_g, val1_o, cnt_g)) <= 1e-4
 
 
+@pytest.mark.parametrize("case", ["one_signal", "all_zero", "tile_plus_one"])
+def test_dl_iterate_edge_cases(dl, case):
+    """Whole iterations (coding, atom update, row update, RMSE) on degenerate
+    inputs against the oracle: a single signal; all-zero signals (no atom is
+    selected, every atom is unused and kept as it is, RMSE 0); a signal count
+    one past a 128-row tile."""
+    p, n, s = 64, 96, 4
+    m = {"one_signal": 1, "all_zero": 300, "tile_plus_one": 129}[case]
+    Y, _, _, _ = synth.recovery_problem(p, n, max(m, 2), s, 30.0, seed=900 + m)
+    Y = np.ascontiguousarray(Y[:m], np.float32)
+    if case == "all_zero":
+        Y[:] = 0.0
+    D = synth.random_dictionary(p, n, seed=901, dtype=np.float32)
+    Y64, D64 = Y.astype(np.float64), D.astype(np.float64)
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+    Yd, Dd = torch.from_numpy(Y).cuda(), torch.from_numpy(D.copy()).cuda()
+    cp = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+    ri = torch.zeros(m * s, dtype=torch.int32, device="cuda")
+    v = torch.zeros(m * s, dtype=torch.float32, device="cuda")
+    rm = np.zeros(4)
+    Dk = D64
+    for k in range(2):
+        Dk = Dd.cpu().numpy().astype(np.float64)
+        dl.dl_iterate(ctx, Yd, m, Dd, s, 1, cp, ri, v, rm[2 * k:2 * k + 2])
+        idx_o, val_o, cnt_o = oracle.omp(Y64, Dk, s)
+        D1_o, val1_o, _ = oracle.jau(Y64, Dk, idx_o, val_o, cnt_o)
+        idx_g, val_g, cnt_g = csc_to_slots(cp.cpu().numpy(), ri.cpu().numpy(), v.cpu().numpy(), s)
+        np.testing.assert_array_equal(cnt_g, cnt_o)
+        np.testing.assert_array_equal(idx_g, idx_o)
+        np.testing.assert_allclose(val_g, val1_o, rtol=0, atol=2e-4)
+        np.testing.assert_allclose(Dd.cpu().numpy(), D1_o, rtol=0, atol=2e-5)
+        assert abs(rm[2 * k] - oracle.rmse(Y64, Dk, idx_o, val_o, cnt_o)) <= 1e-4
+        assert abs(rm[2 * k + 1] - oracle.rmse(Y64, D1_o, idx_o, val1_o, cnt_o)) <= 1e-4
+    dl.dl_destroy(ctx)
+    if case == "all_zero":
+        assert int(cp[-1]) == 0 and np.all(rm == 0.0)
+        np.testing.assert_array_equal(Dd.cpu().numpy(), D)
+
+
 def test_dl_iterate_teacher_forced(dl):
     """Each GPU iteration vs the oracle started from the GPU's own D^(k) (the JAU
     trajectory is erratic, so free-running FP32 and FP64 runs may part ways)."""
