@@ -161,6 +161,19 @@ int dl_iterate(dl_ctx* ctx, const float* Y, int64_t m, float* D, int s, int iter
                int64_t* colptr, int32_t* rowidx, float* val, double* rmse);
 
 /*
+ * dl_check_bounded_wait -- failure-path check of the tensor-core kernels: one
+ * GPU thread waits on a barrier that nothing ever completes, through the same
+ * bounded wait (about 2 s of the GPU's global timer) every mbarrier wait of
+ * the library uses, gives up, and flags a timeout in the context's device
+ * error word.  No fault and no hang: the context stays usable.  The paper has
+ * no counterpart (failure detection of this implementation).  Blocks for about
+ * 2 s on the context's stream.  Returns DL_ETIMEOUT when the wait gave up as
+ * designed, an earlier pending error of the context (DL_EINVAL, DL_ENUMERIC,
+ * DL_ETIMEOUT) if there was one, DL_EINVAL for a null context or DL_ECUDA.
+ */
+int dl_check_bounded_wait(dl_ctx* ctx);
+
+/*
  * dl_set_group_size -- group size ntilde of the atom-update stage (Algorithm 1
  * steps 2-5, Section 3): the atoms are updated in groups of ntilde consecutive
  * atoms [k*ntilde, (k+1)*ntilde), one group after another; the atoms of one

@@ -632,6 +632,15 @@ int dl_sync(dl_ctx* c) {
 
 int64_t dl_kernel_launches(dl_ctx* c) { return c ? c->launches : 0; }
 
+int dl_check_bounded_wait(dl_ctx* c) {
+  if (!c) return DL_EINVAL;
+  DevGuard g(c->dev);
+  if (int rc = take_device_error(c)) return rc;  // report an earlier error first
+  DL_CHECK(dlk::bounded_wait_check(c->err, c->st));
+  c->launches += 1;
+  return take_device_error(c);
+}
+
 int dl_set_group_size(dl_ctx* c, int ntilde) {
   if (!c || ntilde < 1 || ntilde > c->n) return DL_EINVAL;
   if (ntilde != c->ntilde) c->gkey_m = -1;  // captured iterations no longer apply

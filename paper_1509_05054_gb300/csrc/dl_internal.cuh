@@ -34,6 +34,10 @@ cudaError_t corr_tf32x3_pair(const float* A0, int64_t rows0, float* C0, int64_t 
                              const float* Bhi, const float* Blo, int n, int p, int* err,
                              cudaStream_t st);
 
+// Diagnostic: a wait on an mbarrier nothing arrives at, bounded as in the
+// tensor-core kernels; sets ERR_TIMEOUT in *err after about 2 s.
+cudaError_t bounded_wait_check(int* err, cudaStream_t st);
+
 // Reduced-precision correlations (k_corr_lp.cu): operands converted to padded
 // row-major BF16 or E4M3 (+ inverse row scales) buffers, then tcgen05 MMAs.
 enum : int { LP_BF16 = 1, LP_E4M3 = 2 };

@@ -67,6 +67,8 @@ def load(build_if_missing: bool = True):
         lib.dl_set_profiling.argtypes = [P, i32]
         lib.dl_set_group_size.argtypes = [P, i32]
         lib.dl_set_update_rule.argtypes = [P, i32]
+        lib.dl_check_bounded_wait.argtypes = [P]
+        lib.dl_check_bounded_wait.restype = i32
         lib.dl_batch_set_update_rule.argtypes = [P, i32]
         lib.dl_batch_set_group_size.argtypes = [P, i32]
         lib.dl_gram.argtypes = [P, P, P]
@@ -170,6 +172,11 @@ DL_RULE_AKSVD, DL_RULE_SGK, DL_RULE_NSGK = 0, 1, 2
 
 def dl_set_update_rule(ctx: int, rule: int) -> None:
     _check(load().dl_set_update_rule(ctx, rule), "dl_set_update_rule")
+
+
+def dl_check_bounded_wait(ctx: int) -> int:
+    """Status of the bounded-wait failure path (DL_ETIMEOUT when it works)."""
+    return load().dl_check_bounded_wait(ctx)
 
 
 def dl_set_group_size(ctx: int, ntilde: int) -> None:
