@@ -363,23 +363,6 @@ cudaError_t corr_tf32x3_pair(const float* A0, int64_t rows0, float* C0, int64_t 
   return cudaGetLastError();
 }
 
-namespace {
-// One thread waits on phase 0 of an mbarrier that nothing arrives at, through
-// the bounded wait every tensor-core kernel uses, and flags ERR_TIMEOUT when
-// the wait gives up (after kWaitNs of %globaltimer): the failure path of those
-// kernels, exercised without a fault and without a hang.
-__global__ void wait_timeout_kernel(int* err) {
-  __shared__ __align__(8) uint64_t bar;
-  mbar_init(&bar, 1);
-  if (!mbar_wait(&bar, 0)) atomicOr(err, ERR_TIMEOUT);
-}
-}  // namespace
-
-cudaError_t bounded_wait_check(int* err, cudaStream_t st) {
-  wait_timeout_kernel<<<1, 1, 0, st>>>(err);
-  return cudaGetLastError();
-}
-
 cudaError_t corr_tf32x3(const float* A, int64_t rows_a, const float* Bhi, const float* Blo, int n,
                         int p, float* C, int64_t ldc, int* err, cudaStream_t st) {
   return corr_tf32x3_pair(A, rows_a, C, ldc, nullptr, 0, nullptr, 0, Bhi, Blo, n, p, err, st);
