@@ -367,7 +367,10 @@ def run_ours(args):
         rih = torch.zeros(m * s, dtype=torch.int32).pin_memory()
         vh = torch.zeros(m * s, dtype=torch.float32).pin_memory()
         rmh = np.zeros(2)
-        dl.dl_iterate(ctx, Yh, m, Dh, s, 1, cph, rih, vh, rmh)   # warm (staging allocation)
+        # warm-up: staging allocation, then the graph of the whole call is
+        # captured on the second call with the same buffers
+        for _ in range(max(3, args.warmup)):
+            dl.dl_iterate(ctx, Yh, m, Dh, s, 1, cph, rih, vh, rmh)
         Dh.copy_(torch.from_numpy(D))
         barrier()
         t0 = time.perf_counter()

@@ -112,6 +112,14 @@ struct dl_ctx {
   int gkey_s = -1;
   int gkey_seen = 0;
   int gkey_seen_l = 0;
+  // graph of one whole host-buffer call (upload of D, the staged iteration with
+  // its upload of Y, downloads of D and X), keyed by the host pointers, m, s and
+  // every setting that changes what is enqueued
+  cudaGraphExec_t hgexec = nullptr;
+  const void* hkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t hsig[10] = {};
+  int hseen = 0;
+  int hg_kernels = 0;
   int64_t launches = 0;
   // launch shapes (chosen by dl_autotune; defaults otherwise)
   int cfg_omp_warps = 4;  // warps per CTA of the OMP kernel
@@ -142,6 +150,7 @@ void free_ctx(dl_ctx* c) {
   cudaSetDevice(c->dev);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->gexec_learned) cudaGraphExecDestroy(c->gexec_learned);
+  if (c->hgexec) cudaGraphExecDestroy(c->hgexec);
   for (void* q : {(void*)c->rr_ref, (void*)c->rr_L, (void*)c->fb_list, (void*)c->fb_count,
                   (void*)c->cand, c->Ybf})
     if (q) cudaFree(q);
@@ -535,6 +544,90 @@ int check_common(dl_ctx* c, int64_t m) {
   return DL_OK;
 }
 
+// Page-locked host memory (the only host memory a captured copy may use).
+bool pinned_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// One whole host-buffer call of one iteration: D uploaded, the staged
+// iteration (Y uploaded in pieces under the coding pass), D and X downloaded.
+cudaError_t enq_host_call(dl_ctx* c, const float* Y, int64_t m, float* D, int s,
+                          int64_t* colptr, int32_t* rowidx, float* val, int* kernels) {
+  cudaError_t e;
+  const size_t np = (size_t)c->n * c->p, ms = (size_t)m * s;
+  if ((e = cudaMemcpyAsync(c->hD, D, sizeof(float) * np, cudaMemcpyHostToDevice, c->st)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(c->iter, 0, sizeof(int), c->st)) != cudaSuccess)
+    return e;
+  int ko = 0;
+  if ((e = enq_iteration(c, c->hY, m, c->hD, s, c->hcolptr, c->hrowidx, c->hval, Y, &ko)) !=
+      cudaSuccess)
+    return e;
+  *kernels = ko + kKernelsScan + c->jau_kernels;
+  // all s*m entries (the caller's capacity), so no synchronisation is needed to learn nnz
+  if ((e = cudaMemcpyAsync(D, c->hD, sizeof(float) * np, cudaMemcpyDeviceToHost, c->st)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(colptr, c->hcolptr, sizeof(int64_t) * (size_t)(m + 1),
+                           cudaMemcpyDeviceToHost, c->st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(rowidx, c->hrowidx, sizeof(int32_t) * ms, cudaMemcpyDeviceToHost,
+                           c->st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(val, c->hval, sizeof(float) * ms, cudaMemcpyDeviceToHost, c->st)) !=
+          cudaSuccess)
+    return e;
+  return cudaSuccess;
+}
+
+// dl_iterate with host buffers, one iteration, staged upload, page-locked
+// buffers: the first call with a key runs eagerly, the next ones replay a
+// graph of the whole call (the host then only launches it).
+int host_call_graphed(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int64_t* colptr,
+                      int32_t* rowidx, float* val, double* rmse) {
+  // (the caller has matched the host buffers against hkey)
+  c->gkey_m = -1;  // a later call with device buffers starts from a fresh key
+  const int64_t sig[10] = {m, s, c->rule, c->ntilde, c->cfg_omp_warps, c->cfg_acc_mult,
+                           c->cfg_row_per_sm, c->cfg_corr_tc, (int64_t)(intptr_t)c->st,
+                           (int64_t)(intptr_t)c->prop};
+  if (memcmp(sig, c->hsig, sizeof(sig)) != 0) {
+    if (c->hgexec) cudaGraphExecDestroy(c->hgexec);
+    c->hgexec = nullptr;
+    c->hseen = 0;
+    memcpy(c->hsig, sig, sizeof(sig));
+  }
+  if (c->hseen >= 1 && !c->hgexec) {
+    cudaGraph_t graph = nullptr;
+    int k = 0;
+    DL_CHECK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enq_host_call(c, Y, m, D, s, colptr, rowidx, val, &k);
+    cudaError_t e2 = cudaStreamEndCapture(c->st, &graph);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (e2 != cudaSuccess) return cuda_status(e2);
+    e = cudaGraphInstantiate(&c->hgexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->hgexec = nullptr;
+      return cuda_status(e);
+    }
+    c->hg_kernels = k;
+  }
+  if (c->hgexec) {
+    DL_CHECK(cudaGraphLaunch(c->hgexec, c->st));
+    c->launches += c->hg_kernels;
+  } else {
+    int k = 0;
+    DL_CHECK(enq_host_call(c, Y, m, D, s, colptr, rowidx, val, &k));
+    c->launches += k;
+    c->hseen++;
+  }
+  if (rmse)
+    DL_CHECK(cudaMemcpyAsync(rmse, c->rmse, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->st));
+  return take_device_error(c);
+}
+
 }  // namespace
 
 extern "C" {
@@ -855,6 +948,20 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
     staged = staged_ok(c, dY, dD, m);
     if ((group_size(c) < c->n || c->rule == DL_RULE_NSGK) && !dlk::jau_vec4(c->p, dY, dD))
       return DL_ENOTIMPL;
+    const void* hk[5] = {Y, D, colptr, rowidx, val};
+    if (memcmp(hk, c->hkey, sizeof(hk)) != 0) {
+      // other host buffers: the stored P-NSGK representations do not apply (the
+      // staging buffers stay the same, so the device key cannot tell), and a
+      // graph of the previous buffers' call is stale
+      if (c->pvalid) DL_CHECK(cudaMemsetAsync(c->pvalid, 0, sizeof(int), c->st));
+      if (c->hgexec) cudaGraphExecDestroy(c->hgexec);
+      c->hgexec = nullptr;
+      c->hseen = 0;
+      memcpy(c->hkey, hk, sizeof(hk));
+    }
+    if (staged && iters == 1 && !c->prof && c->st && pinned_host(Y) && pinned_host(D) &&
+        pinned_host(colptr) && pinned_host(rowidx) && pinned_host(val))
+      return host_call_graphed(c, Y, m, D, s, colptr, rowidx, val, rmse);
     if (!staged)
       DL_CHECK(cudaMemcpyAsync(c->hY, Y, sizeof(float) * (size_t)m * c->p, cudaMemcpyHostToDevice, c->st));
     DL_CHECK(cudaMemcpyAsync(c->hD, D, sizeof(float) * (size_t)c->n * c->p, cudaMemcpyHostToDevice, c->st));
@@ -874,6 +981,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
     c->gkey_seen = 0;
     // other signals or sizes: the stored P-NSGK representations do not apply
     if (c->pvalid) DL_CHECK(cudaMemsetAsync(c->pvalid, 0, sizeof(int), c->st));
+    c->hkey[0] = nullptr;  // nor to a later graphed host-buffer call
   }
   const bool can_graph = c->st != nullptr && m > 0;
   DL_CHECK(enq_convert_y(c, dY, m));

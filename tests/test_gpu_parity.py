@@ -397,6 +397,68 @@ def test_host_pointer_path_matches_device_path(dl):
     np.testing.assert_allclose(Dh, Dd.cpu().numpy(), rtol=0, atol=1e-5)
 
 
+@pytest.mark.parametrize("rule", [0, 2])
+def test_pinned_host_calls_replay_a_graph_of_the_whole_call(dl, rule):
+    """dl_iterate with page-locked host buffers, one iteration per call: the
+    first call runs eagerly, the second captures a graph of the whole call
+    (uploads, iteration, downloads), later calls replay it.  Each call's RMSE
+    pair, CSC X and D equal those of the same iteration on device buffers; for
+    P-NSGK (rule 2) the previous representations carry from call to call and
+    are dropped when the signals come from another buffer.  Teacher-forced on
+    D: the atom sums are L2 float reductions whose order varies, so both
+    contexts start every step from the host context's dictionary."""
+    name, m, s = "patch_n256", 3000, 6
+    Y, D, _ = synth.workload_inputs(name, m=m)
+    p, n = D.shape[1], D.shape[0]
+    st = torch.cuda.Stream()   # graphs are captured on a stream of the context's own
+    ctx_h = dl.dl_init(p, n, m, s, dl.DL_FP32, st)
+    ctx_d = dl.dl_init(p, n, m, s, dl.DL_FP32, st)
+    for c in (ctx_h, ctx_d):
+        dl.dl_set_update_rule(c, rule)
+    Yh = torch.from_numpy(Y.copy()).pin_memory()
+    Dh = torch.from_numpy(D.copy()).pin_memory()
+    cp_h = torch.zeros(m + 1, dtype=torch.int64).pin_memory()
+    ri_h = torch.zeros(m * s, dtype=torch.int32).pin_memory()
+    v_h = torch.zeros(m * s, dtype=torch.float32).pin_memory()
+    Yd, Dd = torch.from_numpy(Y.copy()).cuda(), torch.from_numpy(D.copy()).cuda()
+    cp, ri, v = (torch.zeros(m + 1, dtype=torch.int64, device="cuda"),
+                 torch.zeros(m * s, dtype=torch.int32, device="cuda"),
+                 torch.zeros(m * s, dtype=torch.float32, device="cuda"))
+    launches = []
+    for k in range(4):
+        rm_h, rm_d = np.zeros(2), np.zeros(2)
+        Dd.copy_(Dh)   # both contexts start the step from the same dictionary
+        torch.cuda.synchronize()
+        before = dl.dl_kernel_launches(ctx_h)
+        dl.dl_iterate(ctx_h, Yh, m, Dh, s, 1, cp_h, ri_h, v_h, rm_h)
+        launches.append(dl.dl_kernel_launches(ctx_h) - before)
+        dl.dl_iterate(ctx_d, Yd, m, Dd, s, 1, cp, ri, v, rm_d)
+        np.testing.assert_allclose(rm_h, rm_d, rtol=0, atol=1e-6)
+        np.testing.assert_array_equal(cp_h.numpy(), cp.cpu().numpy())
+        nnz = int(cp_h[-1])
+        np.testing.assert_array_equal(ri_h.numpy()[:nnz], ri.cpu().numpy()[:nnz])
+        np.testing.assert_allclose(v_h.numpy()[:nnz], v.cpu().numpy()[:nnz], rtol=0, atol=2e-4)
+        np.testing.assert_allclose(Dh.numpy(), Dd.cpu().numpy(), rtol=0, atol=1e-5)
+    assert len(set(launches)) == 1 and launches[0] > 0, launches
+    if rule == 2:
+        # signals from another buffer (same values): no previous representations,
+        # so this call is P-SGK from the current dictionary, as on a fresh context
+        Y2h = torch.from_numpy(Y.copy()).pin_memory()
+        D_now = Dh.numpy().copy()
+        rm_h = np.zeros(2)
+        dl.dl_iterate(ctx_h, Y2h, m, Dh, s, 1, cp_h, ri_h, v_h, rm_h)
+        ctx_f = dl.dl_init(p, n, m, s, dl.DL_FP32, st)
+        dl.dl_set_update_rule(ctx_f, rule)
+        Df = torch.from_numpy(D_now).cuda()
+        rm_f = np.zeros(2)
+        dl.dl_iterate(ctx_f, Yd, m, Df, s, 1, cp, ri, v, rm_f)
+        dl.dl_destroy(ctx_f)
+        np.testing.assert_allclose(rm_h, rm_f, rtol=0, atol=1e-6)
+        np.testing.assert_allclose(Dh.numpy(), Df.cpu().numpy(), rtol=0, atol=1e-5)
+    dl.dl_destroy(ctx_h)
+    dl.dl_destroy(ctx_d)
+
+
 def test_multi_iteration_graph_replay_matches_single_calls(dl):
     """dl_iterate(iters=3) (graph-captured after the first iteration) equals three
     dl_iterate(iters=1) calls to within rounding; the RMSE array has 2*iters entries."""
