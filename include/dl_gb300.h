@@ -27,9 +27,14 @@
  * the context's GPU), or all are host pointers (pageable or pinned); in the
  * host case the call stages them through device buffers owned by the context
  * and copies results back before returning (all s*m entries of rowidx/val;
- * those past colptr[m] are unspecified).  `rmse` outputs are always host
- * memory.  The context owns only its workspace (Gram matrix, correlations,
- * per-signal slots, partial sums, staging buffers).
+ * those past colptr[m] are unspecified).  A dl_iterate of one iteration with
+ * page-locked host buffers on a stream of its own (not the legacy default
+ * stream) is run eagerly the first time and, from the second call with the
+ * same buffers, sizes and settings, by replaying a CUDA graph of the whole call
+ * (uploads, iteration, downloads); host buffers that change between calls are
+ * new signals for P-NSGK (no previous representations).  `rmse` outputs are
+ * always host memory.  The context owns only its workspace (Gram matrix,
+ * correlations, per-signal slots, partial sums, staging buffers).
  *
  * Streams: work is enqueued on the context's stream (set by dl_init or
  * dl_set_stream) and is asynchronous for device pointers unless a host `rmse`
