@@ -588,7 +588,8 @@ cudaError_t enq_host_call(dl_ctx* c, const float* Y, int64_t m, float* D, int s,
 int host_call_graphed(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int64_t* colptr,
                       int32_t* rowidx, float* val, double* rmse) {
   // (the caller has matched the host buffers against hkey)
-  c->gkey_m = -1;  // a later call with device buffers starts from a fresh key
+  if (c->gkey[0] != (const void*)c->hY)
+    c->gkey_m = -1;  // a later call with device buffers starts from a fresh key
   const int64_t sig[10] = {m, s, c->rule, c->ntilde, c->cfg_omp_warps, c->cfg_acc_mult,
                            c->cfg_row_per_sm, c->cfg_corr_tc, (int64_t)(intptr_t)c->st,
                            (int64_t)(intptr_t)c->prop};
@@ -981,7 +982,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
     c->gkey_seen = 0;
     // other signals or sizes: the stored P-NSGK representations do not apply
     if (c->pvalid) DL_CHECK(cudaMemsetAsync(c->pvalid, 0, sizeof(int), c->st));
-    c->hkey[0] = nullptr;  // nor to a later graphed host-buffer call
+    if (kind == 1) c->hkey[0] = nullptr;  // nor to a later host-buffer call
   }
   const bool can_graph = c->st != nullptr && m > 0;
   DL_CHECK(enq_convert_y(c, dY, m));

@@ -459,6 +459,36 @@ def test_pinned_host_calls_replay_a_graph_of_the_whole_call(dl, rule):
     dl.dl_destroy(ctx_d)
 
 
+def test_nsgk_previous_representations_carry_across_host_calls(dl):
+    """P-NSGK with pageable host buffers (no graph): consecutive calls on the same
+    buffers continue from the previous call's X exactly as consecutive calls on
+    device buffers do (teacher-forced on D, as L2 float sums vary in order)."""
+    name, m, s = "patch_n256", 3000, 6
+    Y, D, _ = synth.workload_inputs(name, m=m)
+    p, n = D.shape[1], D.shape[0]
+    st = torch.cuda.Stream()
+    ctx_h = dl.dl_init(p, n, m, s, dl.DL_FP32, st)
+    ctx_d = dl.dl_init(p, n, m, s, dl.DL_FP32, st)
+    for c in (ctx_h, ctx_d):
+        dl.dl_set_update_rule(c, dl.DL_RULE_NSGK)
+    Dh = D.copy()
+    cp_h, ri_h, v_h = np.zeros(m + 1, np.int64), np.zeros(m * s, np.int32), np.zeros(m * s, np.float32)
+    Yd, Dd = torch.from_numpy(Y.copy()).cuda(), torch.from_numpy(D.copy()).cuda()
+    cp, ri, v = (torch.zeros(m + 1, dtype=torch.int64, device="cuda"),
+                 torch.zeros(m * s, dtype=torch.int32, device="cuda"),
+                 torch.zeros(m * s, dtype=torch.float32, device="cuda"))
+    for k in range(3):
+        Dd.copy_(torch.from_numpy(Dh))
+        torch.cuda.synchronize()
+        rm_h, rm_d = np.zeros(2), np.zeros(2)
+        dl.dl_iterate(ctx_h, Y, m, Dh, s, 1, cp_h, ri_h, v_h, rm_h)
+        dl.dl_iterate(ctx_d, Yd, m, Dd, s, 1, cp, ri, v, rm_d)
+        np.testing.assert_allclose(rm_h, rm_d, rtol=0, atol=1e-6)
+        np.testing.assert_allclose(Dh, Dd.cpu().numpy(), rtol=0, atol=1e-5)
+    dl.dl_destroy(ctx_h)
+    dl.dl_destroy(ctx_d)
+
+
 def test_multi_iteration_graph_replay_matches_single_calls(dl):
     """dl_iterate(iters=3) (graph-captured after the first iteration) equals three
     dl_iterate(iters=1) calls to within rounding; the RMSE array has 2*iters entries."""
