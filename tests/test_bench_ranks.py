@@ -65,3 +65,33 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
         gpus = 2
     bench.run_reference(A())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_line_carries_the_contract_keys(monkeypatch, capsys):
+    """Rank 0 of the oracle arm prints one JSON line with the keys the bench
+    contract names, its e2e moving no bytes and its cpu_baseline describing the
+    same run."""
+    import json
+
+    import bench
+    monkeypatch.setenv("RANK", "0")
+
+    class A:
+        workload = "tiny"
+        cpu_sample = 200
+        steps = 1
+        warmup = 0
+        gpus = 1
+    bench.run_reference(A())
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "impl",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
