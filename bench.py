@@ -392,7 +392,7 @@ def run_ours(args):
     if not args.no_batched:
         batched = run_batched(args, dl, torch, st)
     table1 = None
-    if args.table1:
+    if args.table1 and world == 1:  # the same reproduction on every replica adds nothing
         try:
             table1 = run_table1(dl, torch, st)
         except Exception as e:  # a side measurement: report it, keep the headline line
