@@ -117,6 +117,8 @@ struct dl_ctx {
   // every setting that changes what is enqueued
   cudaGraphExec_t hgexec = nullptr;
   const void* hkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t hkey_m = -1;
+  int hkey_s = -1;
   int64_t hsig[10] = {};
   int hseen = 0;
   int hg_kernels = 0;
@@ -950,7 +952,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
     if ((group_size(c) < c->n || c->rule == DL_RULE_NSGK) && !dlk::jau_vec4(c->p, dY, dD))
       return DL_ENOTIMPL;
     const void* hk[5] = {Y, D, colptr, rowidx, val};
-    if (memcmp(hk, c->hkey, sizeof(hk)) != 0) {
+    if (memcmp(hk, c->hkey, sizeof(hk)) != 0 || m != c->hkey_m || s != c->hkey_s) {
       // other host buffers: the stored P-NSGK representations do not apply (the
       // staging buffers stay the same, so the device key cannot tell), and a
       // graph of the previous buffers' call is stale
@@ -959,6 +961,8 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
       c->hgexec = nullptr;
       c->hseen = 0;
       memcpy(c->hkey, hk, sizeof(hk));
+      c->hkey_m = m;
+      c->hkey_s = s;
     }
     if (staged && iters == 1 && !c->prof && c->st && pinned_host(Y) && pinned_host(D) &&
         pinned_host(colptr) && pinned_host(rowidx) && pinned_host(val))
