@@ -36,7 +36,8 @@ METRIC = "signals coded+updated/sec per DL iteration (p=64,n=512,s=8) at equal R
 UNIT = "signals/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-CPU_SAMPLE = 20000
+CPU_SAMPLE = 100000
+ERR_SAMPLE = 20000  # signals of the teacher-forced error check against the oracle
 
 
 def parse():
@@ -67,6 +68,8 @@ def parse():
                          "(empty: none)")
     ap.add_argument("--no-rules", dest="rules", action="store_false",
                     help="skip timing the P-SGK and P-NSGK atom-update rules")
+    ap.add_argument("--no-c1", action="store_true",
+                    help="skip the p=64, n=256, s=6, m=20000 workload (50 iterations)")
     ap.add_argument("--m", type=int, default=None,
                     help="override the number of signals (profiling of smaller cases)")
     return ap.parse_args()
@@ -74,7 +77,7 @@ def parse():
 
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
 DTYPES = {"fp32": "f32", "bf16": "bf16 correlations, f32 OMP/JAU", "fp8": "e4m3 correlations, f32 OMP/JAU"}
-RMSE_ITERS = 10
+RMSE_ITERS = 50  # the iteration count of the throughput workload's quality check
 EQUAL_RMSE = 0.01
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -287,11 +290,16 @@ def run_ours(args):
         st.synchronize()
         phases = dl.dl_phase_times(ctx)
         dl.dl_set_profiling(ctx, False)
-        # quality: RMSE pair per iteration from the common starting dictionary
+        # quality: RMSE pair per iteration from the common starting dictionary, one
+        # iteration per call so that every D^(k) is kept for the error check
         Dq = D0.clone()
         rm = np.zeros(2 * RMSE_ITERS)
-        dl.dl_iterate(ctx, Yd, m, Dq, s, RMSE_ITERS, colptr, rowidx, val, rm)
+        dks = []
+        for k in range(RMSE_ITERS):
+            dks.append(Dq.cpu().numpy())
+            dl.dl_iterate(ctx, Yd, m, Dq, s, 1, colptr, rowidx, val, rm[2 * k: 2 * k + 2])
         resolved = dl.dl_last_resolved(ctx)
+        form_dicts[prec] = dks
         return ctx, {"value": job_throughput(world, m * args.steps, total_ms * 1e-3),
                      "ms_per_step": total_ms / args.steps, "gpu_launches": launches,
                      "phases_ms": phases, "rmse": rm.reshape(RMSE_ITERS, 2).tolist(),
@@ -301,8 +309,10 @@ def run_ours(args):
     clocks.start()
     forms = {}
     ctxs = {}
+    form_dicts = {}
     for prec in args.forms.split(","):
         ctxs[prec], forms[prec] = measure(prec)
+    fp32_peak = measure_fp32_peak(dl, torch, st)
     clk = clocks.stop()
     plain_rmse = forms["fp32"]["final_rmse"] if "fp32" in forms else None
     for prec, f in forms.items():
@@ -315,8 +325,8 @@ def run_ours(args):
     phases = chosen["phases_ms"]
     value, ms_per_step, launches = chosen["value"], chosen["ms_per_step"], chosen["gpu_launches"]
 
-    # roofline of the dominant kernel
-    peak_alu_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    # roofline of the dominant kernel; the FP32 peak is the probe's measured rate
+    peak_alu_tflops = fp32_peak["tflops"]
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -354,7 +364,8 @@ def run_ours(args):
         r = per_phase[dominant]
         roof = {"kernel": dominant, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
                 "unit": r["unit"], "frac": r["frac"], "traffic": traffic,
-                "peak_source": ("FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz"
+                "peak_source": ("FP32 multiply-add rate measured on this GPU in this run "
+                                "(dl_fp32_probe, best of FFMA and FFMA2, CUDA events; of measured)"
                                 if r["bound"] == "alu" else
                                 "MEASURED_PEAKS.json (of measured; TF32 = bf16/2 nominal ratio)")}
 
@@ -401,13 +412,22 @@ def run_ours(args):
     if not args.no_learned:
         learned = run_learned(args, dl, torch, st)
 
+    c1 = None
+    if not args.no_c1:
+        c1 = run_c1(args, dl, torch, st, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         Ys, Ds, sp = synth.workload_inputs(args.workload, m=args.cpu_sample)
-        times, cores = cpu_oracle_steps(Ys, Ds, s, 2)
+        times, cores = cpu_oracle_steps(Ys, Ds, s, 3)
         cpu = {"value": sp["m"] / statistics.mean(times), "unit": UNIT, "cores": cores,
                "kind": "oracle",
-               "sample": f"{sp['m']} of {m} signals, 2 FP64 DL iterations (Batch-OMP + PAK-SVD)"}
+               "sample": f"{sp['m']} of {m} signals, 3 FP64 DL iterations (Batch-OMP + PAK-SVD), "
+                         f"each timed"}
+        # the same leg: the oracle's RMSE pair is the reference of each form's error
+        errs = oracle_errors(dl, torch, st, form_dicts, Ys[:ERR_SAMPLE], s, p, n)
+        for prec, e in errs.items():
+            forms[prec]["error_vs_fp64_oracle"] = e
 
     for c in ctxs.values():
         dl.dl_destroy(c)
@@ -425,11 +445,119 @@ def run_ours(args):
                                   f"{100 * EQUAL_RMSE:.0f}% of the plain FP32 form"}),
                 "roofline": roof, "phases_ms": phases, "phase_roofline": per_phase,
                 "forms": forms, "atom_update_variants": variants, "batched": batched, "table1": table1,
-                "learned": learned,
+                "learned": learned, "c1": c1, "fp32_peak": fp32_peak,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def measure_fp32_peak(dl, torch, st, iters=65536):
+    """The SM array's FP32 multiply-add rate: the probe kernel (independent FMA
+    chains, 4 CTAs x 256 threads per SM) timed with CUDA events on the stream it
+    is launched on, best of 3 launches, scalar FFMA and packed FFMA2 forms."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = torch.empty(sms * 4 * 256, dtype=torch.float32, device="cuda")
+    rates = {}
+    for packed in (0, 1):
+        dl.dl_fp32_probe(packed, 256, out, st)          # warm-up (module load, clocks)
+        best = 0.0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            flops = dl.dl_fp32_probe(packed, iters, out, st)
+            e1.record(st)
+            st.synchronize()
+            best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        rates["ffma2" if packed else "ffma"] = best
+    nominal = sms * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    return {"tflops": max(rates.values()), "unit": "TFLOP/s", "by_form": rates, "sms": sms,
+            "nominal_at_2070_mhz": nominal}
+
+
+def oracle_errors(dl, torch, st, form_dicts, Ys, s, p, n):
+    """Teacher-forced error of each precision form against the FP64 oracle: from
+    every dictionary D^(k) the form's own 50-iteration run passed through, one
+    iteration of the form on the GPU and one of the oracle (D^(k) promoted to
+    FP64) on the same sample of signals; |rho_gpu - rho_oracle| for the pair
+    (after coding, after the atom update) of each iteration."""
+    import oracle
+    ms = Ys.shape[0]
+    Ysd = torch.from_numpy(np.ascontiguousarray(Ys)).cuda()
+    cp = torch.zeros(ms + 1, dtype=torch.int64, device="cuda")
+    ri = torch.zeros(ms * s, dtype=torch.int32, device="cuda")
+    v = torch.zeros(ms * s, dtype=torch.float32, device="cuda")
+    Y64 = np.ascontiguousarray(Ys, np.float64)
+    out = {}
+    for prec, dks in form_dicts.items():
+        ctx = dl.dl_init(p, n, ms, s, PRECISIONS[prec], st)
+        d_omp, d_jau, ref = [], [], []
+        for Dk in dks:
+            rm = np.zeros(2)
+            dl.dl_iterate(ctx, Ysd, ms, torch.from_numpy(Dk).cuda(), s, 1, cp, ri, v, rm)
+            _, _, _, _, r = oracle.dl(Y64, Dk.astype(np.float64), s, 1)
+            d_omp.append(abs(rm[0] - r[0, 0]))
+            d_jau.append(abs(rm[1] - r[0, 1]))
+            ref.append([float(r[0, 0]), float(r[0, 1])])
+        dl.dl_destroy(ctx)
+        out[prec] = {"signals": ms, "iterations": len(dks),
+                     "max_abs_rho_omp": float(max(d_omp)), "max_abs_rho_jau": float(max(d_jau)),
+                     "final_abs_rho_omp": float(d_omp[-1]), "final_abs_rho_jau": float(d_jau[-1]),
+                     "per_iteration_abs": [[float(a), float(b)] for a, b in zip(d_omp, d_jau)],
+                     "oracle_final_rho": ref[-1]}
+    return out
+
+
+def run_c1(args, dl, torch, st, flush):
+    """The smaller plain workload: p=64, n=256, s=6, m=20000, 50 iterations from
+    the same start.  Per-iteration time (single-iteration calls, L2 flushed
+    between them, CUDA events), the time of all 50 iterations as one call (one
+    graph launch), and the RMSE pair of the last iteration."""
+    Y, D, spec = synth.workload_inputs("patch_n256")
+    m, p, n, s, iters = spec["m"], spec["p"], spec["n"], spec["s"], spec["iters"]
+    Yd, D0 = torch.from_numpy(Y).cuda(), torch.from_numpy(D).cuda()
+    cp = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+    ri = torch.zeros(m * s, dtype=torch.int32, device="cuda")
+    v = torch.zeros(m * s, dtype=torch.float32, device="cuda")
+    ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, st)
+    Dd = D0.clone()
+    with torch.cuda.stream(st):
+        for _ in range(5):
+            flush.zero_()
+            dl.dl_iterate(ctx, Yd, m, Dd, s, 1, cp, ri, v, None)
+    st.synchronize()
+    steps = 20
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    with torch.cuda.stream(st):
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(st)
+            dl.dl_iterate(ctx, Yd, m, Dd, s, 1, cp, ri, v, None)
+            ev[k][1].record(st)
+    st.synchronize()
+    ms_step = statistics.median(a.elapsed_time(b) for a, b in ev)
+    Dq = D0.clone()
+    dl.dl_iterate(ctx, Yd, m, Dq, s, iters, cp, ri, v, None)      # capture of the 50-iteration call
+    Dq.copy_(D0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    dl.dl_iterate(ctx, Yd, m, Dq, s, iters, cp, ri, v, None)
+    e1.record(st)
+    st.synchronize()
+    ms_all = e0.elapsed_time(e1)
+    Dq.copy_(D0)
+    torch.cuda.synchronize()
+    rm = np.zeros(2 * iters)
+    dl.dl_iterate(ctx, Yd, m, Dq, s, iters, cp, ri, v, rm)
+    dl.dl_destroy(ctx)
+    return {"workload": f"patch_n256: 1/f^2 8x8 patches, p={p} n={n} s={s} m={m}",
+            "value": m / (ms_step * 1e-3), "unit": UNIT, "ms_per_iteration": ms_step,
+            "ms_per_iteration_in_50_iteration_call": ms_all / iters,
+            "value_in_50_iteration_call": m * iters / (ms_all * 1e-3),
+            "iterations": iters, "final_rmse": [float(rm[-2]), float(rm[-1])],
+            "l2": "flushed between the single-iteration steps"}
 
 
 def run_batched(args, dl, torch, st):

@@ -179,6 +179,21 @@ int dl_iterate(dl_ctx* ctx, const float* Y, int64_t m, float* D, int s, int iter
 int dl_check_bounded_wait(dl_ctx* ctx);
 
 /*
+ * dl_fp32_probe -- measurement aid for the FP32 CUDA-core roofline of the
+ * sparse-coding kernel (the OMP greedy loop of Algorithm 1 step 1 is bound by
+ * FP32 multiply-adds).  The paper has no counterpart.  Enqueues on `stream`
+ * one launch of 4 CTAs x 256 threads per SM, each thread running 8
+ * independent chains of float2 multiply-adds `iters` times (packed FFMA2 when
+ * `packed` != 0, else scalar FFMA), and writes its FLOP count (FMA = 2) to
+ * *flops (host).  The caller times the launch (CUDA events on `stream`);
+ * FLOP / time is the SM array's FP32 multiply-add rate at the running clock.
+ * `out` is a device buffer of 4 * 256 * (SM count) floats that the kernel
+ * never writes in practice (it keeps the chains live).  Returns DL_OK,
+ * DL_EINVAL (null pointers, iters < 1) or DL_ECUDA.
+ */
+int dl_fp32_probe(int packed, int64_t iters, float* out, double* flops, void* stream);
+
+/*
  * dl_set_group_size -- group size ntilde of the atom-update stage (Algorithm 1
  * steps 2-5, Section 3): the atoms are updated in groups of ntilde consecutive
  * atoms [k*ntilde, (k+1)*ntilde), one group after another; the atoms of one
@@ -255,12 +270,29 @@ int dl_correlate(dl_ctx* ctx, const float* Y, int64_t m, const float* D, float* 
  * previous call's contents (the error word is cleared by each call), so calls
  * whose executions overlap on the GPU (different streams) race: order them.
  * Calls no cudaMalloc, cudaFree or allocating library routine.
- * Returns DL_OK, DL_EINVAL or DL_ECUDA.
+ * Returns DL_OK, DL_EINVAL or DL_ECUDA at enqueue time.  A bounded wait of the
+ * tensor-core kernel that gives up (the product is then incomplete) is
+ * recorded in the scratch array's error word and reported by
+ * dl_correlate_noalloc_status, not by this call.
  */
 #define DL_NOALLOC_MAX_N 512
 #define DL_NOALLOC_MAX_P 64
 int dl_correlate_noalloc(const float* Y, int64_t m, const float* D, int p, int n, float* A,
                          void* stream);
+
+/*
+ * dl_correlate_noalloc_status -- the device-side status of the allocation-free
+ * correlations enqueued so far on the current device.  The paper has no
+ * counterpart.  Synchronises `stream` (the stream the calls were enqueued on),
+ * copies the error word of the shared scratch array into a host int, clears
+ * it, and returns DL_ETIMEOUT if a bounded wait of the tensor-core kernel gave
+ * up (its output A is then incomplete), DL_ENUMERIC if a non-finite value was
+ * flagged, DL_OK otherwise, or DL_ECUDA if the copy or the synchronisation
+ * failed.  Allocates nothing.  The word is shared by every call on the device
+ * and each dl_correlate_noalloc call clears it when it starts, so ask for the
+ * status after each call whose output matters, before the next call.
+ */
+int dl_correlate_noalloc_status(void* stream);
 
 /*
  * dl_last_resolved -- synchronise and return how many signals of the most

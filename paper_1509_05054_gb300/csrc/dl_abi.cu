@@ -75,7 +75,6 @@ struct dl_ctx {
   // FP64 re-solve of signals whose FP32 pivot fell below 1e-6
   int* rs_list = nullptr;
   int* rs_count = nullptr;
-  double* rs_scratch = nullptr;
   int64_t rs_flagged = 0;  // total flagged (read back at synchronising calls)
   // learned proposer attached (dl_attach_proposer)
   dl_proposer* prop = nullptr;
@@ -125,6 +124,7 @@ struct dl_ctx {
   int64_t launches = 0;
   // launch shapes (chosen by dl_autotune; defaults otherwise)
   int cfg_omp_warps = 4;  // warps per CTA of the OMP kernel
+  int cfg_omp_tm = 5;     // warps per TMEM quadrant of the TMEM-resident OMP kernel (0: off)
   int cfg_acc_mult = 1;   // accumulation CTAs: 1x or 2x the base count
   int cfg_row_per_sm = 4; // row-update CTAs per SM
   int cfg_corr_tc = 1;    // tensor-core correlations when the shape allows
@@ -164,7 +164,7 @@ void free_ctx(dl_ctx* c) {
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->st2) cudaStreamDestroy(c->st2);
   void* ptrs[] = {c->G, c->A0, c->Dhi, c->Dlo, c->Ylp, c->Ysc, c->Dlp, c->Dsc, c->rs_list,
-                  c->rs_count, c->rs_scratch, c->sidx, c->sval, c->scnt, c->bsum, c->err, c->iter, c->rmse,
+                  c->rs_count, c->sidx, c->sval, c->scnt, c->bsum, c->err, c->iter, c->rmse,
                   c->jw.Upart, c->jw.U, c->jw.epart_a, c->jw.epart_b, c->jw.Dn, c->jw.C,
                   c->hY, c->hD, c->hcolptr, c->hrowidx, c->hval, c->pidx, c->pval, c->pcnt,
                   c->pvalid, c->D0};
@@ -323,8 +323,8 @@ cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D
                       c->sval, c->scnt, c->rr_ref, c->err, c->rs_list, c->rs_count, (int)c->m_max,
                       c->st);
   if (e != cudaSuccess) return e;
-  e = dlk::omp_resolve64(Y, c->p, D, c->n, s, c->rs_list, c->rs_count, (int)c->m_max,
-                         c->rs_scratch, c->sidx, c->sval, c->scnt, c->st);
+  e = dlk::omp_resolve64(Y, c->p, D, c->G, lp_ok(c) ? nullptr : c->A0, c->lda, c->n, s,
+                         c->rs_list, c->rs_count, (int)c->m_max, c->sidx, c->sval, c->scnt, c->st);
   mark(c, 3);
   return e;
 }
@@ -352,12 +352,16 @@ cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s)
   mark(c, 2);
   e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st);
   if (e != cudaSuccess) return e;
-  e = dlk::omp_batch(c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval, c->scnt, c->err,
-                     c->rs_list, c->rs_count, (int)c->m_max, c->cfg_omp_warps,
-                     c->prop ? c->rr_ref : nullptr, c->st);
+  if (c->cfg_omp_tm && !c->prop && dlk::omp_tm_supported(c->n, s))
+    e = dlk::omp_batch_tm(c->cfg_omp_tm, c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval,
+                          c->scnt, c->err, c->rs_list, c->rs_count, (int)c->m_max, c->st);
+  else
+    e = dlk::omp_batch(c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval, c->scnt, c->err,
+                       c->rs_list, c->rs_count, (int)c->m_max, c->cfg_omp_warps,
+                       c->prop ? c->rr_ref : nullptr, lp_ok(c) ? 0.f : dlk::kGapTol, c->st);
   if (e != cudaSuccess) return e;
-  e = dlk::omp_resolve64(Y, c->p, D, c->n, s, c->rs_list, c->rs_count, (int)c->m_max,
-                         c->rs_scratch, c->sidx, c->sval, c->scnt, c->st);
+  e = dlk::omp_resolve64(Y, c->p, D, c->G, lp_ok(c) ? nullptr : c->A0, c->lda, c->n, s,
+                         c->rs_list, c->rs_count, (int)c->m_max, c->sidx, c->sval, c->scnt, c->st);
   mark(c, 3);
   return e;
 }
@@ -502,12 +506,17 @@ cudaError_t enq_omp_staged(dl_ctx* c, const float* hostY, const float* dY, int64
     if (e != cudaSuccess) return e;
     first = false;
     if ((e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
-    e = dlk::omp_batch(Aq, c->lda, c->G, c->n, Yq, c->p, mk, s, c->sidx + off * s,
-                       c->sval + off * s, c->scnt + off, c->err, c->rs_list, c->rs_count,
-                       (int)c->m_max, c->cfg_omp_warps, nullptr, c->st);
+    if (c->cfg_omp_tm && dlk::omp_tm_supported(c->n, s))
+      e = dlk::omp_batch_tm(c->cfg_omp_tm, Aq, c->lda, c->G, c->n, Yq, c->p, mk, s, c->sidx + off * s,
+                            c->sval + off * s, c->scnt + off, c->err, c->rs_list, c->rs_count,
+                            (int)c->m_max, c->st);
+    else
+      e = dlk::omp_batch(Aq, c->lda, c->G, c->n, Yq, c->p, mk, s, c->sidx + off * s,
+                         c->sval + off * s, c->scnt + off, c->err, c->rs_list, c->rs_count,
+                         (int)c->m_max, c->cfg_omp_warps, nullptr, dlk::kGapTol, c->st);
     if (e != cudaSuccess) return e;
-    e = dlk::omp_resolve64(Yq, c->p, D, c->n, s, c->rs_list, c->rs_count, (int)c->m_max,
-                           c->rs_scratch, c->sidx + off * s, c->sval + off * s, c->scnt + off,
+    e = dlk::omp_resolve64(Yq, c->p, D, c->G, Aq, c->lda, c->n, s, c->rs_list, c->rs_count,
+                           (int)c->m_max, c->sidx + off * s, c->sval + off * s, c->scnt + off,
                            c->st);
     if (e != cudaSuccess) return e;
     k += 3;
@@ -663,6 +672,7 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
   c->precision = precision;
   c->st = (cudaStream_t)stream;
   c->lda = ((int64_t)n + 31) / 32 * 32;
+  if (const char* v = getenv("DL_OMP_TM")) c->cfg_omp_tm = atoi(v);  // 0 (off), 4, 5 or 6
   const size_t mm = (size_t)m_max;
   c->jw.nb_accum = dlk::jau_accum_blocks_max(p, n);
   c->jw.nb_row = dlk::jau_row_blocks_max();
@@ -676,8 +686,7 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
             dalloc(&c->jw.U, ulen) && dalloc(&c->jw.epart_a, (size_t)2 * c->jw.nb_accum) &&
             dalloc(&c->jw.epart_b, (size_t)c->jw.nb_row) && dalloc(&c->jw.Dn, (size_t)n * p) &&
             dalloc(&c->jw.C, (size_t)n) && dalloc(&c->Dhi, (size_t)n * p) &&
-            dalloc(&c->Dlo, (size_t)n * p) && dalloc(&c->rs_list, mm) && dalloc(&c->rs_count, 1) &&
-            dalloc(&c->rs_scratch, (size_t)dlk::DL_RESOLVE_WARPS * (dlk::DL_RESOLVE_SMAX + 1) * n);
+            dalloc(&c->Dlo, (size_t)n * p) && dalloc(&c->rs_list, mm) && dalloc(&c->rs_count, 1);
   ok = ok && cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) == cudaSuccess &&
        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
@@ -735,6 +744,12 @@ int dl_check_bounded_wait(dl_ctx* c) {
   DL_CHECK(dlk::bounded_wait_check(c->err, c->st));
   c->launches += 1;
   return take_device_error(c);
+}
+
+int dl_fp32_probe(int packed, int64_t iters, float* out, double* flops, void* stream) {
+  if (!out || !flops || iters < 1) return DL_EINVAL;
+  DL_CHECK(dlk::ffma_probe(packed, iters, out, flops, (cudaStream_t)stream));
+  return DL_OK;
 }
 
 int dl_set_group_size(dl_ctx* c, int ntilde) {

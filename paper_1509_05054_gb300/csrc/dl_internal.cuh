@@ -16,6 +16,12 @@ enum : int {
 
 constexpr float kPivotMin = 1e-6f;     // Cholesky pivot delta below this: dependent atom, stop
 constexpr float kResidRel = 1e-6f;     // residual energy below this * ||y||^2: stop
+// Long supports (s > 8): a top-two |alpha| gap below kGapTol ||y|| sends the
+// signal to the re-solve, which takes the FP64 decisions.  The FP32
+// error of alpha after up to 16 steps -- split-TF32 correlations (~2^-22
+// relative per product) plus the rounding of the progressive Cholesky updates --
+// stays below 1e-6 ||y|| on unit atoms; the tolerance keeps a factor of 4.
+constexpr float kGapTol = 4e-6f;
 
 // ---- correlations and Gram --------------------------------------------------
 // C[i*ldc + j] = sum_r A[i*p + r] * B[j*p + r]  for i < rows_a, j < rows_b (FP32, CUDA cores)
@@ -37,6 +43,9 @@ cudaError_t corr_tf32x3_pair(const float* A0, int64_t rows0, float* C0, int64_t 
 // Diagnostic: a wait on an mbarrier nothing arrives at, bounded as in the
 // tensor-core kernels; sets ERR_TIMEOUT in *err after about 2 s.
 cudaError_t bounded_wait_check(int* err, cudaStream_t st);
+// FP32 multiply-add throughput probe (k_diag.cu): launches 4 CTAs per SM running
+// independent FMA chains; *flops receives the FLOP count of the launch.
+cudaError_t ffma_probe(int packed, int64_t iters, float* out, double* flops, cudaStream_t st);
 
 // Reduced-precision correlations (k_corr_lp.cu): operands converted to padded
 // row-major BF16 or E4M3 (+ inverse row scales) buffers, then tcgen05 MMAs.
@@ -53,12 +62,20 @@ cudaError_t corr_lp(int kind, const void* A, int64_t rows_a, const float* a_inv_
 
 // Batch-OMP of m signals from their correlations A0 (row i = D^T y_i, stride lda) and G = D^T D.
 // Writes s slots per signal (atoms ascending, unused slots idx = -1) and the count.
-// Signals stopped by a pivot below kPivotMin are appended to rs_list (if given) for the
-// FP64 re-solve.
+// Signals stopped by a pivot below kPivotMin, and (s > 8, gap_tol > 0) signals with a
+// top-two gap below gap_tol ||y|| at some step, are appended to rs_list (if given) for
+// the FP64 re-solve.
 cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                       int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
                       int* rs_list, int* rs_count, int rs_cap, int warps_per_block,
-                      float* ores, cudaStream_t st);
+                      float* ores, float gap_tol, cudaStream_t st);
+
+// The same Batch-OMP with the progressive-Cholesky vectors in tensor memory
+// (k_omp_tm.cu): persistent CTAs of 4q warps (q = 4, 5, 6).  n = 512, 5 <= s <= 8.
+bool omp_tm_supported(int n, int s);
+cudaError_t omp_batch_tm(int q, const float* A0, int64_t lda, const float* G, int n, const float* Y,
+                         int p, int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
+                         int* rs_list, int* rs_count, int rs_cap, cudaStream_t st);
 
 // OMP restricted to K ascending candidates per signal (the learned proposer's
 // path) and the full-OMP fallback of listed signals.  ores: residual-energy
@@ -89,12 +106,15 @@ cudaError_t mlp_adam(float* w, const float* g, float* m, float* v, int64_t count
                      void* wbf, cudaStream_t st);
 cudaError_t mlp_topk(const void* z, int64_t m, int n, int K, int32_t* cand, cudaStream_t st);
 
-// FP64 re-solve (k_resolve.cu): full FP64 OMP of the listed signals, overwriting their slots.
+// Re-solve (k_resolve.cu) of the listed signals with the FP64 Batch-OMP's decisions and
+// coefficients (FP64 residual and Cholesky factor, FP32 correlations with an exact check of
+// the atoms within their error bound), overwriting their slots.  G: the FP32 Gram matrix;
+// A0 (row i = FP32 D^T y_i, stride lda) or null to take D^T y here.  p <= 128, s <= 16.
 constexpr int DL_RESOLVE_SMAX = 16;
-constexpr int DL_RESOLVE_WARPS = 64;
-cudaError_t omp_resolve64(const float* Y, int p, const float* D, int n, int s, const int* list,
-                          const int* count, int cap, double* scratch, int32_t* idx, float* val,
-                          int32_t* cnt, cudaStream_t st);
+constexpr int DL_RESOLVE_WARPS = 608;  // CTAs of one warp
+cudaError_t omp_resolve64(const float* Y, int p, const float* D, const float* G, const float* A0,
+                          int64_t lda, int n, int s, const int* list, const int* count, int cap,
+                          int32_t* idx, float* val, int32_t* cnt, cudaStream_t st);
 bool omp_supported(int n, int s);
 
 // ---- JAU / PAK-SVD (group size n) ---------------------------------------------

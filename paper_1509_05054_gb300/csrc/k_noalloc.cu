@@ -58,10 +58,11 @@ extern "C" int dl_correlate_noalloc(const float* Y, int64_t m, const float* D, i
     return DL_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   if (m == 0) return DL_OK;
-  const bool tc = dlk::corr_tc_supported(Y, p, n, n) && dlk::corr_tc_supported(D, p, n, n);
+  const bool tc = dlk::corr_tc_supported(Y, p, n, n) && dlk::corr_tc_supported(D, p, n, n) &&
+                  ((uintptr_t)A % 16) == 0;
   if (!tc) {
-    // p not a multiple of 4, n not a multiple of 16 or unaligned operands: the FP32
-    // CUDA-core GEMM, which needs no scratch
+    // p not a multiple of 4, n not a multiple of 16 or an operand (A included) off a
+    // 16-byte boundary: the FP32 CUDA-core GEMM, which needs no scratch
     return dlk::gemm_nt_simt(Y, m, D, n, p, A, n, st) == cudaSuccess ? DL_OK : DL_ECUDA;
   }
   int dev = 0;
@@ -74,5 +75,20 @@ extern "C" int dl_correlate_noalloc(const float* Y, int64_t m, const float* D, i
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return DL_ECUDA;
   if (dlk::split_tf32(D, (int64_t)n * p, dhi, dlo, st) != cudaSuccess) return DL_ECUDA;
   if (dlk::corr_tf32x3(Y, m, dhi, dlo, n, p, A, n, err, st) != cudaSuccess) return DL_ECUDA;
+  return DL_OK;
+}
+
+extern "C" int dl_correlate_noalloc_status(void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  float* scratch = scratch_for_current_device(&dev);
+  if (!scratch) return DL_ECUDA;
+  int* err = (int*)(scratch + kScratchFloats);
+  int h = 0;  // a host int: the copy below allocates nothing on the device
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return DL_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return DL_ECUDA;
+  if (h && cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return DL_ECUDA;
+  if (h & dlk::ERR_NONFINITE) return DL_ENUMERIC;
+  if (h & dlk::ERR_TIMEOUT) return DL_ETIMEOUT;
   return DL_OK;
 }

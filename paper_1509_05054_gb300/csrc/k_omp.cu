@@ -21,53 +21,15 @@
 // rest in shared memory (see reg_us).  Selected atoms are masked by setting their alpha to NaN,
 // which the argmax ignores.
 #include "dl_internal.cuh"
+#include "omp_common.cuh"
 
 #include <math.h>
 
 namespace dlk {
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
+using namespace omp;
 constexpr int OMP_THREADS = 128;
-
-// Read-only load that does not allocate in L1: each signal's correlations and
-// samples are read once, and keeping them out of L1 leaves it to the Gram rows
-// every step reads (measured: OMP 2.4% faster than plain loads).
-__device__ __forceinline__ float ld_stream(const float* p) {
-  float v;
-  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
-  return v;
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  return v;
-}
-
-// Bits of the argmax key that carry the element index t within a lane.
-template <int NT>
-constexpr int tbits() {
-  return NT <= 1 ? 0 : NT <= 2 ? 1 : NT <= 4 ? 2 : NT <= 8 ? 3 : NT <= 16 ? 4 : 5;
-}
-
-template <int NT>
-__device__ __forceinline__ float elem(const float2 (&a)[NT / 2], int t) {
-  return (t & 1) ? a[t >> 1].y : a[t >> 1].x;
-}
-
-// Argmax key of element t: |alpha| with the low TB mantissa bits replaced by
-// (NT-1-t).  The float maximum of the keys gives the largest |alpha| and, among
-// values equal to within 2^-(23-TB) relative, the lowest t; NaN (masked)
-// elements are ignored by fmaxf.
-template <int NT, int LO, int CNT>
-__device__ __forceinline__ float key_max(const float2 (&a)[NT / 2], unsigned vmask) {
-  if constexpr (CNT == 1) {
-    return __uint_as_float((__float_as_uint(elem<NT>(a, LO)) & vmask) | (unsigned)(NT - 1 - LO));
-  } else {
-    return fmaxf(key_max<NT, LO, CNT / 2>(a, vmask), key_max<NT, LO + CNT / 2, CNT - CNT / 2>(a, vmask));
-  }
-}
 
 // On the lane owning atom sel = 32*tsel + lane: read alpha[tsel] and mask it
 // (NaN), and read u_q[tsel] for q < step.  Executed by one lane; the dense
@@ -157,13 +119,18 @@ struct GramRestricted {
 // the others in u_s (this warp's shared-memory slice).
 // Outputs slots i*s.. (atom index = idxmap[j] when idxmap is given), the count,
 // and the residual-energy estimate ||y||^2 - sum z^2 in ores[i] when given.
+// Long supports (SMAX >= 12, s > 8): a step whose top two |alpha| lie closer than
+// gap_tol ||y|| is a decision FP32 cannot be trusted with -- the accumulated
+// rounding of alpha over many steps is of that size -- so the signal is handed
+// to the re-solve (rs_list), which takes the FP64 decisions, and its FP32 run
+// stops there.
 template <int NT, int SMAX, int NR, bool FULLN, bool A0G, class GSrc>
 __device__ __forceinline__ void omp_one(
     int64_t i, const GSrc& gsrc, float (&L)[SMAX][SMAX], float (&C)[SMAX], float2* u_s,
     const float* __restrict__ a0row, int n, const float* __restrict__ y, int p, int s,
     const int32_t* __restrict__ idxmap, int32_t* __restrict__ oidx, float* __restrict__ oval,
     int32_t* __restrict__ ocnt, float* __restrict__ ores, int* __restrict__ err,
-    int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap) {
+    int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap, float gap_tol) {
   static_assert(NT >= 2 && NT % 2 == 0, "alpha is held in float2 pairs");
   constexpr int NV = NT / 2;
   constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
@@ -209,7 +176,7 @@ __device__ __forceinline__ void omp_one(
   for (int step = 0; step < SMAX; ++step) {
     if (step >= s || !finite_in) break;
     // ---- argmax |alpha| over unselected atoms (see key_max); lowest lane on ties
-    const float kmax = fmaxf(0.f, key_max<NT, 0, NT>(alpha, VMASK));
+    const float kmax = keys_max<NT>(alpha, VMASK);
     const unsigned kbits = __reduce_max_sync(FULL, __float_as_uint(kmax));
     if ((kbits & VMASK) == 0u) break;  // max |alpha| = 0
     const unsigned ball = __ballot_sync(FULL, __float_as_uint(kmax) == kbits);
@@ -240,6 +207,22 @@ __device__ __forceinline__ void omp_one(
       amine = Take<NT, NPHI>::run(alpha, u_at, tsel, step, ul, qnan);
     }
     const float asel = __shfl_sync(FULL, amine, lsel);
+    if constexpr (SMAX >= 12) {
+      if (gap_tol > 0.f && rs_count) {
+        // second largest |alpha| (the winner is masked now), full precision
+        float top2 = 0.f;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) top2 = fmaxf(top2, fmaxf(fabsf(alpha[v].x), fabsf(alpha[v].y)));
+        top2 = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(top2)));
+        if (fabsf(asel) - top2 < gap_tol * sqrtf(yy)) {
+          if (lane == 0) {
+            const int pos = atomicAdd(rs_count, 1);
+            if (pos < rs_cap) rs_list[pos] = (int)i;
+          }
+          break;
+        }
+      }
+    }
     float wsq = 0.f;
 #pragma unroll
     for (int q = 0; q < SMAX - 1; ++q) {
@@ -338,7 +321,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
     const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
     float* __restrict__ oval, int32_t* __restrict__ ocnt, float* __restrict__ ores,
     int* __restrict__ err, int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap,
-    int64_t pf) {
+    int64_t pf, float gap_tol) {
   constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
   extern __shared__ float2 smem_u[];
   __shared__ float Lsh[OMP_THREADS / 32][SMAX][SMAX];  // per warp: L[j][q] (q < j)
@@ -361,7 +344,8 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_warp_kernel(
   float2* u_s = NR < NPHI ? smem_u + (size_t)wib * (NPHI - NR) * (NT / 2) * 32 : nullptr;
   const GramGlobal<FULLN> gsrc{G, n};
   omp_one<NT, SMAX, NR, FULLN, true>(i, gsrc, Lsh[wib], Csh[wib], u_s, A0 + i * lda, n, Y + i * p, p,
-                                s, nullptr, oidx, oval, ocnt, ores, err, rs_list, rs_count, rs_cap);
+                                s, nullptr, oidx, oval, ocnt, ores, err, rs_list, rs_count, rs_cap,
+                                gap_tol);
 }
 
 // OMP restricted to K proposed candidates per signal (cand: m x K, ascending):
@@ -394,7 +378,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_restricted_kernel(
   __syncwarp();
   const GramRestricted gsrc{G, n, ci, K};
   omp_one<2, SMAX, (SMAX > 1 ? SMAX - 1 : 1), false, false>(i, gsrc, Lsh[wib], Csh[wib], nullptr, a0sh[wib], K, y, p, s, ci,
-                                 oidx, oval, ocnt, ores, err, nullptr, nullptr, 0);
+                                 oidx, oval, ocnt, ores, err, nullptr, nullptr, 0, 0.f);
   __syncwarp();
   if (lane == 0 && fb_count && ores[i] > tol2 * ref_res[i]) {
     const int pos = atomicAdd(fb_count, 1);
@@ -421,7 +405,7 @@ __global__ void __launch_bounds__(OMP_THREADS) omp_listed_kernel(
     const GramGlobal<false> gsrc{G, n};
     omp_one<NT, SMAX, (SMAX > 1 ? SMAX - 1 : 1), false, true>(i, gsrc, Lsh[wib], Csh[wib], nullptr, A0 + i * lda, n, Y + i * p,
                                     p, s, nullptr, oidx, oval, ocnt, ores, err, rs_list, rs_count,
-                                    rs_cap);
+                                    rs_cap, 0.f);
     __syncwarp();
   }
 }
@@ -430,7 +414,7 @@ template <int NT, int SMAX, int NR, bool FULLN>
 cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                      int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
                      int* rs_list, int* rs_count, int rs_cap, int warps_hint, float* ores,
-                     cudaStream_t st) {
+                     float gt, cudaStream_t st) {
   constexpr int NPHI = SMAX > 1 ? SMAX - 1 : 1;
   int warps = (warps_hint >= 1 && warps_hint <= OMP_THREADS / 32) ? warps_hint : OMP_THREADS / 32;
   size_t smem = 0;
@@ -449,7 +433,7 @@ cudaError_t launch_t(const float* A0, int64_t lda, const float* G, int n, const 
   const int64_t blocks = (m + warps - 1) / warps;
   omp_warp_kernel<NT, SMAX, NR, FULLN><<<(unsigned)blocks, warps * 32, smem, st>>>(
       A0, lda, G, n, Y, p, m, s, idx, val, cnt, ores, err, rs_list, rs_count, rs_cap,
-      (int64_t)8 * num_sms());
+      (int64_t)8 * num_sms(), gt);
   return cudaGetLastError();
 }
 
@@ -469,21 +453,21 @@ constexpr int reg_us() {
 template <int NT, int SMAX>
 cudaError_t pick_store(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                        int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                       int* rl, int* rc, int rcap, int wh, float* ores, cudaStream_t st) {
+                       int* rl, int* rc, int rcap, int wh, float* ores, float gt, cudaStream_t st) {
   constexpr int NR = reg_us<NT, SMAX>();
   if (n == 32 * NT)
-    return launch_t<NT, SMAX, NR, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
-  return launch_t<NT, SMAX, NR, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+    return launch_t<NT, SMAX, NR, true>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, gt, st);
+  return launch_t<NT, SMAX, NR, false>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, gt, st);
 }
 
 template <int NT>
 cudaError_t pick_s(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                    int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                   int* rl, int* rc, int rcap, int wh, float* ores, cudaStream_t st) {
-  if (s <= 4) return pick_store<NT, 4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
-  if (s <= 8) return pick_store<NT, 8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
-  if (s <= 12) return pick_store<NT, 12>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
-  return pick_store<NT, 16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+                   int* rl, int* rc, int rcap, int wh, float* ores, float gt, cudaStream_t st) {
+  if (s <= 4) return pick_store<NT, 4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, gt, st);
+  if (s <= 8) return pick_store<NT, 8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, gt, st);
+  if (s <= 12) return pick_store<NT, 12>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, gt, st);
+  return pick_store<NT, 16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, gt, st);
 }
 
 }  // namespace
@@ -541,14 +525,14 @@ cudaError_t omp_listed(const int* list, const int* count, const float* A0, int64
 
 cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                       int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                      int* rl, int* rc, int rcap, int wh, float* ores, cudaStream_t st) {
+                      int* rl, int* rc, int rcap, int wh, float* ores, float gt, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   const int nt = (n + 31) / 32;
-  if (nt <= 2) return pick_s<2>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
-  if (nt <= 4) return pick_s<4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
-  if (nt <= 8) return pick_s<8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
-  if (nt <= 16) return pick_s<16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
-  return pick_s<32>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, st);
+  if (nt <= 2) return pick_s<2>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, gt, st);
+  if (nt <= 4) return pick_s<4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, gt, st);
+  if (nt <= 8) return pick_s<8>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, gt, st);
+  if (nt <= 16) return pick_s<16>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, gt, st);
+  return pick_s<32>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, wh, ores, gt, st);
 }
 
 }  // namespace dlk

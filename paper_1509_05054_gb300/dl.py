@@ -75,6 +75,8 @@ def load(build_if_missing: bool = True):
         lib.dl_correlate.argtypes = [P, P, i64, P, P]
         lib.dl_uses_tensor_cores.argtypes = [P]
         lib.dl_correlate_noalloc.argtypes = [P, i64, P, i32, i32, P, P]
+        lib.dl_correlate_noalloc_status.argtypes = [P]
+        lib.dl_fp32_probe.argtypes = [i32, i64, P, P, P]
         lib.dl_last_resolved.argtypes = [P]
         lib.dl_last_resolved.restype = i64
         lib.dl_phase_times.argtypes = [P, P, i32]
@@ -102,7 +104,8 @@ def load(build_if_missing: bool = True):
             getattr(lib, name).restype = i32
         for name in ("dl_init", "dl_set_stream", "dl_destroy", "omp_code", "jau_update", "dl_iterate",
                      "dl_sync", "dl_set_profiling", "dl_phase_times", "dl_gram", "dl_correlate",
-                     "dl_uses_tensor_cores", "dl_correlate_noalloc", "dl_set_group_size",
+                     "dl_uses_tensor_cores", "dl_correlate_noalloc", "dl_correlate_noalloc_status", "dl_fp32_probe",
+                     "dl_set_group_size",
                      "dl_set_update_rule", "dl_batch_set_update_rule", "dl_batch_set_group_size"):
             getattr(lib, name).restype = i32
         _lib = lib
@@ -210,6 +213,20 @@ def dl_correlate_noalloc(Y, m: int, D, p: int, n: int, A, stream=None) -> None:
     synchronisation is not acceptable).  p <= 64, n <= 512."""
     _check(load().dl_correlate_noalloc(_ptr(Y), m, _ptr(D), p, n, _ptr(A), _stream_ptr(stream)),
            "dl_correlate_noalloc")
+
+
+def dl_correlate_noalloc_status(stream=None) -> int:
+    """Synchronise ``stream`` and return (and clear) the device-side status of the
+    allocation-free correlations: DL_OK, DL_ETIMEOUT or DL_ENUMERIC."""
+    return int(load().dl_correlate_noalloc_status(_stream_ptr(stream)))
+
+
+def dl_fp32_probe(packed: int, iters: int, out, stream=None) -> float:
+    """Enqueue the FP32 multiply-add probe on ``stream``; returns its FLOP count."""
+    flops = ctypes.c_double(0.0)
+    _check(load().dl_fp32_probe(int(packed), int(iters), _ptr(out), ctypes.byref(flops),
+                                _stream_ptr(stream)), "dl_fp32_probe")
+    return flops.value
 
 
 def dl_last_resolved(ctx: int) -> int:
