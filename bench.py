@@ -678,18 +678,21 @@ def run_table1(dl, torch, st):
 def run_variants(args, dl, torch, st, Yd, D0, colptr, rowidx, val, flush, m, p, n, s,
                  plain_rmse):
     """Other forms of the atom-update stage beside the Jacobi PAK-SVD: group sizes
-    ntilde < n (groups updated one after another) and the P-SGK and P-NSGK rules
-    (Section 3): time per iteration, and the final RMSE after RMSE_ITERS iterations
-    against the Jacobi PAK-SVD form's."""
-    variants = [(f"ntilde={int(x)}", int(x), 0) for x in args.group_sizes.split(",")
+    ntilde < n (groups updated one after another), the P-SGK and P-NSGK rules
+    (Section 3) and the fixed summation order (dl_set_deterministic): time per
+    iteration, and the final RMSE after RMSE_ITERS iterations against the Jacobi
+    PAK-SVD form's."""
+    variants = [(f"ntilde={int(x)}", int(x), 0, False) for x in args.group_sizes.split(",")
                 if x and 1 <= int(x) < n]
     if args.rules:
-        variants += [("P-SGK", n, 1), ("P-NSGK", n, 2)]
+        variants += [("P-SGK", n, 1, False), ("P-NSGK", n, 2, False)]
+    variants += [("deterministic", n, 0, True)]
     out = {}
-    for name, nt, rule in variants:
+    for name, nt, rule, det in variants:
         ctx = dl.dl_init(p, n, m, s, 0, st)
         dl.dl_set_group_size(ctx, nt)
         dl.dl_set_update_rule(ctx, rule)
+        dl.dl_set_deterministic(ctx, det)
         Dd = D0.clone()
         with torch.cuda.stream(st):
             for _ in range(3):
@@ -714,6 +717,7 @@ def run_variants(args, dl, torch, st, Yd, D0, colptr, rowidx, val, flush, m, p, 
         dl.dl_destroy(ctx)
         out[name] = {"value": m / (ms * 1e-3), "unit": UNIT, "ms_per_iteration": ms,
                      "groups": (n + nt - 1) // nt, "rule": ["PAK-SVD", "P-SGK", "P-NSGK"][rule],
+                     "summation_order": "fixed (bitwise reproducible)" if det else "L2 reductions",
                      "final_rmse": float(rm[-1]),
                      "rmse_vs_pak_svd": (float(rm[-1]) / plain_rmse - 1.0) if plain_rmse else None}
     return out
@@ -723,7 +727,8 @@ def run_learned(args, dl, torch, st):
     """Learned support proposer at p=64, n=512, s=8, m=2e5: plain warm-up, OMP
     labels of disjoint training patches, 5 epochs of training on the GPU, then 20
     DL iterations with the proposer (full OMP every 10th) against 20 plain ones
-    from the same dictionary."""
+    from the same dictionary, and against the same scheme whose candidates are
+    the K largest |D^T y| (no network), at K = 16 and 32."""
     Y, D, spec = synth.workload_inputs("patch_n512_m2e5")
     m, p, n, s = spec["m"], spec["p"], spec["n"], spec["s"]
     K, full_every, iters, warm = 2 * s, 10, 20, 10
@@ -757,15 +762,21 @@ def run_learned(args, dl, torch, st):
     del Ytr, sup
     dl.dl_destroy(ctx)
 
-    def run(with_prop):
+    def attach(c, mode, k):
+        if mode == "learned":
+            dl.dl_attach_proposer(c, prop, k, full_every, 0.01)
+        elif mode == "correlations":
+            dl.dl_attach_correlation_proposer(c, k, full_every, 0.01)
+
+    def run(mode, k=K):
+        with_prop = mode != "plain"
         c = dl.dl_init(p, n, m, s, dl.DL_FP32, st)
-        if with_prop:
-            dl.dl_attach_proposer(c, prop, K, full_every, 0.01)
+        attach(c, mode, k)
         Dd = Dw.clone()
         dl.dl_iterate(c, Yd, m, Dd, s, 1, cp, ri, v, None)       # warm the graphs
         if with_prop:
             dl.dl_iterate(c, Yd, m, Dd, s, 1, cp, ri, v, None)
-            dl.dl_attach_proposer(c, prop, K, full_every, 0.01)   # restart the full/learned cycle
+            attach(c, mode, k)                                    # restart the full/proposed cycle
         Dd.copy_(Dw)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -784,10 +795,20 @@ def run_learned(args, dl, torch, st):
         dl.dl_destroy(c)
         return m * iters / (ms * 1e-3), ms / iters, float(rm[0]), fbs
 
-    v_plain, ms_plain, r_plain, _ = run(False)
-    v_learn, ms_learn, r_learn, fbs = run(True)
+    v_plain, ms_plain, r_plain, _ = run("plain")
+    v_learn, ms_learn, r_learn, fbs = run("learned")
+    # what the trained network gains: the same scheme with the K largest |D^T y| as the
+    # candidates, and both at K = 32
+    others = {}
+    for mode, k in (("correlations", K), ("learned", 32), ("correlations", 32)):
+        vv, mm_, rr_, ff = run(mode, k)
+        others[f"{mode}_K{k}"] = {
+            "value": vv, "ms_per_iteration": mm_, "final_rmse": rr_,
+            "rmse_vs_plain": rr_ / r_plain - 1.0, "speedup_vs_plain": vv / v_plain,
+            "fallback_fraction": float(np.mean(ff) / m) if ff else None}
     dl.dl_proposer_destroy(prop)
     return {"value": v_learn, "unit": UNIT, "ms_per_iteration": ms_learn, "m": m, "K": K,
+            "proposer_comparison": others,
             "full_every": full_every, "iterations": iters, "plain_value": v_plain,
             "plain_ms_per_iteration": ms_plain, "speedup_vs_plain": v_learn / v_plain,
             "final_rmse": r_learn, "plain_final_rmse": r_plain,

@@ -209,6 +209,26 @@ int dl_fp32_probe(int packed, int64_t iters, float* out, double* flops, void* st
 int dl_set_group_size(dl_ctx* ctx, int ntilde);
 
 /*
+ * dl_set_deterministic -- the order in which the atom-update stage sums
+ * U = E X^T and r_j = ||x_j||^2 (Eq. 3, Eq. 5: F x_j^T = U_j + r_j d_j).  The
+ * paper fixes no order; floating-point sums depend on it.
+ *   on = 0 (default): every signal adds its contributions x_{j,i} e_i into
+ *          copies of U in L2 by float vector reductions; the order of those
+ *          additions varies from run to run, so D and X are reproducible to
+ *          rounding, not bit for bit.
+ *   on = 1: the contributions are summed in an order fixed by the signal and
+ *          slot indices (per range of signals, each atom's pairs sorted by
+ *          signal and slot; then the ranges in order), so repeated runs give
+ *          bit-identical D, X and RMSE values.  Slower (about 2x the
+ *          accumulation time at p = 64, n = 512, s = 8).  Needs the float4 data
+ *          path (p % 4 == 0, Y and D 16-byte aligned; other shapes keep the
+ *          default order).
+ * Applies to later jau_update / dl_iterate calls.  Returns DL_OK or DL_EINVAL
+ * (null context).
+ */
+int dl_set_deterministic(dl_ctx* ctx, int on);
+
+/*
  * dl_set_update_rule -- how the atom-update stage treats each atom j of a group
  * (Section 3; F = E_{I_j} + d_j x_{j,I_j}, Eq. 3):
  *   DL_RULE_AKSVD (default)  d_j = F x^T / ||F x^T||, then x_{j,I_j} = F^T d_j
@@ -442,6 +462,18 @@ int dl_proposer_forward(dl_proposer* prop, const float* Y, int64_t m, float* log
  * detaches.  Returns DL_OK, DL_EINVAL or DL_ENOMEM.
  */
 int dl_attach_proposer(dl_ctx* ctx, dl_proposer* prop, int K, int full_every, double tol);
+
+/*
+ * dl_attach_correlation_proposer -- the same sparse-coding scheme as
+ * dl_attach_proposer (K candidates per signal, OMP restricted to them, full
+ * OMP every full_every-th iteration and for the signals whose residual exceeds
+ * their last full OMP's by the margin tol), with the candidates taken without
+ * a network: the K atoms of largest |d_j^T y| (Algorithm 1 step 1's first
+ * correlations).  It is the baseline that shows what the trained network
+ * gains.  Replaces an attached learned proposer; dl_attach_proposer(ctx, NULL,
+ * ...) detaches either.  Returns DL_OK, DL_EINVAL or DL_ENOMEM.
+ */
+int dl_attach_correlation_proposer(dl_ctx* ctx, int K, int full_every, double tol);
 
 /* dl_last_fallbacks -- signals sent to full OMP by the most recent learned
  * iteration (synchronises). */

@@ -88,6 +88,7 @@ struct dl_ctx {
   int32_t* cand = nullptr;   // m_max x K
   void* Ybf = nullptr;       // m_max x pk BF16 copy of Y for the proposer
   bool learned_now = false;  // the iteration being enqueued uses the proposer
+  bool prop_corr = false;    // network-free proposer: the K largest |D^T y| (no MLP)
   cudaGraphExec_t gexec_learned = nullptr;
   int32_t* sidx = nullptr;
   float* sval = nullptr;
@@ -118,13 +119,14 @@ struct dl_ctx {
   const void* hkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int64_t hkey_m = -1;
   int hkey_s = -1;
-  int64_t hsig[10] = {};
+  int64_t hsig[11] = {};
   int hseen = 0;
   int hg_kernels = 0;
   int64_t launches = 0;
   // launch shapes (chosen by dl_autotune; defaults otherwise)
   int cfg_omp_warps = 4;  // warps per CTA of the OMP kernel
   int cfg_omp_tm = 5;     // warps per TMEM quadrant of the TMEM-resident OMP kernel (0: off)
+  int deterministic = 0;  // pass A with a fixed summation order (dl_set_deterministic)
   int cfg_acc_mult = 1;   // accumulation CTAs: 1x or 2x the base count
   int cfg_row_per_sm = 4; // row-update CTAs per SM
   int cfg_corr_tc = 1;    // tensor-core correlations when the shape allows
@@ -301,15 +303,28 @@ cudaError_t enq_corr(dl_ctx* c, const float* Y, int64_t m, const float* D, bool 
 cudaError_t enq_proposer_forward(dl_proposer* P, const void* Xbf, int64_t m, int K, int32_t* cand,
                                  cudaStream_t st);
 int64_t proposer_chunks(dl_proposer* P, int64_t m);
+// A support proposer is attached: the learned one or the network-free one.
+bool has_prop(const dl_ctx* c) { return c->prop != nullptr || c->prop_corr; }
 
 // Sparse coding with the learned proposer: top-K candidates from the MLP,
 // OMP restricted to them, full OMP for the signals whose residual energy
 // exceeds tol2 times the one of their last full OMP.
 cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D, int s, bool tc) {
-  c->omp_kernels[1] = (tc ? 2 : 1) /* Gram */ + 4 * (int)proposer_chunks(c->prop, m) /* 3 GEMMs +
-      top-K per chunk */ + 3 /* restricted, listed, FP64 */ + (lp_ok(c) ? 2 : 1) /* correlations */;
-  cudaError_t e = enq_proposer_forward(c->prop, c->Ybf, m, c->prop_K, c->cand, c->st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (c->prop_corr) {
+    // network-free proposer: the correlations of all signals first, then the K
+    // largest |alpha0| of each
+    c->omp_kernels[1] = (tc ? 2 : 1) /* Gram */ + (lp_ok(c) ? 2 : 1) /* correlations */ +
+                        1 /* top-K */ + 3 /* restricted, listed, re-solve */;
+    if ((e = enq_corr(c, Y, m, D, tc)) != cudaSuccess) return e;
+    if ((e = dlk::topk_abs(c->A0, c->lda, m, c->n, c->prop_K, c->cand, c->st)) != cudaSuccess)
+      return e;
+  } else {
+    c->omp_kernels[1] = (tc ? 2 : 1) /* Gram */ + 4 * (int)proposer_chunks(c->prop, m) /* 3 GEMMs +
+        top-K per chunk */ + 3 /* restricted, listed, re-solve */ + (lp_ok(c) ? 2 : 1) /* correlations */;
+    e = enq_proposer_forward(c->prop, c->Ybf, m, c->prop_K, c->cand, c->st);
+    if (e != cudaSuccess) return e;
+  }
   mark(c, 2);
   if ((e = cudaMemsetAsync(c->fb_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
@@ -318,7 +333,7 @@ cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D
                           c->st);
   if (e != cudaSuccess) return e;
   // the fallback signals read their correlations from the tensor-core product of all signals
-  if ((e = enq_corr(c, Y, m, D, tc)) != cudaSuccess) return e;
+  if (!c->prop_corr && (e = enq_corr(c, Y, m, D, tc)) != cudaSuccess) return e;
   e = dlk::omp_listed(c->fb_list, c->fb_count, c->A0, c->lda, c->G, c->n, Y, c->p, s, c->sidx,
                       c->sval, c->scnt, c->rr_ref, c->err, c->rs_list, c->rs_count, (int)c->m_max,
                       c->st);
@@ -331,7 +346,7 @@ cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D
 
 cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
   const bool tc = tc_ok(c, Y, D);
-  const bool learned = c->prop && c->learned_now;
+  const bool learned = has_prop(c) && c->learned_now;
   mark(c, 0);
   cudaError_t e;
   if (tc && !learned && !lp_ok(c)) {
@@ -352,13 +367,13 @@ cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s)
   mark(c, 2);
   e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st);
   if (e != cudaSuccess) return e;
-  if (c->cfg_omp_tm && !c->prop && dlk::omp_tm_supported(c->n, s))
+  if (c->cfg_omp_tm && !has_prop(c) && dlk::omp_tm_supported(c->n, s))
     e = dlk::omp_batch_tm(c->cfg_omp_tm, c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval,
                           c->scnt, c->err, c->rs_list, c->rs_count, (int)c->m_max, c->st);
   else
     e = dlk::omp_batch(c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval, c->scnt, c->err,
                        c->rs_list, c->rs_count, (int)c->m_max, c->cfg_omp_warps,
-                       c->prop ? c->rr_ref : nullptr, lp_ok(c) ? 0.f : dlk::kGapTol, c->st);
+                       has_prop(c) ? c->rr_ref : nullptr, lp_ok(c) ? 0.f : dlk::kGapTol, c->st);
   if (e != cudaSuccess) return e;
   e = dlk::omp_resolve64(Y, c->p, D, c->G, lp_ok(c) ? nullptr : c->A0, c->lda, c->n, s,
                          c->rs_list, c->rs_count, (int)c->m_max, c->sidx, c->sval, c->scnt, c->st);
@@ -374,7 +389,9 @@ int group_size(dl_ctx* c) { return c->ntilde > 0 && c->ntilde < c->n ? c->ntilde
 // join: when given, colptr is produced on the side stream and the row pass waits for it.
 cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const int64_t* colptr,
                     int32_t* rowidx_out, float* val_out, cudaEvent_t join) {
-  c->jw.nb_accum = dlk::jau_accum_blocks(c->p, c->n, c->cfg_acc_mult);
+  c->jw.det = c->deterministic && dlk::jau_det_supported(c->p, c->n, s, Y, D);
+  c->jw.nb_accum = c->jw.det ? (int)dlk::jau_det_ranges(m, c->p, c->n, s)
+                             : dlk::jau_accum_blocks(c->p, c->n, c->cfg_acc_mult);
   c->jw.nb_row = dlk::jau_row_blocks(c->cfg_row_per_sm);
   const int nt = group_size(c);
   const int ngroups = (c->n + nt - 1) / nt;
@@ -390,7 +407,7 @@ cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const
                                     cudaMemcpyDeviceToDevice, c->st)) != cudaSuccess)
     return e0;
   // (groups need the float4 passes; the entry points check this before enqueuing)
-  c->jau_kernels = ngroups == 1 ? dlk::jau_launches(c->p, Y, D) : 4 * ngroups + 1;
+  c->jau_kernels = (dlk::jau_launches(c->p, Y, D) - 1) * ngroups + 1;
   mark(c, 4);
   cudaError_t e = cudaSuccess;
   for (int a0 = 0; a0 < c->n; a0 += nt) {
@@ -442,7 +459,7 @@ cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const
 // Whether a call with host buffers overlaps the upload of Y with the first
 // iteration's coding pass: plain FP32 tensor-core path, at least kChunks x 128 signals.
 bool staged_ok(dl_ctx* c, const float* dY, const float* dD, int64_t m) {
-  return !c->prop && !lp_ok(c) && tc_ok(c, dY, dD) && m >= (int64_t)dl_ctx::kChunks * 128;
+  return !has_prop(c) && !lp_ok(c) && tc_ok(c, dY, dD) && m >= (int64_t)dl_ctx::kChunks * 128;
 }
 
 // Piece q of the staged coding pass covers signals [off[q], off[q+1]).  Each
@@ -601,9 +618,9 @@ int host_call_graphed(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int
   // (the caller has matched the host buffers against hkey)
   if (c->gkey[0] != (const void*)c->hY)
     c->gkey_m = -1;  // a later call with device buffers starts from a fresh key
-  const int64_t sig[10] = {m, s, c->rule, c->ntilde, c->cfg_omp_warps, c->cfg_acc_mult,
+  const int64_t sig[11] = {m, s, c->rule, c->ntilde, c->cfg_omp_warps, c->cfg_acc_mult,
                            c->cfg_row_per_sm, c->cfg_corr_tc, (int64_t)(intptr_t)c->st,
-                           (int64_t)(intptr_t)c->prop};
+                           (int64_t)(intptr_t)c->prop + (c->prop_corr ? 1 : 0), c->deterministic};
   if (memcmp(sig, c->hsig, sizeof(sig)) != 0) {
     if (c->hgexec) cudaGraphExecDestroy(c->hgexec);
     c->hgexec = nullptr;
@@ -675,10 +692,15 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
   if (const char* v = getenv("DL_OMP_TM")) c->cfg_omp_tm = atoi(v);  // 0 (off), 4, 5 or 6
   const size_t mm = (size_t)m_max;
   c->jw.nb_accum = dlk::jau_accum_blocks_max(p, n);
+  // the deterministic pass A writes one slice of U and one energy partial per range of signals
+  const bool det = dlk::jau_det_supported(p, n, s_max, nullptr, nullptr);
+  const int64_t nbd = det ? dlk::jau_det_ranges(m_max, p, n, s_max) : 0;
+  if (nbd > c->jw.nb_accum) c->jw.nb_accum = (int)nbd;
   c->jw.nb_row = dlk::jau_row_blocks_max();
   const size_t ulen = dlk::jau_ulen(p, n);
   size_t nslices = dlk::jau_accum_smem(p, n) > 0 ? (size_t)c->jw.nb_accum : 1;
   if (nslices < (size_t)dlk::kUCopies) nslices = dlk::kUCopies;
+  if (nslices < (size_t)nbd) nslices = (size_t)nbd;
   bool ok = dalloc(&c->G, (size_t)n * n) && dalloc(&c->A0, mm * c->lda) &&
             dalloc(&c->sidx, mm * s_max) && dalloc(&c->sval, mm * s_max) &&
             dalloc(&c->scnt, mm) && dalloc(&c->bsum, (size_t)dlk::scan_blocks(m_max) + 1) &&
@@ -756,6 +778,14 @@ int dl_set_group_size(dl_ctx* c, int ntilde) {
   if (!c || ntilde < 1 || ntilde > c->n) return DL_EINVAL;
   if (ntilde != c->ntilde) c->gkey_m = -1;  // captured iterations no longer apply
   c->ntilde = ntilde;
+  return DL_OK;
+}
+
+int dl_set_deterministic(dl_ctx* c, int on) {
+  if (!c) return DL_EINVAL;
+  on = on ? 1 : 0;
+  if (on != c->deterministic) c->gkey_m = -1;  // captured iterations no longer apply
+  c->deterministic = on;
   return DL_OK;
 }
 
@@ -1008,7 +1038,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
   if (c->prop) DL_CHECK(dlk::to_lowp(dlk::LP_BF16, dY, m, c->p, c->Ybf, nullptr, c->st));
   c->launches += (lp_ok(c) ? 1 : 0) + (c->prop ? 1 : 0);  // the per-call conversions of Y
   for (int it = 0; it < iters; ++it) {
-    const bool learned = c->prop && (c->prop_counter % c->prop_full_every) != 0;
+    const bool learned = has_prop(c) && (c->prop_counter % c->prop_full_every) != 0;
     c->learned_now = learned;
     cudaGraphExec_t& gx = learned ? c->gexec_learned : c->gexec;
     int& seen = learned ? c->gkey_seen_l : c->gkey_seen;
@@ -1049,7 +1079,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
       seen++;
     }
     c->launches += kernels_per_iteration(c, learned);
-    if (c->prop) c->prop_counter++;
+    if (has_prop(c)) c->prop_counter++;
     c->learned_now = false;
     if (c->prof) {
       DL_CHECK(cudaStreamSynchronize(c->st));
@@ -1612,27 +1642,31 @@ extern "C" int dl_proposer_forward(dl_proposer* P, const float* Y, int64_t m, fl
   return DL_OK;
 }
 
-extern "C" int dl_attach_proposer(dl_ctx* c, dl_proposer* P, int K, int full_every, double tol) {
+// Attach the learned proposer P, or (P null, corr) the network-free one.
+static int attach_proposer(dl_ctx* c, dl_proposer* P, bool corr, int K, int full_every, double tol) {
   if (!c) return DL_EINVAL;
   DevGuard g(c->dev);
-  if (!P) {
+  if (!P && !corr) {
     c->prop = nullptr;
+    c->prop_corr = false;
     return DL_OK;
   }
-  if (P->p != c->p || P->n != c->n || K < c->s_max || K > 32 || full_every < 1 || tol < 0 ||
-      !dlk::omp_restricted_supported(c->n, c->s_max, K))
+  if ((P && (P->p != c->p || P->n != c->n)) || K < c->s_max || K > 32 || full_every < 1 ||
+      tol < 0 || !dlk::omp_restricted_supported(c->n, c->s_max, K))
     return DL_EINVAL;
   const size_t mm = (size_t)c->m_max;
   if (!c->rr_ref) {
     if (!dalloc(&c->rr_ref, mm) || !dalloc(&c->rr_L, mm) || !dalloc(&c->fb_list, mm) ||
-        !dalloc(&c->fb_count, 1) || !dalloc((uint8_t**)&c->Ybf, mm * P->pk * 2))
+        !dalloc(&c->fb_count, 1))
       return DL_ENOMEM;
     DL_CHECK(cudaMemset(c->fb_count, 0, sizeof(int)));
   }
+  if (P && !c->Ybf && !dalloc((uint8_t**)&c->Ybf, mm * P->pk * 2)) return DL_ENOMEM;
   if (c->cand) cudaFree(c->cand);
   c->cand = nullptr;
   if (!dalloc(&c->cand, mm * K)) return DL_ENOMEM;
   c->prop = P;
+  c->prop_corr = corr && !P;
   c->prop_K = K;
   c->prop_full_every = full_every;
   c->prop_tol2 = (float)((1.0 + tol) * (1.0 + tol));
@@ -1644,6 +1678,14 @@ extern "C" int dl_attach_proposer(dl_ctx* c, dl_proposer* P, int K, int full_eve
   c->gexec = nullptr;
   c->gkey_seen = 0;
   return DL_OK;
+}
+
+extern "C" int dl_attach_proposer(dl_ctx* c, dl_proposer* P, int K, int full_every, double tol) {
+  return attach_proposer(c, P, false, K, full_every, tol);
+}
+
+extern "C" int dl_attach_correlation_proposer(dl_ctx* c, int K, int full_every, double tol) {
+  return attach_proposer(c, nullptr, true, K, full_every, tol);
 }
 
 extern "C" int64_t dl_last_fallbacks(dl_ctx* c) {

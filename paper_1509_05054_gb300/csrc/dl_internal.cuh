@@ -105,6 +105,9 @@ cudaError_t mlp_colsum(const void* in, int64_t R, int C, float* out, cudaStream_
 cudaError_t mlp_adam(float* w, const float* g, float* m, float* v, int64_t count, float lr, int t,
                      void* wbf, cudaStream_t st);
 cudaError_t mlp_topk(const void* z, int64_t m, int n, int K, int32_t* cand, cudaStream_t st);
+// The K largest |A[i][j]| of each row (row i at A + i * lda), indices ascending.
+cudaError_t topk_abs(const float* A, int64_t lda, int64_t m, int n, int K, int32_t* cand,
+                     cudaStream_t st);
 
 // Re-solve (k_resolve.cu) of the listed signals with the FP64 Batch-OMP's decisions and
 // coefficients (FP64 residual and Cholesky factor, FP32 correlations with an exact check of
@@ -142,6 +145,9 @@ struct JauWork {
   const int32_t* pcnt = nullptr;
   const int* pvalid = nullptr;
   const float* D0 = nullptr;
+  // pass A in its deterministic form (jau_det_supported): nb_accum ranges of signals,
+  // one slice of Upart each
+  bool det = false;
 };
 // Grid sizes: mult selects 1x/2x the base CTA count of the accumulation pass
 // and 2/4/8 CTAs per SM for the row pass; *_max give the partial-buffer sizes.
@@ -158,6 +164,10 @@ int jau_row_blocks_max();
 size_t jau_accum_smem(int p, int n);
 // float4 passes (p % 4 == 0, Y and D 16-byte aligned); kernel launches of the JAU passes.
 bool jau_vec4(int p, const float* Y, const float* D);
+// Pass A with a fixed summation order, bitwise reproducible (float4 rows, p <= 128,
+// n <= 1024, s <= 16, a range of signals per CTA in shared memory); its CTA count.
+bool jau_det_supported(int p, int n, int s, const float* Y, const float* D);
+int64_t jau_det_ranges(int64_t m, int p, int n, int s);
 int jau_launches(int p, const float* Y, const float* D);
 
 cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int n, int s,

@@ -281,6 +281,247 @@ __global__ void __launch_bounds__(ACC4_THREADS, 4) accum4_kernel(
   }
 }
 
+// ---- Pass A, deterministic form ---------------------------------------------
+// U_j = sum_{i in I_j} x_{j,i} e_i and r_j = sum x_{j,i}^2 summed in an order
+// fixed by the signal and slot indices, so that every run gives the same bits
+// (float4 rows, p <= 128, n <= 1024, s <= 16).  CTA b owns a contiguous range
+// of signals (at most DET_R):
+//   1. eight lanes per signal form e_i into shared memory (as accum4_kernel),
+//      and the (atom, x) pair of every accumulated slot, numbered k = signal x
+//      s + slot within the range; counts per atom;
+//   2. the pairs are bucketed by atom (exclusive scan of the counts, then
+//      positions inside each bucket from shared-memory counters);
+//   3. each bucket is put in ascending k order (ranks by comparison, one warp
+//      per bucket), which fixes the order whatever the counters handed out;
+//   4. one warp per atom sums x e_i and x^2 over its bucket in that order and
+//      writes the range's U_j and r_j as slice b (zeros for atoms the range
+//      does not use).
+// The slices are then summed in slice order (reduce4_kernel).
+constexpr int DET_THREADS = 1024;
+
+int det_range(int p, int n, int s) {  // signals per CTA within 200 KB of shared memory
+  const size_t per = sizeof(float) * (size_t)p + (size_t)s * (4 + 4 + 4 + 4);
+  const size_t fixed = sizeof(int) * (3 * (size_t)n + 1) + 64;
+  const size_t cap = 200u * 1024u;
+  return fixed >= cap ? 0 : (int)((cap - fixed) / per);
+}
+size_t det_smem_bytes(int p, int n, int s, int R) {
+  return sizeof(float) * (size_t)R * p + (size_t)R * s * (4 + 4 + 4 + 4) +
+         sizeof(int) * (3 * (size_t)n + 1) + 64;
+}
+
+template <int RV, int SMAX, bool NS>
+__global__ void __launch_bounds__(DET_THREADS, 1) accum_det_kernel(
+    const float* __restrict__ Y, int p, int64_t m, int64_t R, const float* __restrict__ D, int n,
+    int s, const int32_t* __restrict__ idx, const float* __restrict__ val,
+    const int32_t* __restrict__ cnt, float* __restrict__ Upart, size_t len,
+    double* __restrict__ epart, int* __restrict__ err, int a0, int a1, int energies,
+    const float* __restrict__ D0, const int32_t* __restrict__ pidx, const float* __restrict__ pval,
+    const int32_t* __restrict__ pcnt, const int* __restrict__ pvalid, int moved) {
+  extern __shared__ float dsh[];
+  __shared__ double red[DET_THREADS / 32];
+  const int64_t lo = (int64_t)blockIdx.x * R;
+  const int64_t hi = lo + R < m ? lo + R : m;
+  const int nr = (int)(hi > lo ? hi - lo : 0);  // signals of this range
+  const int npair = nr * s;
+  float* Es = dsh;                                   // [R][p]
+  int* pa = (int*)(Es + (size_t)R * p);              // [R s] atom of pair k (-1: none)
+  float* px = (float*)(pa + (size_t)R * s);          // [R s] x of pair k
+  int* bk = (int*)(px + (size_t)R * s);              // [R s] bucketed: k
+  float* bx = (float*)(bk + (size_t)R * s);          // [R s] bucketed: x
+  int* cntA = (int*)(bx + (size_t)R * s);            // [n] pairs per atom
+  int* off = cntA + n;                               // [n + 1] bucket starts
+  int* fill = off + n + 1;                           // [n]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane & 7, gbase = lane & ~7;
+  const int pv = p >> 2;
+  for (int a = threadIdx.x; a < n; a += DET_THREADS) {
+    cntA[a] = 0;
+    fill[a] = 0;
+  }
+  __syncthreads();
+  const float4* __restrict__ Y4 = (const float4*)Y;
+  const float4* __restrict__ D4 = (const float4*)(NS ? D0 : D);
+  const float4* __restrict__ Dc4 = (const float4*)D;
+  const bool have_prev = NS && *pvalid != 0;
+  const int32_t* __restrict__ sidx = have_prev ? pidx : idx;
+  const float* __restrict__ sval = have_prev ? pval : val;
+  const int32_t* __restrict__ scnt = have_prev ? pcnt : cnt;
+  float ee = 0.f, yy = 0.f;
+  // ---- 1. errors and pairs
+  for (int sl = threadIdx.x >> 3; sl < ((nr + 3) & ~3); sl += DET_THREADS / 8) {
+    const int64_t i = lo + sl;
+    const bool live = sl < nr;
+    float4 e[RV];
+#pragma unroll
+    for (int q = 0; q < RV; ++q) {
+      const int v = g + 8 * q;
+      e[q] = (live && v < pv) ? Y4[i * pv + v] : make_float4(0.f, 0.f, 0.f, 0.f);
+      yy = f4_dot(e[q], e[q], yy);
+    }
+    const int c = live ? cnt[i] : 0;
+    const int j0 = (g < c) ? idx[i * s + g] : 0;
+    const float x0 = (g < c) ? val[i * s + g] : 0.f;
+    const int j1 = (SMAX > 8 && g + 8 < c) ? idx[i * s + g + 8] : 0;
+    const float x1 = (SMAX > 8 && g + 8 < c) ? val[i * s + g + 8] : 0.f;
+    const int cmax = __reduce_max_sync(FULL, (unsigned)c);
+#pragma unroll
+    for (int t = 0; t < SMAX; ++t) {
+      if (t >= cmax) break;
+      const int jj = __shfl_sync(FULL, t < 8 ? j0 : j1, gbase + (t & 7));
+      const float xx = __shfl_sync(FULL, t < 8 ? x0 : x1, gbase + (t & 7));
+      if (t < c) {
+#pragma unroll
+        for (int q = 0; q < RV; ++q) {
+          const int v = g + 8 * q;
+          if (v < pv) e[q] = f4_fma(-xx, __ldg(D4 + (size_t)jj * pv + v), e[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RV; ++q) ee = f4_dot(e[q], e[q], ee);
+    int sc = c, sj0 = j0, sj1 = j1;
+    float sx0 = x0, sx1 = x1;
+    if (NS) {
+      sc = live ? scnt[i] : 0;
+      sj0 = (g < sc) ? sidx[i * s + g] : 0;
+      sx0 = (g < sc) ? sval[i * s + g] : 0.f;
+      sj1 = (SMAX > 8 && g + 8 < sc) ? sidx[i * s + g + 8] : 0;
+      sx1 = (SMAX > 8 && g + 8 < sc) ? sval[i * s + g + 8] : 0.f;
+      const int scmax = __reduce_max_sync(FULL, (unsigned)sc);
+      if (moved) {  // e += (D0 - D) xp for the atoms earlier groups have moved
+#pragma unroll
+        for (int t = 0; t < SMAX; ++t) {
+          if (t >= scmax) break;
+          const int jj = __shfl_sync(FULL, t < 8 ? sj0 : sj1, gbase + (t & 7));
+          const float xx = __shfl_sync(FULL, t < 8 ? sx0 : sx1, gbase + (t & 7));
+          if (t < sc) {
+#pragma unroll
+            for (int q = 0; q < RV; ++q) {
+              const int v = g + 8 * q;
+              if (v < pv) {
+                e[q] = f4_fma(xx, __ldg(D4 + (size_t)jj * pv + v), e[q]);
+                e[q] = f4_fma(-xx, __ldg(Dc4 + (size_t)jj * pv + v), e[q]);
+              }
+            }
+          }
+        }
+      }
+    }
+    if (live) {
+#pragma unroll
+      for (int q = 0; q < RV; ++q) {
+        const int v = g + 8 * q;
+        if (v < pv) *(float4*)(Es + (size_t)sl * p + 4 * v) = e[q];
+      }
+      if (g < s) {
+        const bool ok = g < sc && sj0 >= a0 && sj0 < a1;
+        pa[sl * s + g] = ok ? sj0 : -1;
+        px[sl * s + g] = sx0;
+        if (ok) atomicAdd(&cntA[sj0], 1);
+      }
+      if (SMAX > 8 && g + 8 < s) {
+        const bool ok = g + 8 < sc && sj1 >= a0 && sj1 < a1;
+        pa[sl * s + g + 8] = ok ? sj1 : -1;
+        px[sl * s + g + 8] = sx1;
+        if (ok) atomicAdd(&cntA[sj1], 1);
+      }
+    }
+  }
+  if (!isfinite(ee) || !isfinite(yy)) atomicOr(err, ERR_NONFINITE);
+  __syncthreads();
+  // ---- 2. buckets: exclusive scan of the counts (n <= 1024), then positions
+  {
+    const int a = threadIdx.x;
+    const int v = a < n ? cntA[a] : 0;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc += t;
+    }
+    __shared__ int wsum[32];
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      int x = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += t;
+      }
+      wsum[lane] = x;
+    }
+    __syncthreads();
+    const int ex = (warp > 0 ? wsum[warp - 1] : 0) + inc - v;
+    if (a < n) off[a] = ex;
+    if (a == n - 1) off[n] = ex + v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < npair; k += DET_THREADS) {
+    const int a = pa[k];
+    if (a >= 0) {
+      const int pos = off[a] + atomicAdd(&fill[a], 1);
+      bk[pos] = k;
+      bx[pos] = px[k];
+    }
+  }
+  __syncthreads();
+  // ---- 3. and 4. one warp per atom: order the bucket by k, then sum over it
+  float* out = Upart + (size_t)blockIdx.x * len;
+  const size_t np = (size_t)n * p;
+  for (int a = warp; a < n; a += DET_THREADS / 32) {
+    const int b0 = off[a], L = off[a + 1] - b0;
+    for (int q0 = 0; q0 < L; q0 += 32) {  // rank of each pair by k among the bucket's pairs
+      const int q = q0 + lane;
+      const int kq = q < L ? bk[b0 + q] : 0x7fffffff;
+      const float xq = q < L ? bx[b0 + q] : 0.f;
+      int rank = 0;
+      for (int r0 = 0; r0 < L; r0 += 32) {
+        const int kr = r0 + lane < L ? bk[b0 + r0 + lane] : 0x7fffffff;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) rank += __shfl_sync(FULL, kr, j) < kq ? 1 : 0;
+      }
+      __syncwarp();
+      if (q < L) {  // park at the final position in the pair arrays (free after step 2)
+        pa[b0 + rank] = kq;
+        px[b0 + rank] = xq;
+      }
+      __syncwarp();
+    }
+    __syncwarp();
+    constexpr int RU = RV;  // rows lane + 32 u of U_j, u < ceil(p / 32) <= RV
+    float ac[RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) ac[u] = 0.f;
+    float rx = 0.f;
+    for (int q = 0; q < L; ++q) {
+      const int k = pa[b0 + q];
+      const float xx = px[b0 + q];
+      const float* er = Es + (size_t)(k / s) * p;
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        const int r = lane + 32 * u;
+        if (r < p) ac[u] = fmaf(xx, er[r], ac[u]);
+      }
+      rx = fmaf(xx, xx, rx);
+    }
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const int r = lane + 32 * u;
+      if (r < p) out[(size_t)a * p + r] = ac[u];
+    }
+    if (lane == 0) out[np + a] = rx;
+  }
+  for (size_t q = np + n + threadIdx.x; q < len; q += DET_THREADS) out[q] = 0.f;
+  const double see = block_sum_d((double)ee, red);
+  const double syy = block_sum_d((double)yy, red);
+  if (threadIdx.x == 0 && energies) {
+    epart[2 * blockIdx.x] = see;
+    epart[2 * blockIdx.x + 1] = syy;
+  }
+}
+
 // Pass B, float4 form: e = y - D x; x_t' = e.d'_{j_t} + c_{j_t} x_t for all t
 // (independent dot products), then y - D' x'.  GROUP: only slots whose atom is
 // in [a0, a1) are updated; the others keep x_t and their current atom in the
@@ -308,6 +549,16 @@ __global__ void __launch_bounds__(ROW_THREADS, 4) rows4_kernel(
   for (int64_t k = 0; k < trips; ++k) {
     const int64_t i = g0 + k * groups;
     const bool live = i < m;
+    {  // warm L2 with the next trip's signal: its samples, slots, count and column start
+      const int64_t inx = i + groups;
+      if (inx < m) {
+        const char* a = nullptr;
+        if (g < 2 * RV && 128 * g < 4 * p) a = (const char*)(Y + inx * p) + 128 * g;
+        else if (g == 6) a = (const char*)(idx + inx * s);
+        else if (g == 7) a = (const char*)(val + inx * s);
+        if (a) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+      }
+    }
     float4 y[RV], e[RV];
 #pragma unroll
     for (int q = 0; q < RV; ++q) {
@@ -780,9 +1031,65 @@ int jau_launches(int p, const float* Y, const float* D) {
 int jau_row_blocks(int per_sm) { return (per_sm == 2 || per_sm == 8 ? per_sm : 4) * num_sms(); }
 int jau_row_blocks_max() { return 8 * num_sms(); }
 
+bool jau_det_supported(int p, int n, int s, const float* Y, const float* D) {
+  return (Y || D ? jau_vec4(p, Y, D) : p % 4 == 0) && p <= 128 && n <= 1024 && s <= 16 &&
+         det_range(p, n, s) >= 64;
+}
+// CTAs of the deterministic pass A for m signals: at least one per SM, each range
+// within the shared-memory budget
+int64_t jau_det_ranges(int64_t m, int p, int n, int s) {
+  const int64_t R = det_range(p, n, s);
+  int64_t nb = R > 0 ? (m + R - 1) / R : 1;
+  const int64_t floor_nb = 2 * (int64_t)num_sms();
+  if (nb < floor_nb) nb = floor_nb;
+  return nb;
+}
+
+cudaError_t jau_accumulate_det(const float* Y, int p, int64_t m, const float* D, int n, int s,
+                               const int32_t* idx, const float* val, const int32_t* cnt,
+                               const JauWork& w, int* err, cudaStream_t st) {
+  const int nb = w.nb_accum;
+  const int64_t R = (m + nb - 1) / nb;
+  const size_t len = jau_ulen(p, n);
+  const size_t smem = det_smem_bytes(p, n, s, (int)R);
+  const int a0 = w.a0, a1 = w.a1 > 0 ? w.a1 : n;
+  cudaError_t e = cudaSuccess;
+#define DL_ACCD(RV, SM)                                                                        \
+  do {                                                                                         \
+    if (w.nsgk) {                                                                              \
+      e = cudaFuncSetAttribute(accum_det_kernel<RV, SM, true>,                                 \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
+      if (e == cudaSuccess)                                                                    \
+        accum_det_kernel<RV, SM, true><<<nb, DET_THREADS, smem, st>>>(                         \
+            Y, p, m, R, D, n, s, idx, val, cnt, w.Upart, len, w.epart_a, err, a0, a1,          \
+            (int)w.energies, w.D0, w.pidx, w.pval, w.pcnt, w.pvalid, w.a0 > 0 ? 1 : 0);        \
+    } else {                                                                                   \
+      e = cudaFuncSetAttribute(accum_det_kernel<RV, SM, false>,                                \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);        \
+      if (e == cudaSuccess)                                                                    \
+        accum_det_kernel<RV, SM, false><<<nb, DET_THREADS, smem, st>>>(                        \
+            Y, p, m, R, D, n, s, idx, val, cnt, w.Upart, len, w.epart_a, err, a0, a1,          \
+            (int)w.energies, D, idx, val, cnt, nullptr, 0);                                    \
+    }                                                                                          \
+  } while (0)
+#define DL_ACCD_S(RV) \
+  if (s <= 8) DL_ACCD(RV, 8); else DL_ACCD(RV, 16)
+  if (p <= 32) { DL_ACCD_S(1); }
+  else if (p <= 64) { DL_ACCD_S(2); }
+  else if (p <= 96) { DL_ACCD_S(3); }
+  else { DL_ACCD_S(4); }
+#undef DL_ACCD_S
+#undef DL_ACCD
+  if (e != cudaSuccess) return e;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return reduce_slices(w.Upart, nb, (int)len, w.U, st);
+}
+
 cudaError_t jau_accumulate(const float* Y, int p, int64_t m, const float* D, int n, int s,
                            const int32_t* idx, const float* val, const int32_t* cnt,
                            const JauWork& w, int* err, cudaStream_t st) {
+  if (w.det && jau_det_supported(p, n, s, Y, D))
+    return jau_accumulate_det(Y, p, m, D, n, s, idx, val, cnt, w, err, st);
   if (jau_vec4(p, Y, D)) {
     const size_t len = jau_ulen(p, n);
     cudaError_t e = cudaMemsetAsync(w.Upart, 0, sizeof(float) * len * kUCopies, st);

@@ -317,9 +317,16 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
   if (wbf) wbf[e] = __float2bfloat16_rn(ww);
 }
 
-// Top-K of each row of n logits (one warp per row), indices ascending.
-template <int NT>
-__global__ void topk_kernel(const __nv_bfloat16* __restrict__ z, int64_t m, int n, int K,
+__device__ __forceinline__ float topk_value(const __nv_bfloat16* z, int64_t o) {
+  return __bfloat162float(z[o]);
+}
+__device__ __forceinline__ float topk_value(const float* z, int64_t o) { return fabsf(z[o]); }
+
+// Top-K of each row of n values (one warp per row, row i at z + i * ld), indices
+// ascending: the proposer's logits (BF16), or |correlations| (FP32 rows of
+// D^T y, the network-free proposer).
+template <int NT, typename T>
+__global__ void topk_kernel(const T* __restrict__ z, int64_t ld, int64_t m, int n, int K,
                             int32_t* __restrict__ cand) {
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -328,7 +335,7 @@ __global__ void topk_kernel(const __nv_bfloat16* __restrict__ z, int64_t m, int 
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
     const int j = 32 * t + lane;
-    v[t] = j < n ? __bfloat162float(z[i * n + j]) : -INFINITY;
+    v[t] = j < n ? topk_value(z, i * ld + j) : -INFINITY;
   }
   int mine = -1;  // lane k < K: the k-th pick
   for (int k = 0; k < K; ++k) {
@@ -447,10 +454,21 @@ cudaError_t mlp_topk(const void* z, int64_t m, int n, int K, int32_t* cand, cuda
   if (m <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((m + 7) / 8);
   const __nv_bfloat16* zz = (const __nv_bfloat16*)z;
-  if (n <= 128) topk_kernel<4><<<blocks, 256, 0, st>>>(zz, m, n, K, cand);
-  else if (n <= 256) topk_kernel<8><<<blocks, 256, 0, st>>>(zz, m, n, K, cand);
-  else if (n <= 512) topk_kernel<16><<<blocks, 256, 0, st>>>(zz, m, n, K, cand);
-  else topk_kernel<32><<<blocks, 256, 0, st>>>(zz, m, n, K, cand);
+  if (n <= 128) topk_kernel<4><<<blocks, 256, 0, st>>>(zz, n, m, n, K, cand);
+  else if (n <= 256) topk_kernel<8><<<blocks, 256, 0, st>>>(zz, n, m, n, K, cand);
+  else if (n <= 512) topk_kernel<16><<<blocks, 256, 0, st>>>(zz, n, m, n, K, cand);
+  else topk_kernel<32><<<blocks, 256, 0, st>>>(zz, n, m, n, K, cand);
+  return cudaGetLastError();
+}
+
+cudaError_t topk_abs(const float* A, int64_t lda, int64_t m, int n, int K, int32_t* cand,
+                     cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((m + 7) / 8);
+  if (n <= 128) topk_kernel<4><<<blocks, 256, 0, st>>>(A, lda, m, n, K, cand);
+  else if (n <= 256) topk_kernel<8><<<blocks, 256, 0, st>>>(A, lda, m, n, K, cand);
+  else if (n <= 512) topk_kernel<16><<<blocks, 256, 0, st>>>(A, lda, m, n, K, cand);
+  else topk_kernel<32><<<blocks, 256, 0, st>>>(A, lda, m, n, K, cand);
   return cudaGetLastError();
 }
 

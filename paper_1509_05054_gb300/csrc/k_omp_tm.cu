@@ -53,24 +53,48 @@ __device__ __forceinline__ uint32_t tm_ld1(uint32_t taddr) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
   return r;
 }
-template <int K>
-__device__ __forceinline__ void tm_wait_ld(uint32_t (&r)[K]) {
-  static_assert(K <= 8, "tied registers");
-  if constexpr (K == 0) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-  } else {
-    uint32_t t[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) t[j] = j < K ? r[j < K ? j : 0] : 0u;
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]),
-                   "+r"(t[6]), "+r"(t[7])
-                 :
-                 : "memory");
-#pragma unroll
-    for (int j = 0; j < K; ++j) r[j] = t[j];
+// Completion of the single-column loads of the first K entries of r (K <= 7),
+// with exactly those registers tied to the wait.
+#define DL_TMW_OPS1 "+r"(r[0])
+#define DL_TMW_OPS2 DL_TMW_OPS1, "+r"(r[1])
+#define DL_TMW_OPS3 DL_TMW_OPS2, "+r"(r[2])
+#define DL_TMW_OPS4 DL_TMW_OPS3, "+r"(r[3])
+#define DL_TMW_OPS5 DL_TMW_OPS4, "+r"(r[4])
+#define DL_TMW_OPS6 DL_TMW_OPS5, "+r"(r[5])
+#define DL_TMW_OPS7 DL_TMW_OPS6, "+r"(r[6])
+template <int K, int N>
+__device__ __forceinline__ void tm_wait_ld(uint32_t (&r)[N]) {
+  static_assert(K <= N && K <= 7, "tied registers");
+  if constexpr (K == 0) asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  else if constexpr (K == 1) asm volatile("tcgen05.wait::ld.sync.aligned;" : DL_TMW_OPS1 :: "memory");
+  else if constexpr (K == 2) asm volatile("tcgen05.wait::ld.sync.aligned;" : DL_TMW_OPS2 :: "memory");
+  else if constexpr (K == 3) asm volatile("tcgen05.wait::ld.sync.aligned;" : DL_TMW_OPS3 :: "memory");
+  else if constexpr (K == 4) asm volatile("tcgen05.wait::ld.sync.aligned;" : DL_TMW_OPS4 :: "memory");
+  else if constexpr (K == 5) asm volatile("tcgen05.wait::ld.sync.aligned;" : DL_TMW_OPS5 :: "memory");
+  else if constexpr (K == 6) asm volatile("tcgen05.wait::ld.sync.aligned;" : DL_TMW_OPS6 :: "memory");
+  else asm volatile("tcgen05.wait::ld.sync.aligned;" : DL_TMW_OPS7 :: "memory");
+}
+// The same with K known after unrolling (a switch the compiler folds).
+template <int N>
+__device__ __forceinline__ void tm_wait_ld_k(int k, uint32_t (&r)[N]) {
+  switch (k) {
+    case 0: tm_wait_ld<0>(r); break;
+    case 1: tm_wait_ld<1 <= N ? 1 : 0>(r); break;
+    case 2: tm_wait_ld<2 <= N ? 2 : 0>(r); break;
+    case 3: tm_wait_ld<3 <= N ? 3 : 0>(r); break;
+    case 4: tm_wait_ld<4 <= N ? 4 : 0>(r); break;
+    case 5: tm_wait_ld<5 <= N ? 5 : 0>(r); break;
+    case 6: tm_wait_ld<6 <= N ? 6 : 0>(r); break;
+    default: tm_wait_ld<7 <= N ? 7 : 0>(r); break;
   }
 }
+#undef DL_TMW_OPS7
+#undef DL_TMW_OPS6
+#undef DL_TMW_OPS5
+#undef DL_TMW_OPS4
+#undef DL_TMW_OPS3
+#undef DL_TMW_OPS2
+#undef DL_TMW_OPS1
 __device__ __forceinline__ void tm_st16(uint32_t taddr, const float2 (&v)[8]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
@@ -190,15 +214,14 @@ __device__ __forceinline__ void omp_one_tm(
     // shared memory (read directly from the owning lane's slot)
     float ul[NPHI];
     {
-      uint32_t tv[NPHI < 8 ? NPHI : 8];
-      constexpr int NL = NPHI < 8 ? NPHI : 8;
-#pragma unroll
-      for (int q = 0; q < NL; ++q) tv[q] = 0u;
+      constexpr int NL = NPHI < 7 ? NPHI : 7;
+      const int KL = step < NTM ? step : NTM;  // single columns to load
+      uint32_t tv[NL];
       if (step > 0) tm_wait_st();  // u_{step-1} was just stored
 #pragma unroll
       for (int q = 0; q < NL; ++q)
-        if (q < step && q < NTM) tv[q] = tm_ld1(tcol + 16 * q + tsel);
-      if (step > 0) tm_wait_ld<NL>(tv);
+        if (q < KL) tv[q] = tm_ld1(tcol + 16 * q + tsel);
+      if (KL > 0) tm_wait_ld_k(KL < NL ? KL : NL, tv);
 #pragma unroll
       for (int q = 0; q < NPHI; ++q) {
         ul[q] = 0.f;

@@ -66,6 +66,7 @@ def load(build_if_missing: bool = True):
         lib.dl_kernel_launches.restype = i64
         lib.dl_set_profiling.argtypes = [P, i32]
         lib.dl_set_group_size.argtypes = [P, i32]
+        lib.dl_set_deterministic.argtypes = [P, i32]
         lib.dl_set_update_rule.argtypes = [P, i32]
         lib.dl_check_bounded_wait.argtypes = [P]
         lib.dl_check_bounded_wait.restype = i32
@@ -95,6 +96,7 @@ def load(build_if_missing: bool = True):
         lib.dl_proposer_train.argtypes = [P, P, i64, P, i32, P, i64, ctypes.c_float, P]
         lib.dl_proposer_forward.argtypes = [P, P, i64, P, P, i32]
         lib.dl_attach_proposer.argtypes = [P, P, i32, i32, ctypes.c_double]
+        lib.dl_attach_correlation_proposer.argtypes = [P, i32, i32, ctypes.c_double]
         lib.dl_last_fallbacks.argtypes = [P]
         lib.dl_last_fallbacks.restype = i64
         for name in ("dl_autotune", "dl_get_config", "dl_batch_create", "dl_batch_iterate",
@@ -104,7 +106,7 @@ def load(build_if_missing: bool = True):
             getattr(lib, name).restype = i32
         for name in ("dl_init", "dl_set_stream", "dl_destroy", "omp_code", "jau_update", "dl_iterate",
                      "dl_sync", "dl_set_profiling", "dl_phase_times", "dl_gram", "dl_correlate",
-                     "dl_uses_tensor_cores", "dl_correlate_noalloc", "dl_correlate_noalloc_status", "dl_fp32_probe",
+                     "dl_uses_tensor_cores", "dl_correlate_noalloc", "dl_correlate_noalloc_status", "dl_fp32_probe", "dl_set_deterministic", "dl_attach_correlation_proposer",
                      "dl_set_group_size",
                      "dl_set_update_rule", "dl_batch_set_update_rule", "dl_batch_set_group_size"):
             getattr(lib, name).restype = i32
@@ -180,6 +182,10 @@ def dl_set_update_rule(ctx: int, rule: int) -> None:
 def dl_check_bounded_wait(ctx: int) -> int:
     """Status of the bounded-wait failure path (DL_ETIMEOUT when it works)."""
     return load().dl_check_bounded_wait(ctx)
+
+
+def dl_set_deterministic(ctx: int, on: bool = True) -> None:
+    _check(load().dl_set_deterministic(ctx, int(bool(on))), "dl_set_deterministic")
 
 
 def dl_set_group_size(ctx: int, ntilde: int) -> None:
@@ -350,6 +356,12 @@ def dl_proposer_forward(prop: int, Y, m: int, logits=None, cand=None, K: int = 1
 
 def dl_attach_proposer(ctx: int, prop, K: int = 16, full_every: int = 10, tol: float = 0.01) -> None:
     _check(load().dl_attach_proposer(ctx, prop, K, full_every, tol), "dl_attach_proposer")
+
+
+def dl_attach_correlation_proposer(ctx: int, K: int, full_every: int = 10, tol: float = 0.01) -> None:
+    """Candidates = the K largest |D^T y| (no network); otherwise as dl_attach_proposer."""
+    _check(load().dl_attach_correlation_proposer(ctx, K, full_every, tol),
+           "dl_attach_correlation_proposer")
 
 
 def dl_last_fallbacks(ctx: int) -> int:

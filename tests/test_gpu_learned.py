@@ -204,3 +204,59 @@ def test_learned_dl_restricted_omp_parity_and_equal_rmse(dl, trained):
     assert gap <= 0.01
     learned_iters = [k for k in range(iters) if k % 3 != 0]
     assert sum(fb[k] for k in learned_iters) <= sum(fb_fresh[k] for k in learned_iters)
+
+
+def test_correlation_proposer_parity_and_comparison(dl, trained):
+    """The network-free proposer (candidates = the 2s largest |D^T y|, the same
+    restricted OMP and fallback rule): restricted OMP equals the oracle's OMP on
+    that candidate sub-dictionary for the signals kept, the run ends within 1%
+    of plain's RMSE, and the fallbacks of both proposers are reported side by
+    side (what the trained network gains over the method without it)."""
+    n, s, iters, K = trained["n"], trained["s"], 6, 2 * trained["s"]
+    Y, D = trained["Ydl"], trained["Dw"]
+    m = len(Y)
+    Yd = torch.from_numpy(Y).cuda()
+    st = torch.cuda.Stream()
+
+    def run(mode):
+        ctx = dl.dl_init(64, n, m, s, dl.DL_FP32, st)
+        if mode == "learned":
+            dl.dl_attach_proposer(ctx, trained["prop"], K, 3, 0.01)
+        elif mode == "correlations":
+            dl.dl_attach_correlation_proposer(ctx, K, 3, 0.01)
+        Dd = torch.from_numpy(D.copy()).cuda()
+        cp = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+        ri = torch.zeros(m * s, dtype=torch.int32, device="cuda")
+        v = torch.zeros(m * s, device="cuda")
+        rm = np.zeros(2 * iters)
+        fbs = []
+        for k in range(iters):
+            Dk = Dd.cpu().numpy().astype(np.float64)
+            r2 = np.zeros(2)
+            dl.dl_iterate(ctx, Yd, m, Dd, s, 1, cp, ri, v, r2)
+            rm[2 * k: 2 * k + 2] = r2
+            fbs.append(dl.dl_last_fallbacks(ctx) if mode != "plain" else 0)
+            if mode == "correlations" and k == 1:   # an iteration on the proposed candidates
+                idx_g, _, cnt_g = csc_to_slots(cp.cpu().numpy(), ri.cpu().numpy(), v.cpu().numpy(), s)
+                agree, sample = 0, range(0, m, 97)
+                for i in sample:
+                    y64 = Y[i:i + 1].astype(np.float64)
+                    a = np.abs(Dk @ y64[0])
+                    c = np.sort(np.argsort(-a, kind="stable")[:K])
+                    ii, _, cc = oracle.omp(y64, Dk[c], s)       # restricted to the candidates
+                    jj, _, dd = oracle.omp(y64, Dk, s)          # full (fallback)
+                    got = set(idx_g[i, :cnt_g[i]])
+                    agree += got == set(c[ii[0, :cc[0]]]) or got == set(jj[0, :dd[0]])
+                assert agree >= 0.98 * len(sample), (agree, len(sample))
+        dl.dl_destroy(ctx)
+        return rm.reshape(iters, 2), fbs
+
+    r_plain, _ = run("plain")
+    r_corr, fb_corr = run("correlations")
+    r_learn, fb_learn = run("learned")
+    gap = r_corr[-1, 1] / r_plain[-1, 1] - 1
+    learned_iters = [k for k in range(iters) if k % 3 != 0]
+    print(f"fallbacks on proposed iterations: learned {[fb_learn[k] for k in learned_iters]}, "
+          f"|D^T y| {[fb_corr[k] for k in learned_iters]} of {m}; final rmse learned "
+          f"{r_learn[-1, 1]:.6f}, |D^T y| {r_corr[-1, 1]:.6f}, plain {r_plain[-1, 1]:.6f}")
+    assert gap <= 0.01

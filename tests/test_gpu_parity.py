@@ -602,3 +602,36 @@ def test_tensor_core_products_on_ragged_atom_blocks(dl, side, n, m, s):
     idx_o, val_o, cnt_o, gaps = oracle.omp(Y64, D64, s, return_gaps=True)
     same = assert_support_parity(idx_g, cnt_g, idx_o, cnt_o, gaps)
     np.testing.assert_allclose(val_g[same], val_o[same], rtol=0, atol=5e-4)
+
+
+@pytest.mark.parametrize("name,m,s,rule,ntilde", [("patch_n512", 20011, 8, 0, None),
+                                                  ("patch_n256", 9001, 6, 2, None),
+                                                  ("patch_n256", 5003, 6, 0, 100)])
+def test_iterations_are_bitwise_reproducible(dl, name, m, s, rule, ntilde):
+    """With dl_set_deterministic, pass A sums U = E X^T and r (Eq. 3, Eq. 5) in
+    an order fixed by the signal and slot indices, so two runs of three DL
+    iterations from the same start give bit-identical atoms, supports,
+    coefficients and RMSE pairs: PAK-SVD, P-NSGK (whose update reads the
+    previous representations) and groups of atoms.  The RMSE pairs match the
+    default (reduction-order) path's to rounding."""
+    Y, D, _ = synth.workload_inputs(name, m=m)
+    p, n = D.shape[1], D.shape[0]
+    Yd = torch.from_numpy(Y).cuda()
+    outs = []
+    for run in range(3):
+        ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, torch.cuda.current_stream())
+        dl.dl_set_update_rule(ctx, rule)
+        if ntilde:
+            dl.dl_set_group_size(ctx, ntilde)
+        dl.dl_set_deterministic(ctx, run < 2)
+        Dd = torch.from_numpy(D.copy()).cuda()
+        cp = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+        ri = torch.zeros(m * s, dtype=torch.int32, device="cuda")
+        v = torch.zeros(m * s, dtype=torch.float32, device="cuda")
+        rm = np.zeros(6)
+        dl.dl_iterate(ctx, Yd, m, Dd, s, 3, cp, ri, v, rm)
+        dl.dl_destroy(ctx)
+        outs.append((Dd.cpu().numpy(), cp.cpu().numpy(), ri.cpu().numpy(), v.cpu().numpy(), rm))
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_allclose(outs[0][4], outs[2][4], rtol=0, atol=1e-5)
