@@ -283,9 +283,17 @@ cudaError_t enq_gram(dl_ctx* c, const float* D, bool tc) {
 
 bool lp_ok(dl_ctx* c) { return c->lp_kind != 0 && dlk::corr_lp_supported(c->lp_kind, c->p, c->n, c->lda); }
 
-// Y converted to the reduced-precision format (once per call, before any iteration).
+// BF16 correlations straight from FP32 Y (converted on chip by the pipelined kernel).
+bool lp_ws(dl_ctx* c, const float* Y) {
+  return lp_ok(c) && c->lp_kind == dlk::LP_BF16 &&
+         dlk::corr_bf16_ws_supported(Y, c->p, c->n, c->lda);
+}
+
+// Y converted to the reduced-precision format (once per call, before any iteration),
+// unless the correlation kernel reads it in FP32.
+bool needs_y_conversion(dl_ctx* c, const float* Y) { return lp_ok(c) && !lp_ws(c, Y); }
 cudaError_t enq_convert_y(dl_ctx* c, const float* Y, int64_t m) {
-  if (!lp_ok(c)) return cudaSuccess;
+  if (!needs_y_conversion(c, Y)) return cudaSuccess;
   return dlk::to_lowp(c->lp_kind, Y, m, c->p, c->Ylp, c->Ysc, c->st);
 }
 
@@ -293,6 +301,8 @@ cudaError_t enq_corr(dl_ctx* c, const float* Y, int64_t m, const float* D, bool 
   if (lp_ok(c)) {
     cudaError_t e = dlk::to_lowp(c->lp_kind, D, c->n, c->p, c->Dlp, c->Dsc, c->st);
     if (e != cudaSuccess) return e;
+    if (lp_ws(c, Y))
+      return dlk::corr_bf16_ws(Y, m, c->Dlp, c->n, c->p, c->A0, c->lda, c->err, c->st);
     return dlk::corr_lp(c->lp_kind, c->Ylp, m, c->Ysc, c->Dlp, c->Dsc, c->n, c->p, c->A0, c->lda,
                         c->err, c->st);
   }
@@ -899,7 +909,7 @@ int omp_code(dl_ctx* c, const float* Y, int64_t m, const float* D, int s, int64_
     dv = c->hval;
   }
   DL_CHECK(enq_convert_y(c, dY, m));
-  if (lp_ok(c)) c->launches += 1;
+  if (needs_y_conversion(c, dY)) c->launches += 1;
   c->learned_now = false;
   DL_CHECK(enq_omp(c, dY, m, dD, s));
   DL_CHECK(dlk::counts_to_colptr(c->scnt, m, c->bsum, dcp, c->st));
@@ -1036,7 +1046,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
   const bool can_graph = c->st != nullptr && m > 0;
   DL_CHECK(enq_convert_y(c, dY, m));
   if (c->prop) DL_CHECK(dlk::to_lowp(dlk::LP_BF16, dY, m, c->p, c->Ybf, nullptr, c->st));
-  c->launches += (lp_ok(c) ? 1 : 0) + (c->prop ? 1 : 0);  // the per-call conversions of Y
+  c->launches += (needs_y_conversion(c, dY) ? 1 : 0) + (c->prop ? 1 : 0);  // per-call conversions of Y
   for (int it = 0; it < iters; ++it) {
     const bool learned = has_prop(c) && (c->prop_counter % c->prop_full_every) != 0;
     c->learned_now = learned;

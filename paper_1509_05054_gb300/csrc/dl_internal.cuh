@@ -54,6 +54,11 @@ int lp_row_elems(int kind, int p);  // padded row length in elements
 bool corr_lp_supported(int kind, int p, int n, int64_t ldc);
 cudaError_t to_lowp(int kind, const float* src, int64_t rows, int p, void* dst, float* inv_scale,
                     cudaStream_t st);
+// BF16 correlations of FP32 signals, persistent and pipelined (k_corr_lp.cu): Y is
+// converted to BF16 on chip; Dbf = D converted by to_lowp(LP_BF16).  p <= 64, p % 4 == 0.
+bool corr_bf16_ws_supported(const float* Y, int p, int n, int64_t ldc);
+cudaError_t corr_bf16_ws(const float* Y, int64_t rows, const void* Dbf, int n, int p, float* C,
+                         int64_t ldc, int* err, cudaStream_t st);
 cudaError_t corr_lp(int kind, const void* A, int64_t rows_a, const float* a_inv_scale,
                     const void* B, const float* b_inv_scale, int n, int p, float* C, int64_t ldc,
                     int* err, cudaStream_t st);
