@@ -89,6 +89,7 @@ struct dl_ctx {
   void* Ybf = nullptr;       // m_max x pk BF16 copy of Y for the proposer
   bool learned_now = false;  // the iteration being enqueued uses the proposer
   bool prop_corr = false;    // network-free proposer: the K largest |D^T y| (no MLP)
+  bool a0_bf16 = false;      // the coding pass stores alpha0 in BF16 (BF16 form, TMEM OMP)
   cudaGraphExec_t gexec_learned = nullptr;
   int32_t* sidx = nullptr;
   float* sval = nullptr;
@@ -302,7 +303,7 @@ cudaError_t enq_corr(dl_ctx* c, const float* Y, int64_t m, const float* D, bool 
     cudaError_t e = dlk::to_lowp(c->lp_kind, D, c->n, c->p, c->Dlp, c->Dsc, c->st);
     if (e != cudaSuccess) return e;
     if (lp_ws(c, Y))
-      return dlk::corr_bf16_ws(Y, m, c->Dlp, c->n, c->p, c->A0, c->lda, c->err, c->st);
+      return dlk::corr_bf16_ws(Y, m, c->Dlp, c->n, c->p, c->A0, c->a0_bf16, c->lda, c->err, c->st);
     return dlk::corr_lp(c->lp_kind, c->Ylp, m, c->Ysc, c->Dlp, c->Dsc, c->n, c->p, c->A0, c->lda,
                         c->err, c->st);
   }
@@ -357,6 +358,9 @@ cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D
 cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
   const bool tc = tc_ok(c, Y, D);
   const bool learned = has_prop(c) && c->learned_now;
+  // BF16 form: alpha0 is only as accurate as BF16 anyway, so it is stored in BF16
+  // (half the write) when the TMEM OMP reads it
+  c->a0_bf16 = lp_ws(c, Y) && c->cfg_omp_tm && !has_prop(c) && dlk::omp_tm_supported(c->n, s);
   mark(c, 0);
   cudaError_t e;
   if (tc && !learned && !lp_ok(c)) {
@@ -378,7 +382,7 @@ cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s)
   e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st);
   if (e != cudaSuccess) return e;
   if (c->cfg_omp_tm && !has_prop(c) && dlk::omp_tm_supported(c->n, s))
-    e = dlk::omp_batch_tm(c->cfg_omp_tm, c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval,
+    e = dlk::omp_batch_tm(c->cfg_omp_tm, c->A0, c->a0_bf16, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval,
                           c->scnt, c->err, c->rs_list, c->rs_count, (int)c->m_max, c->st);
   else
     e = dlk::omp_batch(c->A0, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval, c->scnt, c->err,
@@ -534,7 +538,7 @@ cudaError_t enq_omp_staged(dl_ctx* c, const float* hostY, const float* dY, int64
     first = false;
     if ((e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
     if (c->cfg_omp_tm && dlk::omp_tm_supported(c->n, s))
-      e = dlk::omp_batch_tm(c->cfg_omp_tm, Aq, c->lda, c->G, c->n, Yq, c->p, mk, s, c->sidx + off * s,
+      e = dlk::omp_batch_tm(c->cfg_omp_tm, Aq, false, c->lda, c->G, c->n, Yq, c->p, mk, s, c->sidx + off * s,
                             c->sval + off * s, c->scnt + off, c->err, c->rs_list, c->rs_count,
                             (int)c->m_max, c->st);
     else
@@ -859,6 +863,7 @@ int dl_correlate(dl_ctx* c, const float* Y, int64_t m, const float* D, float* A)
   if (!Y || !D || !A || ptr_kind(Y) != 1 || ptr_kind(D) != 1 || ptr_kind(A) != 1) return DL_EINVAL;
   DevGuard g(c->dev);
   const bool tc = tc_ok(c, Y, D);
+  c->a0_bf16 = false;  // the caller's A is FP32
   if (tc) DL_CHECK(dlk::split_tf32(D, (int64_t)c->n * c->p, c->Dhi, c->Dlo, c->st));
   DL_CHECK(enq_convert_y(c, Y, m));
   DL_CHECK(enq_corr(c, Y, m, D, tc));

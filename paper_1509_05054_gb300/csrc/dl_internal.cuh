@@ -57,8 +57,9 @@ cudaError_t to_lowp(int kind, const float* src, int64_t rows, int p, void* dst, 
 // BF16 correlations of FP32 signals, persistent and pipelined (k_corr_lp.cu): Y is
 // converted to BF16 on chip; Dbf = D converted by to_lowp(LP_BF16).  p <= 64, p % 4 == 0.
 bool corr_bf16_ws_supported(const float* Y, int p, int n, int64_t ldc);
-cudaError_t corr_bf16_ws(const float* Y, int64_t rows, const void* Dbf, int n, int p, float* C,
-                         int64_t ldc, int* err, cudaStream_t st);
+// C: FP32, or (out_bf16) BF16 rows of ldc elements.
+cudaError_t corr_bf16_ws(const float* Y, int64_t rows, const void* Dbf, int n, int p, void* C,
+                         bool out_bf16, int64_t ldc, int* err, cudaStream_t st);
 cudaError_t corr_lp(int kind, const void* A, int64_t rows_a, const float* a_inv_scale,
                     const void* B, const float* b_inv_scale, int n, int p, float* C, int64_t ldc,
                     int* err, cudaStream_t st);
@@ -78,9 +79,11 @@ cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const
 // The same Batch-OMP with the progressive-Cholesky vectors in tensor memory
 // (k_omp_tm.cu): persistent CTAs of 4q warps (q = 4, 5, 6).  n = 512, 5 <= s <= 8.
 bool omp_tm_supported(int n, int s);
-cudaError_t omp_batch_tm(int q, const float* A0, int64_t lda, const float* G, int n, const float* Y,
-                         int p, int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                         int* rs_list, int* rs_count, int rs_cap, cudaStream_t st);
+// A0: FP32 rows, or BF16 rows (a0_bf16) of lda elements.
+cudaError_t omp_batch_tm(int q, const void* A0, bool a0_bf16, int64_t lda, const float* G, int n,
+                         const float* Y, int p, int64_t m, int s, int32_t* idx, float* val,
+                         int32_t* cnt, int* err, int* rs_list, int* rs_count, int rs_cap,
+                         cudaStream_t st);
 
 // OMP restricted to K ascending candidates per signal (the learned proposer's
 // path) and the full-OMP fallback of listed signals.  ores: residual-energy

@@ -254,6 +254,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *(const uint32_t*)&v;
 }
 
+template <bool OUTB>
 __global__ void __launch_bounds__(BW_THREADS, 1)
     corr_bf16_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmC, int64_t rows, int64_t tiles, int n,
@@ -387,7 +388,36 @@ __global__ void __launch_bounds__(BW_THREADS, 1)
       }
       tc_fence_after();
       const int64_t row0 = t * BW_M + quad * 32;
-      if (row0 < rows) {
+      if (OUTB && row0 < rows) {
+        // BF16 alpha0: this warp's 64 columns as one 32-row x 128-byte box
+        const int col0 = blk_n * BW_N + 64 * half;
+        if (col0 < n) {
+          uint32_t r0[32], r1[32];
+          tmem_ld32(tmem + lane_base + (uint32_t)(blk * BW_N + 64 * half), r0);
+          tmem_ld32(tmem + lane_base + (uint32_t)(blk * BW_N + 64 * half + 32), r1);
+          float* stg = stg0 + sb * (BW_BOX * BW_BOX);
+          if (lane == 0) bulk_wait_read<BW_STAGES - 1>();
+          __syncwarp();
+          uint8_t* rowp = (uint8_t*)stg + lane * 128;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const uint32_t* rr = c < 4 ? r0 : r1;
+            const int b = 8 * (c & 3);
+            *(uint4*)(rowp + ((c ^ (lane & 7)) << 4)) = make_uint4(
+                pack_bf16x2(__uint_as_float(rr[b]), __uint_as_float(rr[b + 1])),
+                pack_bf16x2(__uint_as_float(rr[b + 2]), __uint_as_float(rr[b + 3])),
+                pack_bf16x2(__uint_as_float(rr[b + 4]), __uint_as_float(rr[b + 5])),
+                pack_bf16x2(__uint_as_float(rr[b + 6]), __uint_as_float(rr[b + 7])));
+          }
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&tmC, stg, col0, (int)row0);
+            bulk_commit();
+          }
+          sb = (sb + 1) % BW_STAGES;
+        }
+      } else if (row0 < rows) {
         for (int j = 2 * half; j < 2 * half + 2; ++j) {
           const int col0 = blk_n * BW_N + j * BW_BOX;
           if (col0 >= n) break;
@@ -440,15 +470,18 @@ bool make_map_f32(CUtensorMap* map, const float* ptr, int64_t rows, int p, int b
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// rows x n row-major FP32 output with leading dimension ldc; 32 x 32 store boxes.
-bool make_map_out_f32(CUtensorMap* map, float* ptr, int64_t rows, int n, int64_t ldc) {
+// rows x n row-major output with leading dimension ldc (elements): FP32 with 32 x 32
+// store boxes, or BF16 with 64-column x 32-row boxes (128-byte rows either way).
+bool make_map_out(CUtensorMap* map, void* ptr, bool bf16, int64_t rows, int n, int64_t ldc) {
   auto fn = encode_fn();
   if (!fn) return false;
+  const int es = bf16 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ldc * 4};
-  cuuint32_t box[2] = {(cuuint32_t)BW_BOX, (cuuint32_t)BW_BOX};
+  cuuint64_t strides[1] = {(cuuint64_t)ldc * es};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)BW_BOX};
   cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, estr,
+  return fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+            (void*)ptr, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -486,17 +519,17 @@ bool corr_bf16_ws_supported(const float* Y, int p, int n, int64_t ldc) {
          (ldc % 4) == 0 && ldc >= (int64_t)(n + 15) / 16 * 16 && encode_fn() != nullptr;
 }
 
-cudaError_t corr_bf16_ws(const float* Y, int64_t rows, const void* Dbf, int n, int p, float* C,
-                         int64_t ldc, int* err, cudaStream_t st) {
+cudaError_t corr_bf16_ws(const float* Y, int64_t rows, const void* Dbf, int n, int p, void* C,
+                         bool out_bf16, int64_t ldc, int* err, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  if (((uintptr_t)C % 16) != 0) return cudaErrorInvalidValue;
+  if (((uintptr_t)C % 16) != 0 || (ldc % 8) != 0) return cudaErrorInvalidValue;
   const int ld = lp_row_elems(LP_BF16, p);
   CUtensorMap ma, mb, mc;
   if (!make_map_f32(&ma, Y, rows, p, BW_M) || !make_map_lp(&mb, Dbf, n, ld, 2, BW_N) ||
-      !make_map_out_f32(&mc, C, rows, n, ldc))
+      !make_map_out(&mc, C, out_bf16, rows, n, ldc))
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(corr_bf16_ws_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+  auto kern = out_bf16 ? corr_bf16_ws_kernel<true> : corr_bf16_ws_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)BwSmem::dyn);
   if (e != cudaSuccess) return e;
   const int64_t tiles = (rows + BW_M - 1) / BW_M;
@@ -505,8 +538,8 @@ cudaError_t corr_bf16_ws(const float* Y, int64_t rows, const void* Dbf, int n, i
   if (groups < 1) groups = 1;
   if (groups > tiles) groups = tiles;
   const int kbf = (p + 31) / 32;
-  corr_bf16_ws_kernel<<<(unsigned)(groups * nq), BW_THREADS, BwSmem::dyn, st>>>(
-      ma, mb, mc, rows, tiles, n, kbf, nq, err);
+  kern<<<(unsigned)(groups * nq), BW_THREADS, BwSmem::dyn, st>>>(ma, mb, mc, rows, tiles, n, kbf,
+                                                                   nq, err);
   return cudaGetLastError();
 }
 

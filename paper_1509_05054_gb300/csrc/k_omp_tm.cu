@@ -111,6 +111,16 @@ __device__ __forceinline__ void tm_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// One correlation of the signal's alpha0 row: FP32, or BF16 (the bits of a
+// uint16_t, the BF16 mixed-precision form), widened to FP32.  Read once, not
+// allocated in L1 (it leaves L1 to the Gram rows).
+__device__ __forceinline__ float ld_a0(const float* p) { return ld_stream(p); }
+__device__ __forceinline__ float ld_a0(const uint16_t* p) {
+  unsigned short h;
+  asm("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(h) : "l"(p));
+  return __uint_as_float((uint32_t)h << 16);
+}
+
 // alpha[tsel] on the owning lane, masked to NaN (selected); an indexed branch
 // executed by one lane.
 template <int NT>
@@ -143,10 +153,10 @@ __device__ __forceinline__ float take_alpha(float2 (&alpha)[NT / 2], int tsel, f
 // The OMP of signal i by one warp; see omp_one in k_omp.cu for the steps.
 // tcol: TMEM address of this warp's first column (its quadrant's lane field
 // set); u_q for q < NTM at tcol + 16 q, the others in u_s (shared memory).
-template <int NT, int SMAX, int NTM>
+template <int NT, int SMAX, int NTM, typename AT>
 __device__ __forceinline__ void omp_one_tm(
     int64_t i, const float* __restrict__ G, int n, float (&L)[SMAX][SMAX], float2* u_s,
-    uint32_t tcol, const float* __restrict__ a0row, const float* __restrict__ y, int p, int s,
+    uint32_t tcol, const AT* __restrict__ a0row, const float* __restrict__ y, int p, int s,
     int32_t* __restrict__ oidx, float* __restrict__ oval, int32_t* __restrict__ ocnt,
     int* __restrict__ err, int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap) {
   static_assert(NT == 16, "alpha layout of this kernel: n = 512");
@@ -172,8 +182,8 @@ __device__ __forceinline__ void omp_one_tm(
   float2 alpha[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    alpha[v].x = ld_stream(a0row + 64 * v + lane);
-    alpha[v].y = ld_stream(a0row + 64 * v + 32 + lane);
+    alpha[v].x = ld_a0(a0row + 64 * v + lane);
+    alpha[v].y = ld_a0(a0row + 64 * v + 32 + lane);
   }
 
   float cq[SMAX];     // c_q = 1 / L_qq, uniform
@@ -339,9 +349,9 @@ __device__ __forceinline__ void omp_one_tm(
 
 // Persistent: one CTA of 4Q warps per SM; warp w of CTA b codes signals
 // b * 4Q + w + t * gridDim.x * 4Q.
-template <int NT, int SMAX, int Q>
+template <int NT, int SMAX, int Q, typename AT>
 __global__ void __launch_bounds__(Q * 128, 1) omp_tm_kernel(
-    const float* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
+    const AT* __restrict__ A0, int64_t lda, const float* __restrict__ G, int n,
     const float* __restrict__ Y, int p, int64_t m, int s, int32_t* __restrict__ oidx,
     float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err,
     int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap, int64_t pf) {
@@ -370,10 +380,12 @@ __global__ void __launch_bounds__(Q * 128, 1) omp_tm_kernel(
   for (int64_t i = (int64_t)blockIdx.x * W + warp; i < m; i += stride) {
     const int64_t ip = i + pf;
     if (ip < m) {  // warm L2 with a later signal's correlations and samples
-      if (lane * 32 < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(A0 + ip * lda + lane * 32));
+      constexpr int per_line = 128 / (int)sizeof(AT);  // correlations per 128-byte line
+      if (lane * per_line < n)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(A0 + ip * lda + lane * per_line));
       if (lane * 32 < p) asm volatile("prefetch.global.L2 [%0];" ::"l"(Y + ip * p + lane * 32));
     }
-    omp_one_tm<NT, SMAX, NTM>(i, G, n, Lsh[warp], u_s, tcol, A0 + i * lda, Y + i * p, p, s, oidx,
+    omp_one_tm<NT, SMAX, NTM, AT>(i, G, n, Lsh[warp], u_s, tcol, A0 + i * lda, Y + i * p, p, s, oidx,
                               oval, ocnt, err, rs_list, rs_count, rs_cap);
   }
   tc::tc_fence_before();
@@ -383,8 +395,8 @@ __global__ void __launch_bounds__(Q * 128, 1) omp_tm_kernel(
                  : "memory");
 }
 
-template <int Q>
-cudaError_t launch_tm(const float* A0, int64_t lda, const float* G, int n, const float* Y, int p,
+template <int Q, typename AT>
+cudaError_t launch_tm(const AT* A0, int64_t lda, const float* G, int n, const float* Y, int p,
                       int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err, int* rl,
                       int* rc, int rcap, cudaStream_t st) {
   constexpr int NT = 16, SMAX = 8, W = 4 * Q;
@@ -392,12 +404,12 @@ cudaError_t launch_tm(const float* A0, int64_t lda, const float* G, int n, const
   constexpr int NTM = (COLS / 16) < (SMAX - 1) ? (COLS / 16) : (SMAX - 1);
   constexpr int NSH = (SMAX - 1) - NTM;
   const size_t smem = (size_t)W * NSH * (NT / 2) * 32 * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(omp_tm_kernel<NT, SMAX, Q>,
+  cudaError_t e = cudaFuncSetAttribute(omp_tm_kernel<NT, SMAX, Q, AT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t need = (m + W - 1) / W;
   const int grid = (int)(need < num_sms() ? need : num_sms());
-  omp_tm_kernel<NT, SMAX, Q><<<grid, W * 32, smem, st>>>(A0, lda, G, n, Y, p, m, s, idx, val, cnt,
+  omp_tm_kernel<NT, SMAX, Q, AT><<<grid, W * 32, smem, st>>>(A0, lda, G, n, Y, p, m, s, idx, val, cnt,
                                                           err, rl, rc, rcap,
                                                           (int64_t)grid * W * 2);
   return cudaGetLastError();
@@ -407,16 +419,22 @@ cudaError_t launch_tm(const float* A0, int64_t lda, const float* G, int n, const
 
 bool omp_tm_supported(int n, int s) { return n == 512 && s >= 5 && s <= 8; }
 
-cudaError_t omp_batch_tm(int q, const float* A0, int64_t lda, const float* G, int n, const float* Y,
-                         int p, int64_t m, int s, int32_t* idx, float* val, int32_t* cnt, int* err,
-                         int* rl, int* rc, int rcap, cudaStream_t st) {
+cudaError_t omp_batch_tm(int q, const void* A0, bool a0_bf16, int64_t lda, const float* G, int n,
+                         const float* Y, int p, int64_t m, int s, int32_t* idx, float* val,
+                         int32_t* cnt, int* err, int* rl, int* rc, int rcap, cudaStream_t st) {
   if (!omp_tm_supported(n, s)) return cudaErrorInvalidValue;
   if (m <= 0) return cudaSuccess;
+#define DL_TM(QQ)                                                                                  \
+  return a0_bf16 ? launch_tm<QQ>((const uint16_t*)A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, \
+                                 rc, rcap, st)                                                     \
+                 : launch_tm<QQ>((const float*)A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl,   \
+                                 rc, rcap, st)
   switch (q) {
-    case 4: return launch_tm<4>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
-    case 6: return launch_tm<6>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
-    default: return launch_tm<5>(A0, lda, G, n, Y, p, m, s, idx, val, cnt, err, rl, rc, rcap, st);
+    case 4: DL_TM(4);
+    case 6: DL_TM(6);
+    default: DL_TM(5);
   }
+#undef DL_TM
 }
 
 }  // namespace dlk
