@@ -11,6 +11,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 // The learned support proposer (MLP p -> hidden -> hidden -> n, BF16 weights
@@ -1223,6 +1224,18 @@ struct dl_batch {
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_iters = -1;
+  // small problems (dlk::small_supported, FP32): all iterations of all problems in one
+  // launch of dlk::small_dl, one CTA per problem
+  bool small = false;
+  int rule = DL_RULE_AKSVD;
+  int ntilde = 0;                              // group size set on the batch (0: n)
+  std::vector<dlk::SmallProblem> sp;           // host copies of the descriptors
+  dlk::SmallProblem* d_sp = nullptr;           // device descriptors
+  void* sbuf = nullptr;                        // slots, previous slots, counts, flags
+  double* srmse = nullptr;                     // count x 2 x srmse_iters
+  int srmse_iters = 0;
+  int* serr = nullptr;
+  int64_t small_launches = 0;
 };
 
 namespace {
@@ -1235,7 +1248,87 @@ void free_batch(dl_batch* b) {
   for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
+  for (void* q : {(void*)b->d_sp, b->sbuf, (void*)b->srmse, (void*)b->serr})
+    if (q) cudaFree(q);
   delete b;
+}
+
+// The small-problem path: every problem small enough for one CTA.  Its slot
+// buffers live in one allocation.
+int setup_small(dl_batch* b) {
+  for (const dl_problem& q : b->probs)
+    if (!dlk::small_supported(q.p, q.n, q.s)) return DL_OK;  // not eligible: graph path
+  size_t words = 0;
+  for (const dl_problem& q : b->probs) words += (size_t)4 * q.m * q.s + 2 * (size_t)q.m + 4;
+  if (!dalloc((int**)&b->sbuf, words) || !dalloc(&b->d_sp, (size_t)b->count) ||
+      !dalloc(&b->serr, 1))
+    return DL_ENOMEM;
+  DL_CHECK(cudaMemset(b->sbuf, 0, sizeof(int) * words));
+  DL_CHECK(cudaMemset(b->serr, 0, sizeof(int)));
+  int* w = (int*)b->sbuf;
+  for (const dl_problem& q : b->probs) {
+    dlk::SmallProblem sp{};
+    const size_t ms = (size_t)q.m * q.s;
+    sp.Y = q.Y;
+    sp.D = q.D;
+    sp.p = q.p;
+    sp.n = q.n;
+    sp.s = q.s;
+    sp.m = q.m;
+    sp.sidx = w;
+    sp.sval = (float*)(w + ms);
+    sp.pidx = w + 2 * ms;
+    sp.pval = (float*)(w + 3 * ms);
+    sp.scnt = w + 4 * ms;
+    sp.pcnt = w + 4 * ms + q.m;
+    sp.pvalid = w + 4 * ms + 2 * q.m;
+    sp.colptr = q.colptr;
+    sp.rowidx = q.rowidx;
+    sp.cval = q.val;
+    w += 4 * ms + 2 * (size_t)q.m + 4;
+    b->sp.push_back(sp);
+  }
+  b->small = true;
+  return DL_OK;
+}
+
+bool small_active(const dl_batch* b) {
+  if (!b->small) return false;
+  for (const dl_problem& q : b->probs)
+    if (b->ntilde > 0 && b->ntilde < q.n) return false;  // groups: the graph path
+  return true;
+}
+
+int iterate_small(dl_batch* b, int iters, double* rmse) {
+  if (iters > b->srmse_iters) {  // per problem 2 x srmse_iters doubles
+    DL_CHECK(cudaStreamSynchronize(b->main));
+    if (b->srmse) cudaFree(b->srmse);
+    b->srmse = nullptr;
+    b->srmse_iters = 0;
+    if (!dalloc(&b->srmse, (size_t)b->count * 2 * iters)) return DL_ENOMEM;
+    b->srmse_iters = iters;
+    for (int k = 0; k < b->count; ++k) b->sp[k].rmse = b->srmse + (size_t)k * 2 * iters;
+    // a copy from pageable memory has read the host array when the call returns
+    DL_CHECK(cudaMemcpyAsync(b->d_sp, b->sp.data(), sizeof(dlk::SmallProblem) * b->count,
+                             cudaMemcpyHostToDevice, b->main));
+  }
+  DL_CHECK(dlk::small_dl(b->d_sp, b->count, iters, b->rule, b->serr, b->main));
+  b->small_launches += 1;
+  if (rmse) {
+    DL_CHECK(cudaStreamSynchronize(b->main));
+    const size_t per = (size_t)2 * b->srmse_iters;
+    std::vector<double> h((size_t)b->count * per);
+    DL_CHECK(cudaMemcpy(h.data(), b->srmse, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < b->count; ++k)
+      std::copy(h.begin() + k * per, h.begin() + k * per + 2 * iters, rmse + (size_t)k * 2 * iters);
+    int e = 0;
+    DL_CHECK(cudaMemcpy(&e, b->serr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      DL_CHECK(cudaMemset(b->serr, 0, sizeof(int)));
+      return DL_ENUMERIC;
+    }
+  }
+  return DL_OK;
 }
 
 cudaError_t enq_batch(dl_batch* b, int iters) {
@@ -1318,6 +1411,10 @@ extern "C" int dl_batch_create(dl_batch** out, const dl_problem* problems, int c
       return rc;
     }
   }
+  if (precision == DL_FP32 && setup_small(b) != DL_OK) {
+    free_batch(b);
+    return DL_ENOMEM;
+  }
   *out = b;
   return DL_OK;
 }
@@ -1326,6 +1423,7 @@ extern "C" int dl_batch_iterate(dl_batch* b, int iters, double* rmse) {
   if (!b || iters < 0) return DL_EINVAL;
   if (iters == 0) return DL_OK;
   DevGuard g(b->dev);
+  if (small_active(b)) return iterate_small(b, iters, rmse);
   for (int k = 0; k < b->count; ++k) {
     dl_ctx* c = b->ctxs[k];
     if ((group_size(c) < c->n || c->rule == DL_RULE_NSGK) &&
@@ -1368,6 +1466,12 @@ extern "C" int dl_batch_set_update_rule(dl_batch* b, int rule) {
   if (!b) return DL_EINVAL;
   for (dl_ctx* c : b->ctxs)
     if (int rc = dl_set_update_rule(c, rule)) return rc;
+  b->rule = rule;
+  if (b->small) {  // the stored representations are dropped
+    DevGuard g(b->dev);
+    DL_CHECK(cudaStreamSynchronize(b->main));
+    for (const dlk::SmallProblem& q : b->sp) DL_CHECK(cudaMemset(q.pvalid, 0, sizeof(int)));
+  }
   for (dl_ctx* c : b->ctxs) DL_CHECK(cudaStreamSynchronize(c->st));  // the flag resets
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   b->gexec = nullptr;
@@ -1379,6 +1483,7 @@ extern "C" int dl_batch_set_group_size(dl_batch* b, int ntilde) {
   for (dl_ctx* c : b->ctxs)
     if (ntilde < 1 || ntilde > c->n) return DL_EINVAL;
   for (dl_ctx* c : b->ctxs) dl_set_group_size(c, ntilde);
+  b->ntilde = ntilde;
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   b->gexec = nullptr;
   return DL_OK;
@@ -1391,7 +1496,7 @@ extern "C" int dl_batch_destroy(dl_batch* b) {
 
 extern "C" int64_t dl_batch_kernel_launches(dl_batch* b) {
   if (!b) return 0;
-  int64_t t = 0;
+  int64_t t = b->small_launches;
   for (dl_ctx* c : b->ctxs) t += c->launches;
   return t;
 }

@@ -85,6 +85,31 @@ cudaError_t omp_batch_tm(int q, const void* A0, bool a0_bf16, int64_t lda, const
                          int32_t* cnt, int* err, int* rs_list, int* rs_count, int rs_cap,
                          cudaStream_t st);
 
+// ---- whole DL iterations of small problems, one CTA per problem (k_small.cu) ----
+// Problems with p <= 32, n <= 64, s <= 8 and group size n: a batch runs all its
+// problems' iterations in one launch.
+struct SmallProblem {
+  const float* Y;        // m x p
+  float* D;              // n x p (in/out)
+  int p, n, s;
+  int64_t m;
+  int32_t* sidx;         // m x s slots of the current X
+  float* sval;
+  int32_t* scnt;
+  int32_t* pidx;         // m x s slots of the previous X (P-NSGK)
+  float* pval;
+  int32_t* pcnt;
+  int* pvalid;           // the previous X exists
+  double* rmse;          // 2 per iteration
+  int64_t* colptr;       // CSC of the final X
+  int32_t* rowidx;
+  float* cval;
+};
+constexpr int kSmallP = 32, kSmallN = 64, kSmallS = 8;
+bool small_supported(int p, int n, int s);
+cudaError_t small_dl(const SmallProblem* probs, int count, int iters, int rule, int* err,
+                     cudaStream_t st);
+
 // OMP restricted to K ascending candidates per signal (the learned proposer's
 // path) and the full-OMP fallback of listed signals.  ores: residual-energy
 // estimate per signal; ref_res/tol2: fallback when ores > tol2 * ref_res.
