@@ -82,12 +82,13 @@ EQUAL_RMSE = 0.01
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def committed_traffic(kernel_phase):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, if the
-    kernel's source is unchanged since it was captured (else None)."""
+def committed_traffic(kernel_phase, form):
+    """DRAM bytes per launch of a phase's kernel in a precision form from the
+    committed ncu summary, if the kernel's source is unchanged since it was
+    captured (else None)."""
     import hashlib
     try:
-        rec = json.load(open(TRAFFIC_FILE)).get(kernel_phase)
+        rec = json.load(open(TRAFFIC_FILE)).get(f"{kernel_phase}@{form}")
         src = os.path.join(ROOT, "paper_1509_05054_gb300", "csrc", rec["source"])
         if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["sha256"]:
             return None
@@ -359,7 +360,7 @@ def run_ours(args):
         ach = amount / (ms * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
         per_phase[name] = {"ms": ms, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                            "frac": ach / peak}
-    traffic = committed_traffic(dominant)
+    traffic = committed_traffic(dominant, best)
     if dominant in per_phase:
         r = per_phase[dominant]
         roof = {"kernel": dominant, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
