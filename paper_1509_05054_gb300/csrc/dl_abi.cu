@@ -128,6 +128,7 @@ struct dl_ctx {
   // launch shapes (chosen by dl_autotune; defaults otherwise)
   int cfg_omp_warps = 4;  // warps per CTA of the OMP kernel
   int cfg_omp_tm = 5;     // warps per TMEM quadrant of the TMEM-resident OMP kernel (0: off)
+  int cfg_omp_res = 1;    // residual-form OMP with per-step tensor-core correlations (0: off)
   int deterministic = 0;  // pass A with a fixed summation order (dl_set_deterministic)
   int cfg_acc_mult = 1;   // accumulation CTAs: 1x or 2x the base count
   int cfg_row_per_sm = 4; // row-update CTAs per SM
@@ -356,7 +357,34 @@ cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D
   return e;
 }
 
+// The residual-form OMP (correlations of every step on the tensor cores, no
+// alpha0 pass) serves the plain FP32 form without a proposer.
+bool use_res(dl_ctx* c, const float* Y, const float* D, int s) {
+  return c->cfg_omp_res && !has_prop(c) && !lp_ok(c) &&
+         dlk::omp_res_supported(c->p, c->n, s, Y, D);
+}
+
+cudaError_t enq_omp_res(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
+  const bool tc = tc_ok(c, Y, D);
+  c->a0_bf16 = false;
+  mark(c, 0);
+  cudaError_t e = enq_gram(c, D, tc);
+  if (e != cudaSuccess) return e;
+  mark(c, 1);
+  mark(c, 2);
+  if ((e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
+  e = dlk::omp_res(Y, m, c->p, D, c->n, c->G, s, c->sidx, c->sval, c->scnt, c->err, c->rs_list,
+                   c->rs_count, (int)c->m_max, c->st);
+  if (e != cudaSuccess) return e;
+  e = dlk::omp_resolve64(Y, c->p, D, c->G, nullptr, c->lda, c->n, s, c->rs_list, c->rs_count,
+                         (int)c->m_max, c->sidx, c->sval, c->scnt, c->st);
+  c->omp_kernels[0] = (tc ? 2 : 1) + 2;  // Gram, OMP, FP64 re-solve
+  mark(c, 3);
+  return e;
+}
+
 cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
+  if (use_res(c, Y, D, s)) return enq_omp_res(c, Y, m, D, s);
   const bool tc = tc_ok(c, Y, D);
   const bool learned = has_prop(c) && c->learned_now;
   // BF16 form: alpha0 is only as accurate as BF16 anyway, so it is stored in BF16
@@ -705,6 +733,7 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
   c->st = (cudaStream_t)stream;
   c->lda = ((int64_t)n + 31) / 32 * 32;
   if (const char* v = getenv("DL_OMP_TM")) c->cfg_omp_tm = atoi(v);  // 0 (off), 4, 5 or 6
+  if (const char* v = getenv("DL_OMP_RES")) c->cfg_omp_res = atoi(v);  // 0 (off) or 1
   const size_t mm = (size_t)m_max;
   c->jw.nb_accum = dlk::jau_accum_blocks_max(p, n);
   // the deterministic pass A writes one slice of U and one energy partial per range of signals

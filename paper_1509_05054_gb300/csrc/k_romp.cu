@@ -1,0 +1,598 @@
+// Residual-form OMP sparse coding on the tensor cores, correlations included
+// (Algorithm 1 step 1: the OMP of every signal with the current dictionary).
+//
+// Batch-OMP (k_omp.cu, k_omp_tm.cu) updates alpha = D^T r from alpha0 = D^T y
+// and Gram rows, one warp per signal: per step a reduction over n correlations
+// spread over 32 lanes, a gathered Gram row and s packed FMAs per element, all
+// on the CUDA cores (about 2,300 warp instructions per signal at n = 512,
+// s = 8), after alpha0 itself made a round trip through HBM.  Here the
+// correlations of every step are recomputed from the residual instead,
+// alpha^(k) = D^T r^(k), as one dense product per 128-signal tile:
+//
+//   * D (n <= 512 atoms, p <= 64) sits in shared memory for the whole kernel as
+//     two FP16 parts, D 2^eD = Dh + Dl (22 significant bits); the residuals of a
+//     tile are split the same way, r 2^er = Rh + Rl, and tcgen05.mma (kind::f16,
+//     FP32 accumulation in TMEM) forms Rl Dh^T + Rh Dl^T + Rh Dh^T: 128 signals x
+//     up to 512 atoms, one signal per TMEM lane.  The dropped Rl Dl^T term and
+//     the FP16 roundings leave an error of about 2^-21 ||r|| ||d_j|| per
+//     correlation -- the accuracy class of FP32 Batch-OMP.  alpha0 is step 0 of
+//     the same product and never leaves the chip.
+//   * One thread per signal ("owner") reads its TMEM row (tcgen05.ld 32x32b,
+//     its lane), takes the argmax of |alpha| with the lowest index among equal
+//     values (16-column keys as in omp_common.cuh, chunks in ascending order),
+//     computes alpha_sel = d_sel^T r exactly in FP32 from D's FP32 row, extends
+//     B = L^-1 (the inverse Cholesky factor of G_I, Gram entries from G), and
+//     updates r^(k+1) = r^(k) - D_I (gamma^(k+1) - gamma^(k)) in FP32.  The
+//     stop rules and the FP64 re-solve hand-off are those of Batch-OMP: max
+//     |alpha| = 0, residual energy <= kResidRel ||y||^2, a Cholesky pivot below
+//     kPivotMin (the signal goes to omp_resolve64).
+//   * A persistent CTA per SM keeps two tiles in flight (slots): while the
+//     owners of one slot sweep and update, the tensor core computes the other
+//     slot's correlations.  TMEM holds two 256-column accumulator units; a step
+//     of a 512-atom problem uses both (the sweep of the first overlaps the MMAs
+//     of the second), a step with n <= 256 uses one, alternating.
+//
+// Warp roles (256 threads, two warps per SM sub-partition, so up to 255
+// registers a thread): warps 0-3 own slot 0, warps 4-7 slot 1 (warp w reads
+// TMEM lanes 32 (w mod 4) ..); thread 0 of a slot's first warp issues the
+// slot's MMAs once the slot's four warps have written their residuals (a named
+// barrier per slot).  mbarriers: tfull[u] (tcgen05.commit -> owners) and
+// tempty[u] (owners -> the next use of accumulator unit u).  The uses of the
+// units follow one fixed order (round, step, slot, half); before waiting for
+// its own tfull phase an owner waits for the unit's previous use to have been
+// read, which makes every parity wait unambiguous.  Every wait is bounded
+// (about 2 s); a timeout sets ERR_TIMEOUT and the kernel unwinds and frees its
+// TMEM.
+#include "dl_internal.cuh"
+#include "omp_common.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda_fp16.h>
+#include <math.h>
+
+namespace dlk {
+namespace {
+
+using namespace tc;
+
+constexpr int RT_M = 128;                 // signals per tile = TMEM lanes
+constexpr int RT_N = 256;                 // atoms per MMA = TMEM columns per unit
+constexpr int RT_ROWB = 128;              // bytes of one FP16 row, p <= 64 padded
+constexpr int RT_NMAX = 2 * RT_N;         // atoms
+constexpr int RT_PMAX = 64;
+constexpr int RT_NS = 2;                  // tiles in flight
+constexpr int RT_OWNER_WARPS = 4 * RT_NS;
+constexpr int RT_THREADS = 32 * RT_OWNER_WARPS;
+constexpr int RT_SMAX = 8;
+// kind::f16: D F32 (bits 4-5 = 1), A and B F16 (format 0), K-major, N = 256, M = 128
+constexpr uint32_t RT_IDESC =
+    (1u << 4) | ((uint32_t)(RT_N >> 3) << 17) | ((uint32_t)(RT_M >> 4) << 24);
+
+enum { RB_TFULL = 0, RB_TEMPTY = 2, RB_COUNT = 4 };
+
+// Shared memory (offsets from a 1024-byte aligned base).
+struct RtSmem {
+  static constexpr size_t dh = 0;                                   // Dh rows, 128-byte swizzle
+  static constexpr size_t dl = dh + (size_t)RT_NMAX * RT_ROWB;      // Dl rows
+  static constexpr size_t a = dl + (size_t)RT_NMAX * RT_ROWB;       // per slot: Rh, Rl
+  static constexpr size_t a_part = (size_t)RT_M * RT_ROWB;          // 16 KB
+  static constexpr size_t a_slot = 2 * a_part;
+  static constexpr size_t bars = a + RT_NS * a_slot;
+  static constexpr size_t misc = bars + 8 * RB_COUNT;               // tmem slot, fail, max|D|
+  static constexpr size_t dyn = misc + 64 + 1024;
+};
+
+// Byte offset of 16-byte unit g (FP16 elements 8g .. 8g+7) of row r in a
+// K-major tile with the 128-byte swizzle (8-row groups of 1024 bytes).
+__device__ __forceinline__ uint32_t sw_off(int r, int g) {
+  return (uint32_t)(r * RT_ROWB + ((g ^ (r & 7)) << 4));
+}
+
+// 32 consecutive TMEM columns of this warp's lanes, without the wait.
+__device__ __forceinline__ void tm_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+// Completion of this thread's TMEM loads, with the registers of the last one
+// tied to the wait so that no use of them is scheduled before it.
+__device__ __forceinline__ void tm_wait32(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                 "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
+// Two FP32 values as packed FP16 (round to nearest), v0 in the low half.
+__device__ __forceinline__ uint32_t pack_f16x2(float v0, float v1) {
+  uint32_t d;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v1), "f"(v0));
+  return d;
+}
+// The two FP16 halves of a 32-bit word as FP32 (exact), the low half first.
+__device__ __forceinline__ void unpack_f16x2(uint32_t u, float& v0, float& v1) {
+  asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+      "cvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+      : "=f"(v0), "=f"(v1)
+      : "r"(u));
+}
+
+// Split 2^e-scaled FP32 values into FP16 parts: v = hi + lo + O(2^-22 |v|).
+// hi = v rounded to 11 significant bits (Veltkamp's splitting with 2^13 + 1),
+// lo = v - hi exactly; both then convert to FP16 without further rounding
+// (|v| < 2^14, so hi is a normal FP16 number unless |v| < 2^-14).
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  const float c0 = __fmul_rn(v0, 8193.f), c1 = __fmul_rn(v1, 8193.f);
+  const float h0 = __fsub_rn(c0, __fsub_rn(c0, v0)), h1 = __fsub_rn(c1, __fsub_rn(c1, v1));
+  hi = pack_f16x2(h0, h1);
+  lo = pack_f16x2(__fsub_rn(v0, h0), __fsub_rn(v1, h1));
+}
+
+// Power of two 2^e as a float, e clamped to the normal range.
+__device__ __forceinline__ float pow2i(int e) {
+  e = e < -120 ? -120 : (e > 120 ? 120 : e);
+  return __int_as_float((127 + e) << 23);
+}
+
+// Argmax key of 16 columns: |alpha| with the low 4 mantissa bits replaced by
+// (15 - t), so the float maximum of the keys is the largest |alpha| and, among
+// values equal to within 2^-19 relative, the lowest column t.
+__device__ __forceinline__ float chunk_key(const uint32_t* v) {
+  float k[17];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) k[t] = __uint_as_float((v[t] & 0x7FFFFFF0u) | (uint32_t)(15 - t));
+  k[16] = 0.f;
+  return omp::max_tree<17>(k);
+}
+
+
+// Position of B_qj (j <= q) in the packed lower triangle.
+__host__ __device__ constexpr int tri(int q, int j) { return q * (q + 1) / 2 + j; }
+
+// One signal's OMP state, held by its owner thread.
+struct Owner {
+  float r[RT_PMAX];           // residual r^(k), FP32, zero past p
+  float B[RT_SMAX * (RT_SMAX + 1) / 2];  // B = L^-1, lower triangle by rows (L L^T = G_I)
+  float gam[RT_SMAX];         // coefficients gamma^(k)
+  int I[RT_SMAX];             // selected atoms, in selection order
+  float yy;                   // ||y||^2
+  float rr;                   // ||y||^2 - sum z_q^2 (the stop rule's residual energy)
+  float rn;                   // ||r||^2 of the stored residual (its FP16 scale)
+  int k;                      // atoms selected
+  bool active;                // still selecting
+};
+
+// Row j of D from the shared-memory FP16 parts, 16-byte unit g (elements
+// 8g .. 8g+7): D_j 2^eD = hi + lo.
+__device__ __forceinline__ void row_unit(const uint8_t* Dh, const uint8_t* Dl, int j, int g,
+                                         float (&h)[8], float (&l)[8]) {
+  const uint4 a = *reinterpret_cast<const uint4*>(Dh + sw_off(j, g));
+  const uint4 b = *reinterpret_cast<const uint4*>(Dl + sw_off(j, g));
+  unpack_f16x2(a.x, h[0], h[1]);
+  unpack_f16x2(a.y, h[2], h[3]);
+  unpack_f16x2(a.z, h[4], h[5]);
+  unpack_f16x2(a.w, h[6], h[7]);
+  unpack_f16x2(b.x, l[0], l[1]);
+  unpack_f16x2(b.y, l[2], l[3]);
+  unpack_f16x2(b.z, l[4], l[5]);
+  unpack_f16x2(b.w, l[6], l[7]);
+}
+
+// Step STEP of one signal after the argmax chose atom sel (Batch-OMP's
+// progressive Cholesky in the inverse-factor form):
+//   alpha_sel = d_sel^T r^(k) (FP32);
+//   g_q = G[I_q][sel], w = B g (the new row of L), delta = G[sel][sel] - ||w||^2;
+//   c = 1/sqrt(delta), z = alpha_sel c; row STEP of B: B_kj = -c sum_{q>=j} w_q B_qj,
+//   B_kk = c; gamma += z B_k,:; r -= D_I (z B_k,:)^T.
+// The atoms come from the shared-memory parts (D = (hi + lo) 2^-eD, exact to
+// about 2^-22 relative; no global-memory latency on the step's chain); the
+// Gram entries from G.  A pivot delta <= kPivotMin stops the signal and lists
+// it for the FP64 re-solve, as in omp_one.
+template <int STEP>
+__device__ __forceinline__ void owner_step(Owner& o, int sel, const uint8_t* Dh, const uint8_t* Dl,
+                                           float dsc, const float* __restrict__ G, int n, int s,
+                                           int64_t i, int* __restrict__ err,
+                                           int* __restrict__ rs_list, int* __restrict__ rs_count,
+                                           int rs_cap) {
+  // the Gram entries first: their latency overlaps the dot product below
+  const float gss = __ldg(G + (size_t)sel * n + sel);
+  float g[STEP > 0 ? STEP : 1];
+#pragma unroll
+  for (int q = 0; q < STEP; ++q) g[q] = __ldg(G + (size_t)o.I[q] * n + sel);
+  float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+  for (int u = 0; u < RT_PMAX / 8; ++u) {
+    float h[8], l[8];
+    row_unit(Dh, Dl, sel, u, h, l);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      a0 = fmaf(o.r[8 * u + e], h[e], a0);
+      a1 = fmaf(o.r[8 * u + e], l[e], a1);
+    }
+  }
+  const float asel = (a0 + a1) * dsc;
+  float w[STEP > 0 ? STEP : 1];
+  float wsq = 0.f;
+#pragma unroll
+  for (int q = 0; q < STEP; ++q) {
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j <= q; ++j) acc = fmaf(o.B[tri(q, j)], g[j], acc);
+    w[q] = acc;
+    wsq = fmaf(acc, acc, wsq);
+  }
+  const float delta = gss - wsq;
+  if (!(delta > kPivotMin)) {
+    if (!isfinite(delta)) atomicOr(err, ERR_NONFINITE);
+    if (rs_count) {  // rounding dominates this pivot: redo the signal in FP64
+      const int pos = atomicAdd(rs_count, 1);
+      if (pos < rs_cap) rs_list[pos] = (int)i;
+    }
+    o.active = false;
+    return;
+  }
+  // c = 1 / L_kk: rsqrtf refined by one Newton-Raphson step, y + y (1 - d y^2) / 2
+  float c = rsqrtf(delta);
+  c = fmaf(0.5f * c, fmaf(-delta * c, c, 1.0f), c);
+  const float z = asel * c;
+  float dg[STEP + 1];
+#pragma unroll
+  for (int j = 0; j < STEP; ++j) {
+    float acc = 0.f;
+#pragma unroll
+    for (int q = j; q < STEP; ++q) acc = fmaf(w[q], o.B[tri(q, j)], acc);
+    o.B[tri(STEP, j)] = -c * acc;
+    dg[j] = z * o.B[tri(STEP, j)];
+    o.gam[j] += dg[j];
+  }
+  o.B[tri(STEP, STEP)] = c;
+  dg[STEP] = z * c;
+  o.gam[STEP] = dg[STEP];
+  o.I[STEP] = sel;
+  o.k = STEP + 1;
+  o.rr = fmaf(-z, z, o.rr);
+  if (STEP + 1 >= s || STEP + 1 >= RT_SMAX || o.rr <= kResidRel * o.yy) {
+    o.active = false;  // complete
+    return;
+  }
+  // r^(k+1) = r^(k) - sum_j dg_j d_{I_j}, the atoms' parts scaled back by 2^-eD
+#pragma unroll
+  for (int j = 0; j <= STEP; ++j) {
+    const int a = j == STEP ? sel : o.I[j];
+    const float nd = -dg[j] * dsc;
+#pragma unroll
+    for (int u = 0; u < RT_PMAX / 8; ++u) {
+      float h[8], l[8];
+      row_unit(Dh, Dl, a, u, h, l);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        o.r[8 * u + e] = fmaf(nd, h[e], o.r[8 * u + e]);
+        o.r[8 * u + e] = fmaf(nd, l[e], o.r[8 * u + e]);
+      }
+    }
+  }
+  float n0 = 0.f, n1 = 0.f;
+#pragma unroll
+  for (int e = 0; e < RT_PMAX; e += 2) {
+    n0 = fmaf(o.r[e], o.r[e], n0);
+    n1 = fmaf(o.r[e + 1], o.r[e + 1], n1);
+  }
+  o.rn = n0 + n1;
+}
+
+// The signal's residual as FP16 parts, scaled by 2^er with ||r|| 2^er < 2^14,
+// into row `row` of the slot's two K-major tiles.
+__device__ __forceinline__ void owner_store(const Owner& o, uint8_t* Ah, uint8_t* Al, int row) {
+  int E = 0;
+  frexpf(sqrtf(o.rn), &E);
+  const float sc = o.rn > 0.f ? pow2i(14 - E) : 1.f;
+#pragma unroll
+  for (int g = 0; g < RT_PMAX / 8; ++g) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      split2(o.r[8 * g + 2 * e] * sc, o.r[8 * g + 2 * e + 1] * sc, h[e], l[e]);
+    *reinterpret_cast<uint4*>(Ah + sw_off(row, g)) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(Al + sw_off(row, g)) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// The signal's support in ascending atom order (slots i*s ..), -1 padding, and its count.
+__device__ __forceinline__ void owner_write(const Owner& o, int64_t i, int s,
+                                            int32_t* __restrict__ oidx, float* __restrict__ oval,
+                                            int32_t* __restrict__ ocnt) {
+  const int64_t base = i * s;
+#pragma unroll
+  for (int q = 0; q < RT_SMAX; ++q) {
+    if (q < o.k) {
+      int rank = 0;
+#pragma unroll
+      for (int t = 0; t < RT_SMAX; ++t) rank += (t < o.k && o.I[t] < o.I[q]) ? 1 : 0;
+      oidx[base + rank] = o.I[q];
+      oval[base + rank] = o.gam[q];
+    } else if (q < s) {
+      oidx[base + q] = -1;
+      oval[base + q] = 0.f;
+    }
+  }
+  ocnt[i] = o.k;
+}
+
+// Bounded wait that also gives up as soon as another thread has recorded a
+// failure; a timeout records one.
+__device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, volatile int* fail) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*fail) return false;
+    if (gtimer() - t0 > kWaitNs) {
+      *fail = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// The sweep of one accumulator unit (256 columns = atoms 256 h ..): running
+// best key and its 16-column chunk, chunks in ascending order (the lowest
+// chunk wins equal keys).  Warp-collective: every lane executes it.
+__device__ __forceinline__ void sweep_unit(uint32_t ta, int h, float& best, int& bc) {
+  uint32_t va[32], vb[32];
+  tm_ld32(ta, va);
+  tm_wait32(va);
+#pragma unroll
+  for (int c = 0; c < RT_N / 32; ++c) {
+    const int c0 = 16 * h + 2 * c;
+    if (c & 1) {
+      if (c + 1 < RT_N / 32) tm_ld32(ta + 32 * (c + 1), va);
+      const float k0 = chunk_key(vb), k1 = chunk_key(vb + 16);
+      if (k0 > best) { best = k0; bc = c0; }
+      if (k1 > best) { best = k1; bc = c0 + 1; }
+      if (c + 1 < RT_N / 32) tm_wait32(va);
+    } else {
+      if (c + 1 < RT_N / 32) tm_ld32(ta + 32 * (c + 1), vb);
+      const float k0 = chunk_key(va), k1 = chunk_key(va + 16);
+      if (k0 > best) { best = k0; bc = c0; }
+      if (k1 > best) { best = k1; bc = c0 + 1; }
+      if (c + 1 < RT_N / 32) tm_wait32(vb);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RT_THREADS, 1)
+    romp_kernel(const float* __restrict__ Y, int64_t m, int p, const float* __restrict__ D, int n,
+                const float* __restrict__ G, int s, int32_t* __restrict__ oidx,
+                float* __restrict__ oval, int32_t* __restrict__ ocnt, int* __restrict__ err,
+                int* __restrict__ rs_list, int* __restrict__ rs_count, int rs_cap) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(base + RtSmem::bars);
+  uint32_t* tmem_slot = (uint32_t*)(base + RtSmem::misc);
+  volatile int* fail = (volatile int*)(tmem_slot + 1);
+  unsigned* dmax = (unsigned*)(tmem_slot + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nh = n > RT_N ? 2 : 1;
+  const int64_t ntiles = (m + RT_M - 1) / RT_M;
+  const int64_t grid = gridDim.x, b = blockIdx.x;
+  const int64_t ntb = b < ntiles ? (ntiles - 1 - b) / grid + 1 : 0;  // tiles of this CTA
+  const int rounds = (int)((ntb + RT_NS - 1) / RT_NS);
+
+  if (threadIdx.x == 0) {
+    *fail = 0;
+    *dmax = 0u;
+    for (int u = 0; u < 2; ++u) {
+      mbar_init(&bars[RB_TFULL + u], 1);
+      mbar_init(&bars[RB_TEMPTY + u], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(2 * RT_N)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+
+  // ---- D 2^eD as FP16 parts, rows padded with zeros to 256 nh atoms x 64
+  {
+    float mx = 0.f;
+    for (int e = threadIdx.x; e < n * p; e += RT_THREADS) mx = fmaxf(mx, fabsf(__ldg(D + e)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(omp::FULL, mx, o));
+    if (lane == 0) atomicMax(dmax, __float_as_uint(mx));  // non-negative floats order as integers
+  }
+  __syncthreads();
+  float dsc = 1.f;  // 2^-eD
+  {
+    const float dm = __uint_as_float(*dmax);
+    int E = 0;
+    frexpf(dm, &E);
+    const bool scaled = dm > 0.f && isfinite(dm);
+    const float sc = scaled ? pow2i(14 - E) : 1.f;  // max |D| 2^eD < 2^14
+    dsc = scaled ? pow2i(E - 14) : 1.f;
+    for (int u = threadIdx.x; u < nh * RT_N * 8; u += RT_THREADS) {
+      const int j = u >> 3, g = u & 7;
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int c = 8 * g + e;
+        v[e] = (j < n && c < p) ? __ldg(D + (size_t)j * p + c) * sc : 0.f;
+      }
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) split2(v[2 * e], v[2 * e + 1], h[e], l[e]);
+      *reinterpret_cast<uint4*>(base + RtSmem::dh + sw_off(j, g)) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(base + RtSmem::dl + sw_off(j, g)) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+  }
+  fence_async_smem();  // generic-proxy writes -> the tensor core's reads
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  {
+    // ---------------- owners: one signal per thread ----------------
+    const int sl = warp >> 2, quad = warp & 3, row = quad * 32 + lane;
+    const bool issuer = quad == 0 && lane == 0;
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+    uint8_t* Ah = base + RtSmem::a + sl * RtSmem::a_slot;
+    uint8_t* Al = Ah + RtSmem::a_part;
+    const uint64_t dhd = sw128_desc(base + RtSmem::dh), dld = sw128_desc(base + RtSmem::dl);
+    const uint64_t ahd = sw128_desc(Ah), ald = sw128_desc(Al);
+    // After a failed wait (*fail set) the loops still run to their end with the
+    // work skipped, so that the four warps of a slot always meet at the same
+    // named barriers.
+    for (int j = 0; j < rounds; ++j) {
+      const int64_t v = (int64_t)j * RT_NS + sl;
+      if (v >= ntb) break;  // this slot has no tile in the CTA's last round (slot-uniform)
+      const int aj = (int)(ntb - (int64_t)j * RT_NS < RT_NS ? ntb - (int64_t)j * RT_NS : RT_NS);
+      const int64_t i = (b + v * grid) * RT_M + row;
+      Owner o;
+      o.active = i < m;
+      o.k = 0;
+      {
+        const float4* yp = reinterpret_cast<const float4*>(Y + (size_t)(o.active ? i : 0) * p);
+#pragma unroll
+        for (int q = 0; q < RT_PMAX / 4; ++q) {
+          const float4 t = (o.active && 4 * q < p) ? __ldg(yp + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+          o.r[4 * q] = t.x;
+          o.r[4 * q + 1] = t.y;
+          o.r[4 * q + 2] = t.z;
+          o.r[4 * q + 3] = t.w;
+        }
+      }
+      float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+      for (int e = 0; e < RT_PMAX; e += 2) {
+        y0 = fmaf(o.r[e], o.r[e], y0);
+        y1 = fmaf(o.r[e + 1], o.r[e + 1], y1);
+      }
+      o.yy = o.rr = o.rn = y0 + y1;
+      if (!isfinite(o.yy)) {
+        atomicOr(err, ERR_NONFINITE);
+        o.active = false;
+#pragma unroll
+        for (int e = 0; e < RT_PMAX; ++e) o.r[e] = 0.f;
+        o.rn = 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < RT_SMAX; ++q) {
+        o.gam[q] = 0.f;
+        o.I[q] = 0;
+      }
+      for (int step = 0; step < s; ++step) {
+        if (step == 0 || o.active) owner_store(o, Ah, Al, row);
+        fence_async_smem();  // the residual rows -> the tensor core's reads
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + sl), "r"(128) : "memory");
+        const int u = j * s * RT_NS + step * aj + sl;  // this use's place in the fixed order
+        if (issuer && !*fail) {
+          for (int h = 0; h < nh; ++h) {
+            const int hc = u * nh + h, unit = hc & 1;
+            if (hc >= 2 && !wait_or_fail(&bars[RB_TEMPTY + unit], (uint32_t)(((hc >> 1) - 1) & 1), fail))
+              break;
+            tc_fence_after();
+            const uint32_t dcol = tmem + (uint32_t)(unit * RT_N);
+            const uint64_t boff = (uint64_t)((h * RT_N * RT_ROWB) >> 4);
+            const uint64_t bh = dhd + boff, bl = dld + boff;
+            // the two correction products first, then the leading one
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)  // 16 FP16 = 32 bytes of K per MMA
+              mma_f16(dcol, ald + (uint64_t)(2 * kk), bh + (uint64_t)(2 * kk), RT_IDESC,
+                      kk > 0 ? 1u : 0u);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma_f16(dcol, ahd + (uint64_t)(2 * kk), bl + (uint64_t)(2 * kk), RT_IDESC, 1u);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma_f16(dcol, ahd + (uint64_t)(2 * kk), bh + (uint64_t)(2 * kk), RT_IDESC, 1u);
+            mma_commit(&bars[RB_TFULL + unit]);
+          }
+        }
+        __syncwarp();
+        float best = -1.f;
+        int bc = 0;
+        bool good = true;
+        for (int h = 0; h < nh; ++h) {
+          const int hc = u * nh + h, unit = hc & 1;
+          bool w = good && !*fail;
+          if (w && hc >= 2) w = wait_or_fail(&bars[RB_TEMPTY + unit], (uint32_t)(((hc >> 1) - 1) & 1), fail);
+          if (w) w = wait_or_fail(&bars[RB_TFULL + unit], (uint32_t)((hc >> 1) & 1), fail);
+          good = __all_sync(omp::FULL, w);
+          if (!good) continue;
+          tc_fence_after();
+          sweep_unit(tl + (uint32_t)(unit * RT_N), h, best, bc);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars[RB_TEMPTY + unit]);
+        }
+        if (good && o.active) {
+          const uint32_t kb = __float_as_uint(best);
+          const int sel = 16 * bc + 15 - (int)(kb & 15u);
+          if ((kb & 0x7FFFFFF0u) == 0u || sel >= n) {
+            o.active = false;  // max |alpha| = 0
+          } else {
+            switch (step) {
+#define DL_ROMP_STEP(S)                                                                    \
+  case S:                                                                                  \
+    owner_step<S>(o, sel, base + RtSmem::dh, base + RtSmem::dl, dsc, G, n, s, i, err,    \
+                  rs_list, rs_count, rs_cap);                                            \
+    break;
+              DL_ROMP_STEP(0) DL_ROMP_STEP(1) DL_ROMP_STEP(2) DL_ROMP_STEP(3)
+              DL_ROMP_STEP(4) DL_ROMP_STEP(5) DL_ROMP_STEP(6) DL_ROMP_STEP(7)
+#undef DL_ROMP_STEP
+              default: break;
+            }
+          }
+        }
+        if (!good) o.active = false;
+      }
+      if (!*fail && i < m) owner_write(o, i, s, oidx, oval, ocnt);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * RT_N)
+                 : "memory");
+  }
+  if (threadIdx.x == 0 && *fail) atomicOr(err, ERR_TIMEOUT);
+}
+
+}  // namespace
+
+bool omp_res_supported(int p, int n, int s, const float* Y, const float* D) {
+  return p >= 4 && p <= RT_PMAX && p % 4 == 0 && n >= 1 && n <= RT_NMAX && s >= 1 &&
+         s <= RT_SMAX && s <= n && ((uintptr_t)Y % 16) == 0 && ((uintptr_t)D % 16) == 0;
+}
+
+cudaError_t omp_res(const float* Y, int64_t m, int p, const float* D, int n, const float* G, int s,
+                    int32_t* idx, float* val, int32_t* cnt, int* err, int* rs_list, int* rs_count,
+                    int rs_cap, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(romp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)RtSmem::dyn);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (m + RT_M - 1) / RT_M;
+  const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
+  romp_kernel<<<grid, RT_THREADS, RtSmem::dyn, st>>>(Y, m, p, D, n, G, s, idx, val, cnt, err,
+                                                     rs_list, rs_count, rs_cap);
+  return cudaGetLastError();
+}
+
+}  // namespace dlk
