@@ -82,13 +82,18 @@ EQUAL_RMSE = 0.01
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def committed_traffic(kernel_phase, form):
+OMP_SOURCES = {0: "k_omp.cu", 1: "k_omp_tm.cu", 2: "k_romp.cu", 3: "k_mlp.cu"}
+
+
+def committed_traffic(kernel_phase, form, source=None):
     """DRAM bytes per launch of a phase's kernel in a precision form from the
-    committed ncu summary, if the kernel's source is unchanged since it was
-    captured (else None)."""
+    committed ncu summary, if the record is for the source file that ran (when
+    given) and that source is unchanged since it was captured (else None)."""
     import hashlib
     try:
         rec = json.load(open(TRAFFIC_FILE)).get(f"{kernel_phase}@{form}")
+        if source is not None and rec["source"] != source:
+            return None
         src = os.path.join(ROOT, "paper_1509_05054_gb300", "csrc", rec["source"])
         if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["sha256"]:
             return None
@@ -300,11 +305,13 @@ def run_ours(args):
             dks.append(Dq.cpu().numpy())
             dl.dl_iterate(ctx, Yd, m, Dq, s, 1, colptr, rowidx, val, rm[2 * k: 2 * k + 2])
         resolved = dl.dl_last_resolved(ctx)
+        omp_kernel = dl.dl_last_omp_kernel(ctx)
         form_dicts[prec] = dks
         return ctx, {"value": job_throughput(world, m * args.steps, total_ms * 1e-3),
                      "ms_per_step": total_ms / args.steps, "gpu_launches": launches,
                      "phases_ms": phases, "rmse": rm.reshape(RMSE_ITERS, 2).tolist(),
-                     "final_rmse": float(rm[-1]), "fp64_resolved_last_pass": resolved}
+                     "final_rmse": float(rm[-1]), "fp64_resolved_last_pass": resolved,
+                     "omp_kernel": omp_kernel}
 
     clocks = ClockSampler(physical_gpu_index(local_rank))
     clocks.start()
@@ -343,7 +350,15 @@ def run_ours(args):
         "accumulate": ("hbm", m * (4 * p + 8 * s), hbm, "GB/s"),
         "rows": ("hbm", m * (4 * p + 12 * s), hbm, "GB/s"),
     }
-    if best == "fp32":  # one launch: the correlations of all signals and the Gram matrix
+    omp_kernel = chosen.get("omp_kernel")
+    if omp_kernel == 2:
+        # residual-form OMP: the correlations D^T r of every step are its work
+        # (2 n p per signal and step, one product counted; the kernel runs three
+        # FP16 products per correlation for FP32 accuracy), against the FP16 dense
+        # tensor peak (same rate as BF16)
+        algo["omp"] = ("tensor", 2.0 * m * s * n * p, float(peaks.get("bf16_tflops", 1891.2)),
+                       "TFLOP/s")
+    elif best == "fp32":  # one launch: the correlations of all signals and the Gram matrix
         algo["correlations"] = ("tensor", 2.0 * m * n * p + 2.0 * n * n * p,
                                 float(peaks.get("bf16_tflops", 1891.2)) / 2.0, "TFLOP/s")
     else:
@@ -360,7 +375,8 @@ def run_ours(args):
         ach = amount / (ms * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
         per_phase[name] = {"ms": ms, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                            "frac": ach / peak}
-    traffic = committed_traffic(dominant, best)
+    traffic = committed_traffic(dominant, best,
+                                OMP_SOURCES.get(omp_kernel) if dominant == "omp" else None)
     if dominant in per_phase:
         r = per_phase[dominant]
         roof = {"kernel": dominant, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
@@ -368,7 +384,11 @@ def run_ours(args):
                 "peak_source": ("FP32 multiply-add rate measured on this GPU in this run "
                                 "(dl_fp32_probe, best of FFMA and FFMA2, CUDA events; of measured)"
                                 if r["bound"] == "alu" else
+                                "MEASURED_PEAKS.json bf16_tflops (of measured; FP16 at the BF16 rate)"
+                                if omp_kernel == 2 and dominant == "omp" else
                                 "MEASURED_PEAKS.json (of measured; TF32 = bf16/2 nominal ratio)")}
+        if omp_kernel == 2 and dominant == "omp":
+            roof["executed_products"] = 3  # Rl Dh + Rh Dl + Rh Dh per correlation
 
     # end to end through the C ABI with host buffers (staging copies inside the timed region)
     e2e = None

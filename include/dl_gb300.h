@@ -346,6 +346,19 @@ int dl_autotune(dl_ctx* ctx, const float* Y, int64_t m, const float* D, int s);
 int dl_get_config(dl_ctx* ctx, int* cfg4);
 
 /*
+ * dl_last_omp_kernel -- which sparse-coding kernel the context's last coding
+ * pass (omp_code, dl_iterate) ran (Algorithm 1 step 1), one of
+ *   0  Batch-OMP, one warp per signal, from stored correlations alpha0
+ *   1  the same with the progressive-Cholesky vectors in TMEM
+ *   2  residual-form OMP, the correlations D^T r of every step on the tensor
+ *      cores (FP16 hi/lo parts, FP32 accumulation), no stored alpha0
+ *   3  OMP restricted to proposed candidates (a proposer is attached)
+ *  -1  no coding pass yet
+ * written to *kind.  Returns DL_OK, or DL_EINVAL for a NULL argument.
+ */
+int dl_last_omp_kernel(dl_ctx* ctx, int* kind);
+
+/*
  * Batches of independent DL problems of uneven shapes (p, n, m, s each their
  * own), run together: each problem gets its own context (workspace) and CUDA
  * stream; all problems' iterations are captured once into one CUDA graph with

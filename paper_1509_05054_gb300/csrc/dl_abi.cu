@@ -129,6 +129,7 @@ struct dl_ctx {
   int cfg_omp_warps = 4;  // warps per CTA of the OMP kernel
   int cfg_omp_tm = 5;     // warps per TMEM quadrant of the TMEM-resident OMP kernel (0: off)
   int cfg_omp_res = 1;    // residual-form OMP with per-step tensor-core correlations (0: off)
+  int last_omp = -1;      // the coding kernel of the last pass (dl_last_omp_kernel)
   int deterministic = 0;  // pass A with a fixed summation order (dl_set_deterministic)
   int cfg_acc_mult = 1;   // accumulation CTAs: 1x or 2x the base count
   int cfg_row_per_sm = 4; // row-update CTAs per SM
@@ -324,6 +325,7 @@ bool has_prop(const dl_ctx* c) { return c->prop != nullptr || c->prop_corr; }
 // exceeds tol2 times the one of their last full OMP.
 cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D, int s, bool tc) {
   cudaError_t e;
+  c->last_omp = 3;
   if (c->prop_corr) {
     // network-free proposer: the correlations of all signals first, then the K
     // largest |alpha0| of each
@@ -358,9 +360,11 @@ cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D
 }
 
 // The residual-form OMP (correlations of every step on the tensor cores, no
-// alpha0 pass) serves the plain FP32 form without a proposer.
+// alpha0 pass) serves the plain FP32 form without a proposer for n > 256; at
+// n <= 256 the alpha0 pass is half as costly and the TMEM Batch-OMP was faster
+// (p=64, n=256, s=6, m=2e4: 180 against 160 M signals/s per iteration).
 bool use_res(dl_ctx* c, const float* Y, const float* D, int s) {
-  return c->cfg_omp_res && !has_prop(c) && !lp_ok(c) &&
+  return c->cfg_omp_res && !has_prop(c) && !lp_ok(c) && c->n > 256 &&
          dlk::omp_res_supported(c->p, c->n, s, Y, D);
 }
 
@@ -373,6 +377,7 @@ cudaError_t enq_omp_res(dl_ctx* c, const float* Y, int64_t m, const float* D, in
   mark(c, 1);
   mark(c, 2);
   if ((e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
+  c->last_omp = 2;
   e = dlk::omp_res(Y, m, c->p, D, c->n, c->G, s, c->sidx, c->sval, c->scnt, c->err, c->rs_list,
                    c->rs_count, (int)c->m_max, c->st);
   if (e != cudaSuccess) return e;
@@ -410,7 +415,9 @@ cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s)
   mark(c, 2);
   e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st);
   if (e != cudaSuccess) return e;
-  if (c->cfg_omp_tm && !has_prop(c) && dlk::omp_tm_supported(c->n, s))
+  const bool tm = c->cfg_omp_tm && !has_prop(c) && dlk::omp_tm_supported(c->n, s);
+  c->last_omp = tm ? 1 : 0;
+  if (tm)
     e = dlk::omp_batch_tm(c->cfg_omp_tm, c->A0, c->a0_bf16, c->lda, c->G, c->n, Y, c->p, m, s, c->sidx, c->sval,
                           c->scnt, c->err, c->rs_list, c->rs_count, (int)c->m_max, c->st);
   else
@@ -582,6 +589,7 @@ cudaError_t enq_omp_staged(dl_ctx* c, const float* hostY, const float* dY, int64
     k += 3;
   }
   mark(c, 3);
+  c->last_omp = c->cfg_omp_tm && dlk::omp_tm_supported(c->n, s) ? 1 : 0;
   *kernels = k;
   return cudaSuccess;
 }
@@ -1227,6 +1235,12 @@ extern "C" int dl_autotune(dl_ctx* c, const float* Y, int64_t m, const float* D,
   cudaFree(Dtmp); cudaFree(cp); cudaFree(ri); cudaFree(v);
   cudaMemset(c->err, 0, sizeof(int));
   return rc;
+}
+
+extern "C" int dl_last_omp_kernel(dl_ctx* c, int* kind) {
+  if (!c || !kind) return DL_EINVAL;
+  *kind = c->last_omp;
+  return DL_OK;
 }
 
 extern "C" int dl_get_config(dl_ctx* c, int* cfg4) {

@@ -79,7 +79,8 @@ struct RtSmem {
   static constexpr size_t a_slot = 2 * a_part;
   static constexpr size_t bars = a + RT_NS * a_slot;
   static constexpr size_t misc = bars + 8 * RB_COUNT;               // tmem slot, fail, max|D|
-  static constexpr size_t dyn = misc + 64 + 1024;
+  static constexpr size_t scratch = misc + 64;                      // per thread: I, dg
+  static constexpr size_t dyn = scratch + 2 * RT_SMAX * RT_THREADS * 4 + 1024;
 };
 
 // Byte offset of 16-byte unit g (FP16 elements 8g .. 8g+7) of row r in a
@@ -161,12 +162,14 @@ __device__ __forceinline__ float chunk_key(const uint32_t* v) {
 // Position of B_qj (j <= q) in the packed lower triangle.
 __host__ __device__ constexpr int tri(int q, int j) { return q * (q + 1) / 2 + j; }
 
-// One signal's OMP state, held by its owner thread.
+// One signal's OMP state, held by its owner thread; the selected atoms and
+// the coefficient changes of the current step live in the thread's column of
+// a shared-memory scratch (Is, dgs: element q at q * RT_THREADS + thread), so
+// that the residual update is one rolled loop rather than a copy per step.
 struct Owner {
   float r[RT_PMAX];           // residual r^(k), FP32, zero past p
   float B[RT_SMAX * (RT_SMAX + 1) / 2];  // B = L^-1, lower triangle by rows (L L^T = G_I)
   float gam[RT_SMAX];         // coefficients gamma^(k)
-  int I[RT_SMAX];             // selected atoms, in selection order
   float yy;                   // ||y||^2
   float rr;                   // ||y||^2 - sum z_q^2 (the stop rule's residual energy)
   float rn;                   // ||r||^2 of the stored residual (its FP16 scale)
@@ -190,39 +193,21 @@ __device__ __forceinline__ void row_unit(const uint8_t* Dh, const uint8_t* Dl, i
   unpack_f16x2(b.w, l[6], l[7]);
 }
 
-// Step STEP of one signal after the argmax chose atom sel (Batch-OMP's
-// progressive Cholesky in the inverse-factor form):
-//   alpha_sel = d_sel^T r^(k) (FP32);
-//   g_q = G[I_q][sel], w = B g (the new row of L), delta = G[sel][sel] - ||w||^2;
+// Step STEP of one signal after the argmax chose atom sel and alpha_sel =
+// d_sel^T r^(k) is known (Batch-OMP's progressive Cholesky in the
+// inverse-factor form):
+//   w = B g with g_q = G[I_q][sel] (the new row of L), delta = G[sel][sel] - ||w||^2;
 //   c = 1/sqrt(delta), z = alpha_sel c; row STEP of B: B_kj = -c sum_{q>=j} w_q B_qj,
-//   B_kk = c; gamma += z B_k,:; r -= D_I (z B_k,:)^T.
-// The atoms come from the shared-memory parts (D = (hi + lo) 2^-eD, exact to
-// about 2^-22 relative; no global-memory latency on the step's chain); the
-// Gram entries from G.  A pivot delta <= kPivotMin stops the signal and lists
-// it for the FP64 re-solve, as in omp_one.
+//   B_kk = c; dg = z B_k,: (the change of gamma), gamma += dg.
+// Writes I_STEP = sel and dg to the thread's scratch.  Returns true when the
+// residual is to be updated (r -= D_I dg) for a further step.  A pivot delta <=
+// kPivotMin stops the signal and lists it for the FP64 re-solve, as in omp_one.
 template <int STEP>
-__device__ __forceinline__ void owner_step(Owner& o, int sel, const uint8_t* Dh, const uint8_t* Dl,
-                                           float dsc, const float* __restrict__ G, int n, int s,
-                                           int64_t i, int* __restrict__ err,
+__device__ __forceinline__ bool owner_chol(Owner& o, int sel, float asel, float gss,
+                                           const float (&g)[RT_SMAX], int* Is, float* dgs,
+                                           int s, int64_t i, int* __restrict__ err,
                                            int* __restrict__ rs_list, int* __restrict__ rs_count,
                                            int rs_cap) {
-  // the Gram entries first: their latency overlaps the dot product below
-  const float gss = __ldg(G + (size_t)sel * n + sel);
-  float g[STEP > 0 ? STEP : 1];
-#pragma unroll
-  for (int q = 0; q < STEP; ++q) g[q] = __ldg(G + (size_t)o.I[q] * n + sel);
-  float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-  for (int u = 0; u < RT_PMAX / 8; ++u) {
-    float h[8], l[8];
-    row_unit(Dh, Dl, sel, u, h, l);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      a0 = fmaf(o.r[8 * u + e], h[e], a0);
-      a1 = fmaf(o.r[8 * u + e], l[e], a1);
-    }
-  }
-  const float asel = (a0 + a1) * dsc;
   float w[STEP > 0 ? STEP : 1];
   float wsq = 0.f;
 #pragma unroll
@@ -241,37 +226,62 @@ __device__ __forceinline__ void owner_step(Owner& o, int sel, const uint8_t* Dh,
       if (pos < rs_cap) rs_list[pos] = (int)i;
     }
     o.active = false;
-    return;
+    return false;
   }
   // c = 1 / L_kk: rsqrtf refined by one Newton-Raphson step, y + y (1 - d y^2) / 2
   float c = rsqrtf(delta);
   c = fmaf(0.5f * c, fmaf(-delta * c, c, 1.0f), c);
   const float z = asel * c;
-  float dg[STEP + 1];
 #pragma unroll
   for (int j = 0; j < STEP; ++j) {
     float acc = 0.f;
 #pragma unroll
     for (int q = j; q < STEP; ++q) acc = fmaf(w[q], o.B[tri(q, j)], acc);
     o.B[tri(STEP, j)] = -c * acc;
-    dg[j] = z * o.B[tri(STEP, j)];
-    o.gam[j] += dg[j];
+    const float dg = z * o.B[tri(STEP, j)];
+    dgs[j * RT_THREADS] = dg;
+    o.gam[j] += dg;
   }
   o.B[tri(STEP, STEP)] = c;
-  dg[STEP] = z * c;
-  o.gam[STEP] = dg[STEP];
-  o.I[STEP] = sel;
+  dgs[STEP * RT_THREADS] = z * c;
+  o.gam[STEP] = z * c;
+  Is[STEP * RT_THREADS] = sel;
   o.k = STEP + 1;
   o.rr = fmaf(-z, z, o.rr);
   if (STEP + 1 >= s || STEP + 1 >= RT_SMAX || o.rr <= kResidRel * o.yy) {
     o.active = false;  // complete
-    return;
+    return false;
   }
-  // r^(k+1) = r^(k) - sum_j dg_j d_{I_j}, the atoms' parts scaled back by 2^-eD
+  return true;
+}
+
+// d_j^T r for atom j, from the shared-memory parts (D = (hi + lo) 2^-eD, exact
+// to about 2^-22 relative; no global-memory latency on the step's chain), in
+// units of 2^-eD.
+__device__ __forceinline__ float owner_dot(const Owner& o, int j, const uint8_t* Dh,
+                                           const uint8_t* Dl) {
+  float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-  for (int j = 0; j <= STEP; ++j) {
-    const int a = j == STEP ? sel : o.I[j];
-    const float nd = -dg[j] * dsc;
+  for (int u = 0; u < RT_PMAX / 8; ++u) {
+    float h[8], l[8];
+    row_unit(Dh, Dl, j, u, h, l);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      a0 = fmaf(o.r[8 * u + e], h[e], a0);
+      a1 = fmaf(o.r[8 * u + e], l[e], a1);
+    }
+  }
+  return a0 + a1;
+}
+
+// r^(k+1) = r^(k) - sum_{j <= step} dg_j d_{I_j} (atoms from the shared-memory
+// parts, scaled back by 2^-eD), and ||r^(k+1)||^2.  One rolled loop over atoms.
+__device__ __forceinline__ void owner_update(Owner& o, int step, const int* Is, const float* dgs,
+                                             const uint8_t* Dh, const uint8_t* Dl, float dsc) {
+#pragma unroll 1
+  for (int j = 0; j <= step; ++j) {
+    const int a = Is[j * RT_THREADS];
+    const float nd = -dgs[j * RT_THREADS] * dsc;
 #pragma unroll
     for (int u = 0; u < RT_PMAX / 8; ++u) {
       float h[8], l[8];
@@ -310,17 +320,20 @@ __device__ __forceinline__ void owner_store(const Owner& o, uint8_t* Ah, uint8_t
 }
 
 // The signal's support in ascending atom order (slots i*s ..), -1 padding, and its count.
-__device__ __forceinline__ void owner_write(const Owner& o, int64_t i, int s,
+__device__ __forceinline__ void owner_write(const Owner& o, const int* Is, int64_t i, int s,
                                             int32_t* __restrict__ oidx, float* __restrict__ oval,
                                             int32_t* __restrict__ ocnt) {
   const int64_t base = i * s;
+  int I[RT_SMAX];
+#pragma unroll
+  for (int q = 0; q < RT_SMAX; ++q) I[q] = q < o.k ? Is[q * RT_THREADS] : 0;
 #pragma unroll
   for (int q = 0; q < RT_SMAX; ++q) {
     if (q < o.k) {
       int rank = 0;
 #pragma unroll
-      for (int t = 0; t < RT_SMAX; ++t) rank += (t < o.k && o.I[t] < o.I[q]) ? 1 : 0;
-      oidx[base + rank] = o.I[q];
+      for (int t = 0; t < RT_SMAX; ++t) rank += (t < o.k && I[t] < I[q]) ? 1 : 0;
+      oidx[base + rank] = I[q];
       oval[base + rank] = o.gam[q];
     } else if (q < s) {
       oidx[base + q] = -1;
@@ -451,6 +464,10 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
     uint8_t* Ah = base + RtSmem::a + sl * RtSmem::a_slot;
     uint8_t* Al = Ah + RtSmem::a_part;
+    const uint8_t* Dh = base + RtSmem::dh;
+    const uint8_t* Dl = base + RtSmem::dl;
+    int* Is = (int*)(base + RtSmem::scratch) + threadIdx.x;  // this thread's column
+    float* dgs = (float*)(base + RtSmem::scratch) + RT_SMAX * RT_THREADS + threadIdx.x;
     const uint64_t dhd = sw128_desc(base + RtSmem::dh), dld = sw128_desc(base + RtSmem::dl);
     const uint64_t ahd = sw128_desc(Ah), ald = sw128_desc(Al);
     // After a failed wait (*fail set) the loops still run to their end with the
@@ -490,10 +507,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         o.rn = 0.f;
       }
 #pragma unroll
-      for (int q = 0; q < RT_SMAX; ++q) {
-        o.gam[q] = 0.f;
-        o.I[q] = 0;
-      }
+      for (int q = 0; q < RT_SMAX; ++q) o.gam[q] = 0.f;
       for (int step = 0; step < s; ++step) {
         if (step == 0 || o.active) owner_store(o, Ah, Al, row);
         fence_async_smem();  // the residual rows -> the tensor core's reads
@@ -545,22 +559,30 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
           if ((kb & 0x7FFFFFF0u) == 0u || sel >= n) {
             o.active = false;  // max |alpha| = 0
           } else {
+            // the Gram entries first: their latency overlaps the dot product
+            const float gss = __ldg(G + (size_t)sel * n + sel);
+            float g[RT_SMAX];
+#pragma unroll
+            for (int q = 0; q < RT_SMAX; ++q)
+              g[q] = q < step ? __ldg(G + (size_t)Is[q * RT_THREADS] * n + sel) : 0.f;
+            const float asel = owner_dot(o, sel, Dh, Dl) * dsc;
+            bool more = false;
             switch (step) {
-#define DL_ROMP_STEP(S)                                                                    \
-  case S:                                                                                  \
-    owner_step<S>(o, sel, base + RtSmem::dh, base + RtSmem::dl, dsc, G, n, s, i, err,    \
-                  rs_list, rs_count, rs_cap);                                            \
+#define DL_ROMP_STEP(S)                                                                       \
+  case S:                                                                                     \
+    more = owner_chol<S>(o, sel, asel, gss, g, Is, dgs, s, i, err, rs_list, rs_count, rs_cap); \
     break;
               DL_ROMP_STEP(0) DL_ROMP_STEP(1) DL_ROMP_STEP(2) DL_ROMP_STEP(3)
               DL_ROMP_STEP(4) DL_ROMP_STEP(5) DL_ROMP_STEP(6) DL_ROMP_STEP(7)
 #undef DL_ROMP_STEP
               default: break;
             }
+            if (more) owner_update(o, step, Is, dgs, Dh, Dl, dsc);
           }
         }
         if (!good) o.active = false;
       }
-      if (!*fail && i < m) owner_write(o, i, s, oidx, oval, ocnt);
+      if (!*fail && i < m) owner_write(o, Is, i, s, oidx, oval, ocnt);
     }
   }
 

@@ -83,6 +83,7 @@ def load(build_if_missing: bool = True):
         lib.dl_phase_times.argtypes = [P, P, i32]
         lib.dl_autotune.argtypes = [P, P, i64, P, i32]
         lib.dl_get_config.argtypes = [P, P]
+        lib.dl_last_omp_kernel.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
         lib.dl_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(DLProblem), i32, i32, i32, P]
         lib.dl_batch_iterate.argtypes = [P, i32, P]
         lib.dl_batch_destroy.argtypes = [P]
@@ -266,6 +267,14 @@ def dl_iterate(ctx: int, Y, m: int, D, s: int, iters: int, colptr, rowidx, val, 
 
 def dl_autotune(ctx: int, Y, m: int, D, s: int) -> None:
     _check(load().dl_autotune(ctx, _ptr(Y), m, _ptr(D), s), "dl_autotune")
+
+
+def dl_last_omp_kernel(ctx: int) -> int:
+    """The coding kernel of the last pass: 0 Batch-OMP (warp), 1 Batch-OMP (TMEM),
+    2 residual-form tensor-core OMP, 3 restricted to proposed candidates, -1 none."""
+    out = ctypes.c_int(0)
+    _check(load().dl_last_omp_kernel(ctx, ctypes.byref(out)), "dl_last_omp_kernel")
+    return int(out.value)
 
 
 def dl_get_config(ctx: int) -> dict:
