@@ -538,8 +538,56 @@ void staged_pieces(int64_t m, int64_t (&off)[dl_ctx::kChunks + 1]) {
 // side stream, and the correlations (the Gram matrix with the first piece), the
 // OMP and the FP64 re-solve of each piece start as soon as it has arrived.
 // dY is the device staging buffer the pieces go to.  Returns the kernel count.
+// The staged coding pass of the residual-form OMP: the Gram matrix first (it
+// needs no signal), then Y in two pieces; the first holds one full round of the
+// OMP kernel's tiles (all SMs, both slots), so that only its upload is waited
+// for and splitting adds no partial round.
+cudaError_t enq_omp_res_staged(dl_ctx* c, const float* hostY, const float* dY, int64_t m,
+                               const float* D, int s, int* kernels) {
+  const int64_t p = c->p;
+  const bool tc = tc_ok(c, dY, D);
+  int64_t offs[3] = {0, std::min(m, dlk::omp_res_round_signals()), m};
+  cudaError_t e;
+  c->a0_bf16 = false;
+  c->last_omp = 2;
+  mark(c, 0);
+  if ((e = enq_gram(c, D, tc)) != cudaSuccess) return e;
+  int k = tc ? 2 : 1;
+  mark(c, 1);
+  if ((e = cudaEventRecord(c->ev_fork, c->st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(c->st2, c->ev_fork, 0)) != cudaSuccess) return e;
+  for (int q = 0; q < 2; ++q) {
+    const int64_t off = offs[q], mk = offs[q + 1] - offs[q];
+    if (mk <= 0) continue;
+    e = cudaMemcpyAsync((float*)dY + off * p, hostY + off * p, sizeof(float) * (size_t)(mk * p),
+                        cudaMemcpyHostToDevice, c->st2);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(c->ev_chunk[q], c->st2)) != cudaSuccess) return e;
+  }
+  mark(c, 2);
+  for (int q = 0; q < 2; ++q) {
+    const int64_t off = offs[q], mk = offs[q + 1] - offs[q];
+    if (mk <= 0) continue;
+    const float* Yq = dY + off * p;
+    if ((e = cudaStreamWaitEvent(c->st, c->ev_chunk[q], 0)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
+    e = dlk::omp_res(Yq, mk, c->p, D, c->n, c->G, s, c->sidx + off * s, c->sval + off * s,
+                     c->scnt + off, c->err, c->rs_list, c->rs_count, (int)c->m_max, c->st);
+    if (e != cudaSuccess) return e;
+    e = dlk::omp_resolve64(Yq, c->p, D, c->G, nullptr, c->lda, c->n, s, c->rs_list, c->rs_count,
+                           (int)c->m_max, c->sidx + off * s, c->sval + off * s, c->scnt + off,
+                           c->st);
+    if (e != cudaSuccess) return e;
+    k += 2;
+  }
+  mark(c, 3);
+  *kernels = k;
+  return cudaSuccess;
+}
+
 cudaError_t enq_omp_staged(dl_ctx* c, const float* hostY, const float* dY, int64_t m,
                            const float* D, int s, int* kernels) {
+  if (use_res(c, dY, D, s)) return enq_omp_res_staged(c, hostY, dY, m, D, s, kernels);
   const int64_t p = c->p;
   int64_t offs[dl_ctx::kChunks + 1];
   staged_pieces(m, offs);

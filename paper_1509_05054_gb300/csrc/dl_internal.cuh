@@ -84,6 +84,7 @@ cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const
 // p % 4 == 0, p <= 64, n <= 512, s <= 8, Y and D 16-byte aligned.  Signals with
 // a pivot below kPivotMin are listed for omp_resolve64.
 bool omp_res_supported(int p, int n, int s, const float* Y, const float* D);
+int64_t omp_res_round_signals();  // signals of one round of tiles (all SMs, all slots)
 cudaError_t omp_res(const float* Y, int64_t m, int p, const float* D, int n, const float* G, int s,
                     int32_t* idx, float* val, int32_t* cnt, int* err, int* rs_list, int* rs_count,
                     int rs_cap, cudaStream_t st);

@@ -598,6 +598,8 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
 
 }  // namespace
 
+int64_t omp_res_round_signals() { return (int64_t)num_sms() * RT_NS * RT_M; }
+
 bool omp_res_supported(int p, int n, int s, const float* Y, const float* D) {
   return p >= 4 && p <= RT_PMAX && p % 4 == 0 && n >= 1 && n <= RT_NMAX && s >= 1 &&
          s <= RT_SMAX && s <= n && ((uintptr_t)Y % 16) == 0 && ((uintptr_t)D % 16) == 0;
