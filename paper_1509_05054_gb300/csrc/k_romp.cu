@@ -20,9 +20,13 @@
 //   * One thread per signal ("owner") reads its TMEM row (tcgen05.ld 32x32b,
 //     its lane), takes the argmax of |alpha| with the lowest index among equal
 //     values (16-column keys as in omp_common.cuh, chunks in ascending order),
-//     computes alpha_sel = d_sel^T r exactly in FP32 from D's FP32 row, extends
-//     B = L^-1 (the inverse Cholesky factor of G_I, Gram entries from G), and
-//     updates r^(k+1) = r^(k) - D_I (gamma^(k+1) - gamma^(k)) in FP32.  The
+//     computes alpha_sel = d_sel^T r in FP32 from D's shared-memory parts
+//     (hi + lo, 22 significant bits), extends B = L^-1 (the inverse Cholesky
+//     factor of G_I, Gram entries from G), and updates
+//     r^(k+1) = r^(k) - D_I (gamma^(k+1) - gamma^(k)) in FP32 in one rolled loop
+//     over the selected atoms (kept with the step's coefficient changes in a
+//     per-thread shared-memory scratch: one copy of that code, not one per
+//     step, keeps the kernel small enough for the instruction cache).  The
 //     stop rules and the FP64 re-solve hand-off are those of Batch-OMP: max
 //     |alpha| = 0, residual energy <= kResidRel ||y||^2, a Cholesky pivot below
 //     kPivotMin (the signal goes to omp_resolve64).
