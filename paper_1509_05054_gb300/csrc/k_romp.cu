@@ -171,7 +171,7 @@ __host__ __device__ constexpr int tri(int q, int j) { return q * (q + 1) / 2 + j
 // a shared-memory scratch (Is, dgs: element q at q * RT_THREADS + thread), so
 // that the residual update is one rolled loop rather than a copy per step.
 struct Owner {
-  float r[RT_PMAX];           // residual r^(k), FP32, zero past p
+  float2 r[RT_PMAX / 2];      // residual r^(k), FP32 pairs (packed FMAs), zero past p
   float B[RT_SMAX * (RT_SMAX + 1) / 2];  // B = L^-1, lower triangle by rows (L L^T = G_I)
   float gam[RT_SMAX];         // coefficients gamma^(k)
   float yy;                   // ||y||^2
@@ -184,17 +184,17 @@ struct Owner {
 // Row j of D from the shared-memory FP16 parts, 16-byte unit g (elements
 // 8g .. 8g+7): D_j 2^eD = hi + lo.
 __device__ __forceinline__ void row_unit(const uint8_t* Dh, const uint8_t* Dl, int j, int g,
-                                         float (&h)[8], float (&l)[8]) {
+                                         float2 (&h)[4], float2 (&l)[4]) {
   const uint4 a = *reinterpret_cast<const uint4*>(Dh + sw_off(j, g));
   const uint4 b = *reinterpret_cast<const uint4*>(Dl + sw_off(j, g));
-  unpack_f16x2(a.x, h[0], h[1]);
-  unpack_f16x2(a.y, h[2], h[3]);
-  unpack_f16x2(a.z, h[4], h[5]);
-  unpack_f16x2(a.w, h[6], h[7]);
-  unpack_f16x2(b.x, l[0], l[1]);
-  unpack_f16x2(b.y, l[2], l[3]);
-  unpack_f16x2(b.z, l[4], l[5]);
-  unpack_f16x2(b.w, l[6], l[7]);
+  unpack_f16x2(a.x, h[0].x, h[0].y);
+  unpack_f16x2(a.y, h[1].x, h[1].y);
+  unpack_f16x2(a.z, h[2].x, h[2].y);
+  unpack_f16x2(a.w, h[3].x, h[3].y);
+  unpack_f16x2(b.x, l[0].x, l[0].y);
+  unpack_f16x2(b.y, l[1].x, l[1].y);
+  unpack_f16x2(b.z, l[2].x, l[2].y);
+  unpack_f16x2(b.w, l[3].x, l[3].y);
 }
 
 // Step STEP of one signal after the argmax chose atom sel and alpha_sel =
@@ -264,46 +264,50 @@ __device__ __forceinline__ bool owner_chol(Owner& o, int sel, float asel, float 
 // units of 2^-eD.
 __device__ __forceinline__ float owner_dot(const Owner& o, int j, const uint8_t* Dh,
                                            const uint8_t* Dl) {
-  float a0 = 0.f, a1 = 0.f;
+  float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
   for (int u = 0; u < RT_PMAX / 8; ++u) {
-    float h[8], l[8];
+    float2 h[4], l[4];
     row_unit(Dh, Dl, j, u, h, l);
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      a0 = fmaf(o.r[8 * u + e], h[e], a0);
-      a1 = fmaf(o.r[8 * u + e], l[e], a1);
+    for (int e = 0; e < 4; ++e) {
+      a0 = __ffma2_rn(o.r[4 * u + e], h[e], a0);
+      a1 = __ffma2_rn(o.r[4 * u + e], l[e], a1);
     }
   }
-  return a0 + a1;
+  return (a0.x + a0.y) + (a1.x + a1.y);
+}
+
+// ||r||^2 of the residual, packed.
+__device__ __forceinline__ float owner_norm2(const Owner& o) {
+  float2 n = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int e = 0; e < RT_PMAX / 2; ++e) n = __ffma2_rn(o.r[e], o.r[e], n);
+  return n.x + n.y;
 }
 
 // r^(k+1) = r^(k) - sum_{j <= step} dg_j d_{I_j} (atoms from the shared-memory
-// parts, scaled back by 2^-eD), and ||r^(k+1)||^2.  One rolled loop over atoms.
+// parts, scaled back by 2^-eD), and ||r^(k+1)||^2.  One rolled loop over atoms;
+// packed FP32x2 multiply-adds.
 __device__ __forceinline__ void owner_update(Owner& o, int step, const int* Is, const float* dgs,
                                              const uint8_t* Dh, const uint8_t* Dl, float dsc) {
 #pragma unroll 1
   for (int j = 0; j <= step; ++j) {
     const int a = Is[j * RT_THREADS];
     const float nd = -dgs[j * RT_THREADS] * dsc;
+    const float2 nd2 = make_float2(nd, nd);
 #pragma unroll
     for (int u = 0; u < RT_PMAX / 8; ++u) {
-      float h[8], l[8];
+      float2 h[4], l[4];
       row_unit(Dh, Dl, a, u, h, l);
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        o.r[8 * u + e] = fmaf(nd, h[e], o.r[8 * u + e]);
-        o.r[8 * u + e] = fmaf(nd, l[e], o.r[8 * u + e]);
+      for (int e = 0; e < 4; ++e) {
+        o.r[4 * u + e] = __ffma2_rn(nd2, h[e], o.r[4 * u + e]);
+        o.r[4 * u + e] = __ffma2_rn(nd2, l[e], o.r[4 * u + e]);
       }
     }
   }
-  float n0 = 0.f, n1 = 0.f;
-#pragma unroll
-  for (int e = 0; e < RT_PMAX; e += 2) {
-    n0 = fmaf(o.r[e], o.r[e], n0);
-    n1 = fmaf(o.r[e + 1], o.r[e + 1], n1);
-  }
-  o.rn = n0 + n1;
+  o.rn = owner_norm2(o);
 }
 
 // The signal's residual as FP16 parts, scaled by 2^er with ||r|| 2^er < 2^14,
@@ -312,12 +316,22 @@ __device__ __forceinline__ void owner_store(const Owner& o, uint8_t* Ah, uint8_t
   int E = 0;
   frexpf(sqrtf(o.rn), &E);
   const float sc = o.rn > 0.f ? pow2i(14 - E) : 1.f;
+  const float2 sc2 = make_float2(sc, sc), m1 = make_float2(-1.f, -1.f);
+  const float2 k2 = make_float2(8193.f, 8193.f);
 #pragma unroll
   for (int g = 0; g < RT_PMAX / 8; ++g) {
     uint32_t h[4], l[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
-      split2(o.r[8 * g + 2 * e] * sc, o.r[8 * g + 2 * e + 1] * sc, h[e], l[e]);
+    for (int e = 0; e < 4; ++e) {
+      // split2 with packed operations: c = 8193 v, hi = c - (c - v), lo = v - hi
+      // (each subtraction one FMA with -1: a single rounding, as __fsub_rn)
+      const float2 v = __fmul2_rn(o.r[4 * g + e], sc2);
+      const float2 c = __fmul2_rn(v, k2);
+      const float2 hi = __ffma2_rn(__ffma2_rn(v, m1, c), m1, c);
+      const float2 lo = __ffma2_rn(hi, m1, v);
+      h[e] = pack_f16x2(hi.x, hi.y);
+      l[e] = pack_f16x2(lo.x, lo.y);
+    }
     *reinterpret_cast<uint4*>(Ah + sw_off(row, g)) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(Al + sw_off(row, g)) = make_uint4(l[0], l[1], l[2], l[3]);
   }
@@ -490,24 +504,16 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
 #pragma unroll
         for (int q = 0; q < RT_PMAX / 4; ++q) {
           const float4 t = (o.active && 4 * q < p) ? __ldg(yp + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-          o.r[4 * q] = t.x;
-          o.r[4 * q + 1] = t.y;
-          o.r[4 * q + 2] = t.z;
-          o.r[4 * q + 3] = t.w;
+          o.r[2 * q] = make_float2(t.x, t.y);
+          o.r[2 * q + 1] = make_float2(t.z, t.w);
         }
       }
-      float y0 = 0.f, y1 = 0.f;
-#pragma unroll
-      for (int e = 0; e < RT_PMAX; e += 2) {
-        y0 = fmaf(o.r[e], o.r[e], y0);
-        y1 = fmaf(o.r[e + 1], o.r[e + 1], y1);
-      }
-      o.yy = o.rr = o.rn = y0 + y1;
+      o.yy = o.rr = o.rn = owner_norm2(o);
       if (!isfinite(o.yy)) {
         atomicOr(err, ERR_NONFINITE);
         o.active = false;
 #pragma unroll
-        for (int e = 0; e < RT_PMAX; ++e) o.r[e] = 0.f;
+        for (int e = 0; e < RT_PMAX / 2; ++e) o.r[e] = make_float2(0.f, 0.f);
         o.rn = 0.f;
       }
 #pragma unroll
