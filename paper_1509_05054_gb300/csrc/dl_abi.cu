@@ -369,10 +369,9 @@ bool use_res(dl_ctx* c, const float* Y, const float* D, int s) {
 }
 
 cudaError_t enq_omp_res(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
-  const bool tc = tc_ok(c, Y, D);
   c->a0_bf16 = false;
   mark(c, 0);
-  cudaError_t e = enq_gram(c, D, tc);
+  cudaError_t e = dlk::gram_simt(D, c->n, c->p, c->G, c->st);  // G for the Cholesky rows
   if (e != cudaSuccess) return e;
   mark(c, 1);
   mark(c, 2);
@@ -383,7 +382,7 @@ cudaError_t enq_omp_res(dl_ctx* c, const float* Y, int64_t m, const float* D, in
   if (e != cudaSuccess) return e;
   e = dlk::omp_resolve64(Y, c->p, D, c->G, nullptr, c->lda, c->n, s, c->rs_list, c->rs_count,
                          (int)c->m_max, c->sidx, c->sval, c->scnt, c->st);
-  c->omp_kernels[0] = (tc ? 2 : 1) + 2;  // Gram, OMP, FP64 re-solve
+  c->omp_kernels[0] = 3;  // Gram, OMP, FP64 re-solve
   mark(c, 3);
   return e;
 }
@@ -545,14 +544,13 @@ void staged_pieces(int64_t m, int64_t (&off)[dl_ctx::kChunks + 1]) {
 cudaError_t enq_omp_res_staged(dl_ctx* c, const float* hostY, const float* dY, int64_t m,
                                const float* D, int s, int* kernels) {
   const int64_t p = c->p;
-  const bool tc = tc_ok(c, dY, D);
   int64_t offs[3] = {0, std::min(m, dlk::omp_res_round_signals()), m};
   cudaError_t e;
   c->a0_bf16 = false;
   c->last_omp = 2;
   mark(c, 0);
-  if ((e = enq_gram(c, D, tc)) != cudaSuccess) return e;
-  int k = tc ? 2 : 1;
+  if ((e = dlk::gram_simt(D, c->n, c->p, c->G, c->st)) != cudaSuccess) return e;
+  int k = 1;
   mark(c, 1);
   if ((e = cudaEventRecord(c->ev_fork, c->st)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(c->st2, c->ev_fork, 0)) != cudaSuccess) return e;

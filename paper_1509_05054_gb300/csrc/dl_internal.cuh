@@ -27,6 +27,8 @@ constexpr float kGapTol = 4e-6f;
 // C[i*ldc + j] = sum_r A[i*p + r] * B[j*p + r]  for i < rows_a, j < rows_b (FP32, CUDA cores)
 cudaError_t gemm_nt_simt(const float* A, int64_t rows_a, const float* B, int rows_b, int p, float* C,
                          int64_t ldc, cudaStream_t st);
+// G = D D^T (n x n, exactly symmetric), FP32 on the CUDA cores in one short launch.
+cudaError_t gram_simt(const float* D, int n, int p, float* G, cudaStream_t st);
 
 // FP32-accurate C = A B^T on tcgen05 tensor cores (split TF32, see k_corr_tc.cu).
 // B is given pre-split (B = Bhi + Blo).  Requires corr_tc_supported().

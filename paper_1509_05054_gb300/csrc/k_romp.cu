@@ -17,32 +17,38 @@
 //     the FP16 roundings leave an error of about 2^-21 ||r|| ||d_j|| per
 //     correlation -- the accuracy class of FP32 Batch-OMP.  alpha0 is step 0 of
 //     the same product and never leaves the chip.
-//   * One thread per signal ("owner") reads its TMEM row (tcgen05.ld 32x32b,
-//     its lane), takes the argmax of |alpha| with the lowest index among equal
-//     values (16-column keys as in omp_common.cuh, chunks in ascending order),
-//     computes alpha_sel = d_sel^T r in FP32 from D's shared-memory parts
-//     (hi + lo, 22 significant bits), extends B = L^-1 (the inverse Cholesky
-//     factor of G_I, Gram entries from G), and updates
-//     r^(k+1) = r^(k) - D_I (gamma^(k+1) - gamma^(k)) in FP32 in one rolled loop
-//     over the selected atoms (kept with the step's coefficient changes in a
-//     per-thread shared-memory scratch: one copy of that code, not one per
-//     step, keeps the kernel small enough for the instruction cache).  The
-//     stop rules and the FP64 re-solve hand-off are those of Batch-OMP: max
-//     |alpha| = 0, residual energy <= kResidRel ||y||^2, a Cholesky pivot below
-//     kPivotMin (the signal goes to omp_resolve64).
+//   * Two threads per signal ("halves", the same lane of two warps) read its
+//     TMEM row (tcgen05.ld 32x32b, its lane), each half 128 of every
+//     accumulator unit's 256 columns, and take the argmax of |alpha| with the
+//     lowest index among equal values (16-column keys as in omp_common.cuh,
+//     chunks in ascending order; the halves' bests are exchanged through
+//     shared memory).  Each half holds 32 of the residual's 64 elements and
+//     computes its part of alpha_sel = d_sel^T r in FP32 from D's
+//     shared-memory parts (hi + lo, 22 significant bits).  The lead half
+//     extends B = L^-1 (the inverse Cholesky factor of G_I, Gram entries from
+//     G) and writes the step's coefficient changes; both halves then update
+//     their elements of r^(k+1) = r^(k) - D_I (gamma^(k+1) - gamma^(k)) in FP32
+//     in one rolled loop over the selected atoms (one copy of that code, not
+//     one per step, keeps the kernel small enough for the instruction cache).
+//     The stop rules and the FP64 re-solve hand-off are those of Batch-OMP:
+//     max |alpha| = 0, residual energy <= kResidRel ||y||^2, a Cholesky pivot
+//     below kPivotMin (the signal goes to omp_resolve64).
 //   * A persistent CTA per SM keeps two tiles in flight (slots): while the
 //     owners of one slot sweep and update, the tensor core computes the other
 //     slot's correlations.  TMEM holds two 256-column accumulator units; a step
 //     of a 512-atom problem uses both (the sweep of the first overlaps the MMAs
 //     of the second), a step with n <= 256 uses one, alternating.
 //
-// Warp roles (256 threads, two warps per SM sub-partition, so up to 255
-// registers a thread): warps 0-3 own slot 0, warps 4-7 slot 1 (warp w reads
-// TMEM lanes 32 (w mod 4) ..); thread 0 of a slot's first warp issues the
-// slot's MMAs once the slot's four warps have written their residuals (a named
-// barrier per slot).  mbarriers: tfull[u] (tcgen05.commit -> owners) and
+// Warp roles (512 threads, four warps per SM sub-partition, so up to 128
+// registers a thread): warps 0-7 hold slot 0, warps 8-15 slot 1; within a
+// slot, warps 0-3 are the lead halves and warps 4-7 the other halves of the
+// same 128 signals (warp w reads TMEM lanes 32 (w mod 4) ..).  Thread 0 of a
+// slot's first warp issues the slot's MMAs once the slot's eight warps have
+// written their residuals (a named barrier per slot); the two warps of a
+// signal quad meet at a named barrier of their own for each exchange.
+// mbarriers: tfull[u] (tcgen05.commit -> owners) and
 // tempty[u] (owners -> the next use of accumulator unit u).  The uses of the
-// units follow one fixed order (round, step, slot, half); before waiting for
+// units follow one fixed order (round, step, slot, unit); before waiting for
 // its own tfull phase an owner waits for the unit's previous use to have been
 // read, which makes every parity wait unambiguous.  Every wait is bounded
 // (about 2 s); a timeout sets ERR_TIMEOUT and the kernel unwinds and frees its
@@ -65,9 +71,12 @@ constexpr int RT_ROWB = 128;              // bytes of one FP16 row, p <= 64 padd
 constexpr int RT_NMAX = 2 * RT_N;         // atoms
 constexpr int RT_PMAX = 64;
 constexpr int RT_NS = 2;                  // tiles in flight
-constexpr int RT_OWNER_WARPS = 4 * RT_NS;
+constexpr int RT_HALVES = 2;              // threads per signal
+constexpr int RT_OWNER_WARPS = 4 * RT_NS * RT_HALVES;
 constexpr int RT_THREADS = 32 * RT_OWNER_WARPS;
+constexpr int RT_SIGS = RT_M * RT_NS;     // signals in flight per CTA
 constexpr int RT_SMAX = 8;
+constexpr int RT_PH = RT_PMAX / RT_HALVES;  // residual elements a thread holds
 // kind::f16: D F32 (bits 4-5 = 1), A and B F16 (format 0), K-major, N = 256, M = 128
 constexpr uint32_t RT_IDESC =
     (1u << 4) | ((uint32_t)(RT_N >> 3) << 17) | ((uint32_t)(RT_M >> 4) << 24);
@@ -83,9 +92,14 @@ struct RtSmem {
   static constexpr size_t a_slot = 2 * a_part;
   static constexpr size_t bars = a + RT_NS * a_slot;
   static constexpr size_t misc = bars + 8 * RB_COUNT;               // tmem slot, fail, max|D|
-  static constexpr size_t scratch = misc + 64;                      // per thread: I, dg
-  static constexpr size_t dyn = scratch + 2 * RT_SMAX * RT_THREADS * 4 + 1024;
+  // per signal (element q at q * RT_SIGS + signal): I (u16), dg and gamma
+  static constexpr size_t is = misc + 64;
+  static constexpr size_t dg = is + (size_t)RT_SMAX * RT_SIGS * 2;
+  static constexpr size_t gm = dg + (size_t)RT_SMAX * RT_SIGS * 4;
+  static constexpr size_t xch = gm + (size_t)RT_SMAX * RT_SIGS * 4;  // per signal and half
+  static constexpr size_t dyn = xch + (size_t)RT_SIGS * RT_HALVES * 20 + 1024;
 };
+static_assert(RtSmem::dyn <= 232448, "shared memory of one CTA");
 
 // Byte offset of 16-byte unit g (FP16 elements 8g .. 8g+7) of row r in a
 // K-major tile with the 128-byte swizzle (8-row groups of 1024 bytes).
@@ -93,29 +107,21 @@ __device__ __forceinline__ uint32_t sw_off(int r, int g) {
   return (uint32_t)(r * RT_ROWB + ((g ^ (r & 7)) << 4));
 }
 
-// 32 consecutive TMEM columns of this warp's lanes, without the wait.
-__device__ __forceinline__ void tm_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 consecutive TMEM columns of this warp's lanes, without the wait.
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
-// Completion of this thread's TMEM loads, with the registers of the last one
-// tied to the wait so that no use of them is scheduled before it.
-__device__ __forceinline__ void tm_wait32(uint32_t (&r)[32]) {
+__device__ __forceinline__ void tm_wait16(uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
                : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
                  "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
-                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
-                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
-                 "+r"(r[30]), "+r"(r[31])
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
                :
                : "memory");
 }
@@ -153,36 +159,43 @@ __device__ __forceinline__ float pow2i(int e) {
 
 // Argmax key of 16 columns: |alpha| with the low 4 mantissa bits replaced by
 // (15 - t), so the float maximum of the keys is the largest |alpha| and, among
-// values equal to within 2^-19 relative, the lowest column t.
+// values equal to within 2^-19 relative, the lowest column t.  Two interleaved
+// running maxima keep few keys live at once.
 __device__ __forceinline__ float chunk_key(const uint32_t* v) {
-  float k[17];
-#pragma unroll
-  for (int t = 0; t < 16; ++t) k[t] = __uint_as_float((v[t] & 0x7FFFFFF0u) | (uint32_t)(15 - t));
-  k[16] = 0.f;
-  return omp::max_tree<17>(k);
+  auto key = [&](int t) { return __uint_as_float((v[t] & 0x7FFFFFF0u) | (uint32_t)(15 - t)); };
+  float m = omp::fmax3(key(0), key(1), key(2));
+  float q = omp::fmax3(key(3), key(4), key(5));
+  m = omp::fmax3(m, key(6), key(7));
+  q = omp::fmax3(q, key(8), key(9));
+  m = omp::fmax3(m, key(10), key(11));
+  q = omp::fmax3(q, key(12), key(13));
+  m = omp::fmax3(m, key(14), key(15));
+  return fmaxf(m, q);
 }
-
 
 // Position of B_qj (j <= q) in the packed lower triangle.
 __host__ __device__ constexpr int tri(int q, int j) { return q * (q + 1) / 2 + j; }
 
-// One signal's OMP state, held by its owner thread; the selected atoms and
-// the coefficient changes of the current step live in the thread's column of
-// a shared-memory scratch (Is, dgs: element q at q * RT_THREADS + thread), so
-// that the residual update is one rolled loop rather than a copy per step.
+// One signal's OMP state as its two threads ("halves") hold it.  Half hf
+// holds the 16-byte units g = 2u + hf (u < 4) of the residual, elements 8g ..
+// 8g+7.  Half 0 (the lead) also holds B and the stop rule's energies and runs
+// the Cholesky step; it writes the step's atom, the coefficient changes and
+// gamma to the signal's column of a shared-memory scratch (element q at
+// q * RT_SIGS + signal), from which both halves update their residual
+// elements in one rolled loop (one copy of that code, not one per step, keeps
+// the kernel small enough for the instruction cache).
 struct Owner {
-  float2 r[RT_PMAX / 2];      // residual r^(k), FP32 pairs (packed FMAs), zero past p
-  float B[RT_SMAX * (RT_SMAX + 1) / 2];  // B = L^-1, lower triangle by rows (L L^T = G_I)
-  float gam[RT_SMAX];         // coefficients gamma^(k)
-  float yy;                   // ||y||^2
-  float rr;                   // ||y||^2 - sum z_q^2 (the stop rule's residual energy)
+  float2 r[RT_PH / 2];        // this half of r^(k), FP32 pairs (packed FMAs), zero past p
+  float B[RT_SMAX * (RT_SMAX + 1) / 2];  // lead: B = L^-1, lower triangle by rows (L L^T = G_I)
+  float yy;                   // lead: ||y||^2
+  float rr;                   // lead: ||y||^2 - sum z_q^2 (the stop rule's residual energy)
   float rn;                   // ||r||^2 of the stored residual (its FP16 scale)
-  int k;                      // atoms selected
+  int k;                      // lead: atoms selected
   bool active;                // still selecting
 };
 
-// Row j of D from the shared-memory FP16 parts, 16-byte unit g (elements
-// 8g .. 8g+7): D_j 2^eD = hi + lo.
+// Unit g of row j of D from the shared-memory FP16 parts (elements 8g ..
+// 8g+7): D_j 2^eD = hi + lo.
 __device__ __forceinline__ void row_unit(const uint8_t* Dh, const uint8_t* Dl, int j, int g,
                                          float2 (&h)[4], float2 (&l)[4]) {
   const uint4 a = *reinterpret_cast<const uint4*>(Dh + sw_off(j, g));
@@ -199,17 +212,18 @@ __device__ __forceinline__ void row_unit(const uint8_t* Dh, const uint8_t* Dl, i
 
 // Step STEP of one signal after the argmax chose atom sel and alpha_sel =
 // d_sel^T r^(k) is known (Batch-OMP's progressive Cholesky in the
-// inverse-factor form):
+// inverse-factor form), run by the lead:
 //   w = B g with g_q = G[I_q][sel] (the new row of L), delta = G[sel][sel] - ||w||^2;
 //   c = 1/sqrt(delta), z = alpha_sel c; row STEP of B: B_kj = -c sum_{q>=j} w_q B_qj,
 //   B_kk = c; dg = z B_k,: (the change of gamma), gamma += dg.
-// Writes I_STEP = sel and dg to the thread's scratch.  Returns true when the
-// residual is to be updated (r -= D_I dg) for a further step.  A pivot delta <=
-// kPivotMin stops the signal and lists it for the FP64 re-solve, as in omp_one.
+// Writes I_STEP = sel, dg and gamma to the signal's scratch column.  Returns
+// true when the residual is to be updated (r -= D_I dg) for a further step.  A
+// pivot delta <= kPivotMin stops the signal and lists it for the FP64
+// re-solve, as in omp_one.
 template <int STEP>
 __device__ __forceinline__ bool owner_chol(Owner& o, int sel, float asel, float gss,
-                                           const float (&g)[RT_SMAX], int* Is, float* dgs,
-                                           int s, int64_t i, int* __restrict__ err,
+                                           const float (&g)[RT_SMAX], uint16_t* Is, float* dgs,
+                                           float* gms, int s, int64_t i, int* __restrict__ err,
                                            int* __restrict__ rs_list, int* __restrict__ rs_count,
                                            int rs_cap) {
   float w[STEP > 0 ? STEP : 1];
@@ -243,13 +257,13 @@ __device__ __forceinline__ bool owner_chol(Owner& o, int sel, float asel, float 
     for (int q = j; q < STEP; ++q) acc = fmaf(w[q], o.B[tri(q, j)], acc);
     o.B[tri(STEP, j)] = -c * acc;
     const float dg = z * o.B[tri(STEP, j)];
-    dgs[j * RT_THREADS] = dg;
-    o.gam[j] += dg;
+    dgs[j * RT_SIGS] = dg;
+    gms[j * RT_SIGS] += dg;
   }
   o.B[tri(STEP, STEP)] = c;
-  dgs[STEP * RT_THREADS] = z * c;
-  o.gam[STEP] = z * c;
-  Is[STEP * RT_THREADS] = sel;
+  dgs[STEP * RT_SIGS] = z * c;
+  gms[STEP * RT_SIGS] = z * c;
+  Is[STEP * RT_SIGS] = (uint16_t)sel;
   o.k = STEP + 1;
   o.rr = fmaf(-z, z, o.rr);
   if (STEP + 1 >= s || STEP + 1 >= RT_SMAX || o.rr <= kResidRel * o.yy) {
@@ -259,16 +273,16 @@ __device__ __forceinline__ bool owner_chol(Owner& o, int sel, float asel, float 
   return true;
 }
 
-// d_j^T r for atom j, from the shared-memory parts (D = (hi + lo) 2^-eD, exact
-// to about 2^-22 relative; no global-memory latency on the step's chain), in
-// units of 2^-eD.
-__device__ __forceinline__ float owner_dot(const Owner& o, int j, const uint8_t* Dh,
+// This half's part of d_j^T r for atom j, from the shared-memory parts (D =
+// (hi + lo) 2^-eD, exact to about 2^-22 relative; no global-memory latency on
+// the step's chain), in units of 2^-eD.
+__device__ __forceinline__ float owner_dot(const Owner& o, int j, int hf, const uint8_t* Dh,
                                            const uint8_t* Dl) {
   float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int u = 0; u < RT_PMAX / 8; ++u) {
+  for (int u = 0; u < RT_PH / 8; ++u) {
     float2 h[4], l[4];
-    row_unit(Dh, Dl, j, u, h, l);
+    row_unit(Dh, Dl, j, 2 * u + hf, h, l);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       a0 = __ffma2_rn(o.r[4 * u + e], h[e], a0);
@@ -278,28 +292,29 @@ __device__ __forceinline__ float owner_dot(const Owner& o, int j, const uint8_t*
   return (a0.x + a0.y) + (a1.x + a1.y);
 }
 
-// ||r||^2 of the residual, packed.
+// This half's part of ||r||^2, packed.
 __device__ __forceinline__ float owner_norm2(const Owner& o) {
   float2 n = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int e = 0; e < RT_PMAX / 2; ++e) n = __ffma2_rn(o.r[e], o.r[e], n);
+  for (int e = 0; e < RT_PH / 2; ++e) n = __ffma2_rn(o.r[e], o.r[e], n);
   return n.x + n.y;
 }
 
-// r^(k+1) = r^(k) - sum_{j <= step} dg_j d_{I_j} (atoms from the shared-memory
-// parts, scaled back by 2^-eD), and ||r^(k+1)||^2.  One rolled loop over atoms;
-// packed FP32x2 multiply-adds.
-__device__ __forceinline__ void owner_update(Owner& o, int step, const int* Is, const float* dgs,
-                                             const uint8_t* Dh, const uint8_t* Dl, float dsc) {
+// r^(k+1) = r^(k) - sum_{j <= step} dg_j d_{I_j} on this half's elements (atoms
+// from the shared-memory parts, scaled back by 2^-eD); returns this half's part
+// of ||r^(k+1)||^2.  One rolled loop over atoms; packed FP32x2 multiply-adds.
+__device__ __forceinline__ float owner_update(Owner& o, int step, int hf, const uint16_t* Is,
+                                              const float* dgs, const uint8_t* Dh,
+                                              const uint8_t* Dl, float dsc) {
 #pragma unroll 1
   for (int j = 0; j <= step; ++j) {
-    const int a = Is[j * RT_THREADS];
-    const float nd = -dgs[j * RT_THREADS] * dsc;
+    const int a = Is[j * RT_SIGS];
+    const float nd = -dgs[j * RT_SIGS] * dsc;
     const float2 nd2 = make_float2(nd, nd);
 #pragma unroll
-    for (int u = 0; u < RT_PMAX / 8; ++u) {
+    for (int u = 0; u < RT_PH / 8; ++u) {
       float2 h[4], l[4];
-      row_unit(Dh, Dl, a, u, h, l);
+      row_unit(Dh, Dl, a, 2 * u + hf, h, l);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         o.r[4 * u + e] = __ffma2_rn(nd2, h[e], o.r[4 * u + e]);
@@ -307,44 +322,47 @@ __device__ __forceinline__ void owner_update(Owner& o, int step, const int* Is, 
       }
     }
   }
-  o.rn = owner_norm2(o);
+  return owner_norm2(o);
 }
 
-// The signal's residual as FP16 parts, scaled by 2^er with ||r|| 2^er < 2^14,
-// into row `row` of the slot's two K-major tiles.
-__device__ __forceinline__ void owner_store(const Owner& o, uint8_t* Ah, uint8_t* Al, int row) {
+// This half of the signal's residual as FP16 parts, scaled by 2^er with
+// ||r|| 2^er < 2^14 (o.rn: the whole residual's ||r||^2), into row `row` of the
+// slot's two K-major tiles.
+__device__ __forceinline__ void owner_store(const Owner& o, int hf, uint8_t* Ah, uint8_t* Al,
+                                            int row) {
   int E = 0;
   frexpf(sqrtf(o.rn), &E);
   const float sc = o.rn > 0.f ? pow2i(14 - E) : 1.f;
   const float2 sc2 = make_float2(sc, sc), m1 = make_float2(-1.f, -1.f);
   const float2 k2 = make_float2(8193.f, 8193.f);
 #pragma unroll
-  for (int g = 0; g < RT_PMAX / 8; ++g) {
+  for (int u = 0; u < RT_PH / 8; ++u) {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       // split2 with packed operations: c = 8193 v, hi = c - (c - v), lo = v - hi
       // (each subtraction one FMA with -1: a single rounding, as __fsub_rn)
-      const float2 v = __fmul2_rn(o.r[4 * g + e], sc2);
+      const float2 v = __fmul2_rn(o.r[4 * u + e], sc2);
       const float2 c = __fmul2_rn(v, k2);
       const float2 hi = __ffma2_rn(__ffma2_rn(v, m1, c), m1, c);
       const float2 lo = __ffma2_rn(hi, m1, v);
       h[e] = pack_f16x2(hi.x, hi.y);
       l[e] = pack_f16x2(lo.x, lo.y);
     }
+    const int g = 2 * u + hf;
     *reinterpret_cast<uint4*>(Ah + sw_off(row, g)) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(Al + sw_off(row, g)) = make_uint4(l[0], l[1], l[2], l[3]);
   }
 }
 
 // The signal's support in ascending atom order (slots i*s ..), -1 padding, and its count.
-__device__ __forceinline__ void owner_write(const Owner& o, const int* Is, int64_t i, int s,
-                                            int32_t* __restrict__ oidx, float* __restrict__ oval,
-                                            int32_t* __restrict__ ocnt) {
+__device__ __forceinline__ void owner_write(const Owner& o, const uint16_t* Is, const float* gms,
+                                            int64_t i, int s, int32_t* __restrict__ oidx,
+                                            float* __restrict__ oval, int32_t* __restrict__ ocnt) {
   const int64_t base = i * s;
   int I[RT_SMAX];
 #pragma unroll
-  for (int q = 0; q < RT_SMAX; ++q) I[q] = q < o.k ? Is[q * RT_THREADS] : 0;
+  for (int q = 0; q < RT_SMAX; ++q) I[q] = q < o.k ? (int)Is[q * RT_SIGS] : 0;
 #pragma unroll
   for (int q = 0; q < RT_SMAX; ++q) {
     if (q < o.k) {
@@ -352,7 +370,7 @@ __device__ __forceinline__ void owner_write(const Owner& o, const int* Is, int64
 #pragma unroll
       for (int t = 0; t < RT_SMAX; ++t) rank += (t < o.k && I[t] < I[q]) ? 1 : 0;
       oidx[base + rank] = I[q];
-      oval[base + rank] = o.gam[q];
+      oval[base + rank] = gms[q * RT_SIGS];
     } else if (q < s) {
       oidx[base + q] = -1;
       oval[base + q] = 0.f;
@@ -375,31 +393,36 @@ __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, vol
   return true;
 }
 
-// The sweep of one accumulator unit (256 columns = atoms 256 h ..): running
-// best key and its 16-column chunk, chunks in ascending order (the lowest
-// chunk wins equal keys).  Warp-collective: every lane executes it.
-__device__ __forceinline__ void sweep_unit(uint32_t ta, int h, float& best, int& bc) {
-  uint32_t va[32], vb[32];
-  tm_ld32(ta, va);
-  tm_wait32(va);
+// This half's sweep of one accumulator unit: its 128 columns (atoms 256 h +
+// 128 hf ..) as eight 16-column chunks in ascending order, keeping the running
+// best key and its chunk (global chunk index; the lowest chunk wins equal
+// keys).  Warp-collective: every lane executes it.
+__device__ __forceinline__ void sweep_half(uint32_t ta, int h, int hf, float& best, int& bc) {
+  constexpr int NC = RT_N / RT_HALVES / 16;
+  const int cb = 16 * h + NC * hf;
+  uint32_t va[16], vb[16];
+  tm_ld16(ta, va);
 #pragma unroll
-  for (int c = 0; c < RT_N / 32; ++c) {
-    const int c0 = 16 * h + 2 * c;
-    if (c & 1) {
-      if (c + 1 < RT_N / 32) tm_ld32(ta + 32 * (c + 1), va);
-      const float k0 = chunk_key(vb), k1 = chunk_key(vb + 16);
-      if (k0 > best) { best = k0; bc = c0; }
-      if (k1 > best) { best = k1; bc = c0 + 1; }
-      if (c + 1 < RT_N / 32) tm_wait32(va);
-    } else {
-      if (c + 1 < RT_N / 32) tm_ld32(ta + 32 * (c + 1), vb);
-      const float k0 = chunk_key(va), k1 = chunk_key(va + 16);
-      if (k0 > best) { best = k0; bc = c0; }
-      if (k1 > best) { best = k1; bc = c0 + 1; }
-      if (c + 1 < RT_N / 32) tm_wait32(vb);
-    }
+  for (int c = 0; c < NC; c += 2) {  // two loads in flight
+    tm_ld16(ta + 16 * (c + 1), vb);
+    tm_wait16(va);
+    const float k0 = chunk_key(va);
+    if (k0 > best) { best = k0; bc = cb + c; }
+    if (c + 2 < NC) tm_ld16(ta + 16 * (c + 2), va);
+    tm_wait16(vb);
+    const float k1 = chunk_key(vb);
+    if (k1 > best) { best = k1; bc = cb + c + 1; }
   }
 }
+
+// Pair exchange record of one half of a signal.
+struct Xch {
+  float key;   // best argmax key of the half's columns (-2: failed wait)
+  int chunk;   // its chunk
+  float dot;   // half 1: its part of d_sel^T r; both: their parts of ||y||^2
+  float nrm;   // the half's part of ||r^(k+1)||^2
+  int more;    // lead: the Cholesky step's outcome (1: update and go on)
+};
 
 __global__ void __launch_bounds__(RT_THREADS, 1)
     romp_kernel(const float* __restrict__ Y, int64_t m, int p, const float* __restrict__ D, int n,
@@ -424,7 +447,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
     *dmax = 0u;
     for (int u = 0; u < 2; ++u) {
       mbar_init(&bars[RB_TFULL + u], 1);
-      mbar_init(&bars[RB_TEMPTY + u], 4);
+      mbar_init(&bars[RB_TEMPTY + u], 4 * RT_HALVES);  // the slot's warps
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -476,21 +499,29 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   {
-    // ---------------- owners: one signal per thread ----------------
-    const int sl = warp >> 2, quad = warp & 3, row = quad * 32 + lane;
-    const bool issuer = quad == 0 && lane == 0;
-    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+    // ---------------- owners: two threads (halves) per signal ----------------
+    const int sl = warp >> 3, hf = (warp >> 2) & 1, quad = warp & 3, row = quad * 32 + lane;
+    const bool issuer = hf == 0 && quad == 0 && lane == 0;
+    const bool lead = hf == 0;  // the half that runs the Cholesky step and writes the results
+    const int pair_bar = 1 + RT_NS + sl * 4 + quad;  // the quad's two warps
+    const int sig = sl * RT_M + row;                 // the signal's scratch column
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(hf * (RT_N / 2));
     uint8_t* Ah = base + RtSmem::a + sl * RtSmem::a_slot;
     uint8_t* Al = Ah + RtSmem::a_part;
     const uint8_t* Dh = base + RtSmem::dh;
     const uint8_t* Dl = base + RtSmem::dl;
-    int* Is = (int*)(base + RtSmem::scratch) + threadIdx.x;  // this thread's column
-    float* dgs = (float*)(base + RtSmem::scratch) + RT_SMAX * RT_THREADS + threadIdx.x;
-    const uint64_t dhd = sw128_desc(base + RtSmem::dh), dld = sw128_desc(base + RtSmem::dl);
-    const uint64_t ahd = sw128_desc(Ah), ald = sw128_desc(Al);
+    uint16_t* Is = (uint16_t*)(base + RtSmem::is) + sig;
+    float* dgs = (float*)(base + RtSmem::dg) + sig;
+    float* gms = (float*)(base + RtSmem::gm) + sig;
+    Xch* xme = (Xch*)(base + RtSmem::xch) + sig * RT_HALVES + hf;
+    const Xch* xpa = (const Xch*)(base + RtSmem::xch) + sig * RT_HALVES + (hf ^ 1);
+    // Per step the halves meet at the slot barrier and at four pair barriers:
+    // X1 (argmax keys), X2 (half 1's part of alpha_sel), X4 (the lead's
+    // Cholesky outcome) and X3 (the parts of ||r||^2).  An exchange field is
+    // rewritten only after a barrier that the reader passes after reading it.
     // After a failed wait (*fail set) the loops still run to their end with the
-    // work skipped, so that the four warps of a slot always meet at the same
-    // named barriers.
+    // work skipped, so that the warps of a slot and the two halves of a signal
+    // always meet at the same named barriers.
     for (int j = 0; j < rounds; ++j) {
       const int64_t v = (int64_t)j * RT_NS + sl;
       if (v >= ntb) break;  // this slot has no tile in the CTA's last round (slot-uniform)
@@ -500,30 +531,45 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       o.active = i < m;
       o.k = 0;
       {
-        const float4* yp = reinterpret_cast<const float4*>(Y + (size_t)(o.active ? i : 0) * p);
+        const float* yp = Y + (size_t)(o.active ? i : 0) * p;
 #pragma unroll
-        for (int q = 0; q < RT_PMAX / 4; ++q) {
-          const float4 t = (o.active && 4 * q < p) ? __ldg(yp + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-          o.r[2 * q] = make_float2(t.x, t.y);
-          o.r[2 * q + 1] = make_float2(t.z, t.w);
+        for (int u = 0; u < RT_PH / 8; ++u) {
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int c = 8 * (2 * u + hf) + 4 * q;
+            const float4 t = (o.active && c < p) ? __ldg(reinterpret_cast<const float4*>(yp + c))
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+            o.r[4 * u + 2 * q] = make_float2(t.x, t.y);
+            o.r[4 * u + 2 * q + 1] = make_float2(t.z, t.w);
+          }
         }
       }
-      o.yy = o.rr = o.rn = owner_norm2(o);
+      if (lead) {
+#pragma unroll
+        for (int q = 0; q < RT_SMAX; ++q) gms[q * RT_SIGS] = 0.f;
+      }
+      {  // ||y||^2: the halves' parts (a sum of two terms: the same in both halves),
+         // through the dot fields, which were last read before the previous X4
+        const float mine = owner_norm2(o);
+        xme->dot = mine;
+        asm volatile("bar.sync %0, %1;" ::"r"(pair_bar), "r"(64) : "memory");
+        o.yy = o.rr = o.rn = mine + xpa->dot;
+      }
       if (!isfinite(o.yy)) {
-        atomicOr(err, ERR_NONFINITE);
+        if (lead) atomicOr(err, ERR_NONFINITE);
         o.active = false;
 #pragma unroll
-        for (int e = 0; e < RT_PMAX / 2; ++e) o.r[e] = make_float2(0.f, 0.f);
+        for (int e = 0; e < RT_PH / 2; ++e) o.r[e] = make_float2(0.f, 0.f);
         o.rn = 0.f;
       }
-#pragma unroll
-      for (int q = 0; q < RT_SMAX; ++q) o.gam[q] = 0.f;
       for (int step = 0; step < s; ++step) {
-        if (step == 0 || o.active) owner_store(o, Ah, Al, row);
+        if (step == 0 || o.active) owner_store(o, hf, Ah, Al, row);
         fence_async_smem();  // the residual rows -> the tensor core's reads
-        asm volatile("bar.sync %0, %1;" ::"r"(1 + sl), "r"(128) : "memory");
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + sl), "r"(32 * 4 * RT_HALVES) : "memory");
         const int u = j * s * RT_NS + step * aj + sl;  // this use's place in the fixed order
         if (issuer && !*fail) {
+          const uint64_t dhd = sw128_desc(base + RtSmem::dh), dld = sw128_desc(base + RtSmem::dl);
+          const uint64_t ahd = sw128_desc(Ah), ald = sw128_desc(Al);
           for (int h = 0; h < nh; ++h) {
             const int hc = u * nh + h, unit = hc & 1;
             if (hc >= 2 && !wait_or_fail(&bars[RB_TEMPTY + unit], (uint32_t)(((hc >> 1) - 1) & 1), fail))
@@ -558,44 +604,81 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
           good = __all_sync(omp::FULL, w);
           if (!good) continue;
           tc_fence_after();
-          sweep_unit(tl + (uint32_t)(unit * RT_N), h, best, bc);
+          sweep_half(tl + (uint32_t)(unit * RT_N), h, hf, best, bc);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&bars[RB_TEMPTY + unit]);
         }
-        if (good && o.active) {
-          const uint32_t kb = __float_as_uint(best);
-          const int sel = 16 * bc + 15 - (int)(kb & 15u);
-          if ((kb & 0x7FFFFFF0u) == 0u || sel >= n) {
-            o.active = false;  // max |alpha| = 0
-          } else {
-            // the Gram entries first: their latency overlaps the dot product
-            const float gss = __ldg(G + (size_t)sel * n + sel);
-            float g[RT_SMAX];
-#pragma unroll
-            for (int q = 0; q < RT_SMAX; ++q)
-              g[q] = q < step ? __ldg(G + (size_t)Is[q * RT_THREADS] * n + sel) : 0.f;
-            const float asel = owner_dot(o, sel, Dh, Dl) * dsc;
-            bool more = false;
-            switch (step) {
-#define DL_ROMP_STEP(S)                                                                       \
-  case S:                                                                                     \
-    more = owner_chol<S>(o, sel, asel, gss, g, Is, dgs, s, i, err, rs_list, rs_count, rs_cap); \
-    break;
-              DL_ROMP_STEP(0) DL_ROMP_STEP(1) DL_ROMP_STEP(2) DL_ROMP_STEP(3)
-              DL_ROMP_STEP(4) DL_ROMP_STEP(5) DL_ROMP_STEP(6) DL_ROMP_STEP(7)
-#undef DL_ROMP_STEP
-              default: break;
-            }
-            if (more) owner_update(o, step, Is, dgs, Dh, Dl, dsc);
+        // X1: the halves' best keys; equal keys go to the lower chunk
+        xme->key = good ? best : -2.f;
+        xme->chunk = bc;
+        asm volatile("bar.sync %0, %1;" ::"r"(pair_bar), "r"(64) : "memory");
+        {
+          const float pk = xpa->key;
+          const int pc = xpa->chunk;
+          good = good && pk > -1.5f;
+          if (pk > best || (pk == best && pc < bc)) {
+            best = pk;
+            bc = pc;
           }
         }
+        bool pick = good && o.active;
+        int sel = 0;
+        if (pick) {
+          const uint32_t kb = __float_as_uint(best);
+          sel = 16 * bc + 15 - (int)(kb & 15u);
+          if ((kb & 0x7FFFFFF0u) == 0u || sel >= n) {
+            o.active = false;  // max |alpha| = 0
+            pick = false;
+          }
+        }
+        float gss = 0.f, dpart = 0.f;
+        float g[RT_SMAX];
+        if (pick) {
+          if (lead) {  // the Gram entries first: their latency overlaps the dot product
+            gss = __ldg(G + (size_t)sel * n + sel);
+#pragma unroll
+            for (int q = 0; q < RT_SMAX; ++q)
+              g[q] = q < step ? __ldg(G + (size_t)Is[q * RT_SIGS] * n + sel) : 0.f;
+          }
+          dpart = owner_dot(o, sel, hf, Dh, Dl);
+        }
+        // X2: half 1's part of alpha_sel to the lead
+        if (!lead) xme->dot = dpart;
+        asm volatile("bar.sync %0, %1;" ::"r"(pair_bar), "r"(64) : "memory");
+        bool more = false;
+        if (pick && lead) {
+          const float asel = (dpart + xpa->dot) * dsc;
+          switch (step) {
+#define DL_ROMP_STEP(S)                                                                    \
+  case S:                                                                                  \
+    more = owner_chol<S>(o, sel, asel, gss, g, Is, dgs, gms, s, i, err, rs_list, rs_count, \
+                         rs_cap);                                                          \
+    break;
+            DL_ROMP_STEP(0) DL_ROMP_STEP(1) DL_ROMP_STEP(2) DL_ROMP_STEP(3)
+            DL_ROMP_STEP(4) DL_ROMP_STEP(5) DL_ROMP_STEP(6) DL_ROMP_STEP(7)
+#undef DL_ROMP_STEP
+            default: break;
+          }
+          xme->more = more ? 1 : 0;
+        }
+        // X4: the lead's Cholesky outcome (and its scratch writes) to half 1
+        asm volatile("bar.sync %0, %1;" ::"r"(pair_bar), "r"(64) : "memory");
+        if (pick && !lead) {
+          more = xpa->more != 0;
+          o.active = more;
+        }
+        float npart = 0.f;
+        if (more) npart = owner_update(o, step, hf, Is, dgs, Dh, Dl, dsc);
         if (!good) o.active = false;
+        // X3: ||r^(k+1)||^2 from the halves' parts
+        xme->nrm = npart;
+        asm volatile("bar.sync %0, %1;" ::"r"(pair_bar), "r"(64) : "memory");
+        if (more) o.rn = npart + xpa->nrm;
       }
-      if (!*fail && i < m) owner_write(o, Is, i, s, oidx, oval, ocnt);
+      if (lead && !*fail && i < m) owner_write(o, Is, gms, i, s, oidx, oval, ocnt);
     }
   }
-
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
