@@ -132,14 +132,6 @@ __device__ __forceinline__ uint32_t pack_f16x2(float v0, float v1) {
   asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v1), "f"(v0));
   return d;
 }
-// The two FP16 halves of a 32-bit word as FP32 (exact), the low half first.
-__device__ __forceinline__ void unpack_f16x2(uint32_t u, float& v0, float& v1) {
-  asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
-      "cvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
-      : "=f"(v0), "=f"(v1)
-      : "r"(u));
-}
-
 // Split 2^e-scaled FP32 values into FP16 parts: v = hi + lo + O(2^-22 |v|).
 // hi = v rounded to 11 significant bits (Veltkamp's splitting with 2^13 + 1),
 // lo = v - hi exactly; both then convert to FP16 without further rounding
@@ -194,20 +186,31 @@ struct Owner {
   bool active;                // still selecting
 };
 
+// (hi + lo) of two FP16 pairs as FP32: the two halves of word hw and of word
+// lw, the low halves first.  Exact: lo is the remainder of hi, so the sum has
+// at most 24 significant bits.  hi is converted, lo is added in the same
+// instruction (the mixed-precision add with an FP16 and an FP32 operand).
+__device__ __forceinline__ float2 hl_sum(uint32_t hw, uint32_t lw) {
+  float2 d;
+  asm("{\n\t.reg .f16 h0, h1, l0, l1;\n\t.reg .f32 f0, f1;\n\t"
+      "mov.b32 {h0, h1}, %2;\n\tmov.b32 {l0, l1}, %3;\n\t"
+      "cvt.f32.f16 f0, h0;\n\tcvt.f32.f16 f1, h1;\n\t"
+      "add.f32.f16 %0, l0, f0;\n\tadd.f32.f16 %1, l1, f1;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "r"(hw), "r"(lw));
+  return d;
+}
+
 // Unit g of row j of D from the shared-memory FP16 parts (elements 8g ..
-// 8g+7): D_j 2^eD = hi + lo.
+// 8g+7) as FP32 pairs: D_j 2^eD = hi + lo.
 __device__ __forceinline__ void row_unit(const uint8_t* Dh, const uint8_t* Dl, int j, int g,
-                                         float2 (&h)[4], float2 (&l)[4]) {
+                                         float2 (&d)[4]) {
   const uint4 a = *reinterpret_cast<const uint4*>(Dh + sw_off(j, g));
   const uint4 b = *reinterpret_cast<const uint4*>(Dl + sw_off(j, g));
-  unpack_f16x2(a.x, h[0].x, h[0].y);
-  unpack_f16x2(a.y, h[1].x, h[1].y);
-  unpack_f16x2(a.z, h[2].x, h[2].y);
-  unpack_f16x2(a.w, h[3].x, h[3].y);
-  unpack_f16x2(b.x, l[0].x, l[0].y);
-  unpack_f16x2(b.y, l[1].x, l[1].y);
-  unpack_f16x2(b.z, l[2].x, l[2].y);
-  unpack_f16x2(b.w, l[3].x, l[3].y);
+  d[0] = hl_sum(a.x, b.x);
+  d[1] = hl_sum(a.y, b.y);
+  d[2] = hl_sum(a.z, b.z);
+  d[3] = hl_sum(a.w, b.w);
 }
 
 // Step STEP of one signal after the argmax chose atom sel and alpha_sel =
@@ -281,13 +284,12 @@ __device__ __forceinline__ float owner_dot(const Owner& o, int j, int hf, const 
   float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
   for (int u = 0; u < RT_PH / 8; ++u) {
-    float2 h[4], l[4];
-    row_unit(Dh, Dl, j, 2 * u + hf, h, l);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      a0 = __ffma2_rn(o.r[4 * u + e], h[e], a0);
-      a1 = __ffma2_rn(o.r[4 * u + e], l[e], a1);
-    }
+    float2 d[4];
+    row_unit(Dh, Dl, j, 2 * u + hf, d);
+    a0 = __ffma2_rn(o.r[4 * u], d[0], a0);
+    a1 = __ffma2_rn(o.r[4 * u + 1], d[1], a1);
+    a0 = __ffma2_rn(o.r[4 * u + 2], d[2], a0);
+    a1 = __ffma2_rn(o.r[4 * u + 3], d[3], a1);
   }
   return (a0.x + a0.y) + (a1.x + a1.y);
 }
@@ -313,13 +315,10 @@ __device__ __forceinline__ float owner_update(Owner& o, int step, int hf, const 
     const float2 nd2 = make_float2(nd, nd);
 #pragma unroll
     for (int u = 0; u < RT_PH / 8; ++u) {
-      float2 h[4], l[4];
-      row_unit(Dh, Dl, a, 2 * u + hf, h, l);
+      float2 d[4];
+      row_unit(Dh, Dl, a, 2 * u + hf, d);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        o.r[4 * u + e] = __ffma2_rn(nd2, h[e], o.r[4 * u + e]);
-        o.r[4 * u + e] = __ffma2_rn(nd2, l[e], o.r[4 * u + e]);
-      }
+      for (int e = 0; e < 4; ++e) o.r[4 * u + e] = __ffma2_rn(nd2, d[e], o.r[4 * u + e]);
     }
   }
   return owner_norm2(o);
