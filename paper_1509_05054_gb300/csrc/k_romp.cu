@@ -399,18 +399,21 @@ __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, vol
 __device__ __forceinline__ void sweep_half(uint32_t ta, int h, int hf, float& best, int& bc) {
   constexpr int NC = RT_N / RT_HALVES / 16;
   const int cb = 16 * h + NC * hf;
+  // tcgen05.wait::ld waits for all of the thread's loads: the next chunk's
+  // load is issued before the current chunk's keys and waited for after them
   uint32_t va[16], vb[16];
   tm_ld16(ta, va);
+  tm_wait16(va);
 #pragma unroll
-  for (int c = 0; c < NC; c += 2) {  // two loads in flight
+  for (int c = 0; c < NC; c += 2) {
     tm_ld16(ta + 16 * (c + 1), vb);
-    tm_wait16(va);
     const float k0 = chunk_key(va);
     if (k0 > best) { best = k0; bc = cb + c; }
-    if (c + 2 < NC) tm_ld16(ta + 16 * (c + 2), va);
     tm_wait16(vb);
+    if (c + 2 < NC) tm_ld16(ta + 16 * (c + 2), va);
     const float k1 = chunk_key(vb);
     if (k1 > best) { best = k1; bc = cb + c + 1; }
+    if (c + 2 < NC) tm_wait16(va);
   }
 }
 
