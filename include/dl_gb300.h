@@ -351,7 +351,11 @@ int dl_get_config(dl_ctx* ctx, int* cfg4);
  *   0  Batch-OMP, one warp per signal, from stored correlations alpha0
  *   1  the same with the progressive-Cholesky vectors in TMEM
  *   2  residual-form OMP, the correlations D^T r of every step on the tensor
- *      cores (FP16 hi/lo parts, FP32 accumulation), no stored alpha0
+ *      cores (FP16 hi/lo parts, FP32 accumulation), no stored alpha0; taken
+ *      for plain FP32 calls with 256 < n <= 512, p <= 64, p % 4 == 0, s <= 8
+ *      and at least 3/4 of (SM count x 256) signals; the environment variable
+ *      DL_OMP_RES, read by dl_init, turns it off (0) or takes it for every
+ *      supported call (2)
  *   3  OMP restricted to proposed candidates (a proposer is attached)
  *  -1  no coding pass yet
  * written to *kind.  Returns DL_OK, or DL_EINVAL for a NULL argument.

@@ -363,9 +363,16 @@ cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D
 // alpha0 pass) serves the plain FP32 form without a proposer for n > 256; at
 // n <= 256 the alpha0 pass is half as costly and the TMEM Batch-OMP was faster
 // (p=64, n=256, s=6, m=2e4: 180 against 160 M signals/s per iteration).
-bool use_res(dl_ctx* c, const float* Y, const float* D, int s) {
-  return c->cfg_omp_res && !has_prop(c) && !lp_ok(c) && c->n > 256 &&
-         dlk::omp_res_supported(c->p, c->n, s, Y, D);
+// The residual-form OMP codes a call when it is supported and, in the automatic
+// mode, when n > 256 and the call has at least three quarters of one round of
+// tiles (both slots of most SMs busy): at n = 256, or with about one tile per
+// SM (p = 64, n = 512, m = 20000: 96 against 90 us for Gram, correlations and
+// the TMEM Batch-OMP), the Batch-OMP forms are as fast or faster.  Mode 2
+// (DL_OMP_RES=2) takes it for every supported call.
+bool use_res(dl_ctx* c, const float* Y, const float* D, int s, int64_t m) {
+  if (!c->cfg_omp_res || has_prop(c) || lp_ok(c) || !dlk::omp_res_supported(c->p, c->n, s, Y, D))
+    return false;
+  return c->cfg_omp_res == 2 || (c->n > 256 && 4 * m >= 3 * dlk::omp_res_round_signals());
 }
 
 cudaError_t enq_omp_res(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
@@ -388,7 +395,7 @@ cudaError_t enq_omp_res(dl_ctx* c, const float* Y, int64_t m, const float* D, in
 }
 
 cudaError_t enq_omp(dl_ctx* c, const float* Y, int64_t m, const float* D, int s) {
-  if (use_res(c, Y, D, s)) return enq_omp_res(c, Y, m, D, s);
+  if (use_res(c, Y, D, s, m)) return enq_omp_res(c, Y, m, D, s);
   const bool tc = tc_ok(c, Y, D);
   const bool learned = has_prop(c) && c->learned_now;
   // BF16 form: alpha0 is only as accurate as BF16 anyway, so it is stored in BF16
@@ -585,7 +592,7 @@ cudaError_t enq_omp_res_staged(dl_ctx* c, const float* hostY, const float* dY, i
 
 cudaError_t enq_omp_staged(dl_ctx* c, const float* hostY, const float* dY, int64_t m,
                            const float* D, int s, int* kernels) {
-  if (use_res(c, dY, D, s)) return enq_omp_res_staged(c, hostY, dY, m, D, s, kernels);
+  if (use_res(c, dY, D, s, m)) return enq_omp_res_staged(c, hostY, dY, m, D, s, kernels);
   const int64_t p = c->p;
   int64_t offs[dl_ctx::kChunks + 1];
   staged_pieces(m, offs);
@@ -787,7 +794,7 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
   c->st = (cudaStream_t)stream;
   c->lda = ((int64_t)n + 31) / 32 * 32;
   if (const char* v = getenv("DL_OMP_TM")) c->cfg_omp_tm = atoi(v);  // 0 (off), 4, 5 or 6
-  if (const char* v = getenv("DL_OMP_RES")) c->cfg_omp_res = atoi(v);  // 0 (off) or 1
+  if (const char* v = getenv("DL_OMP_RES")) c->cfg_omp_res = atoi(v);  // 0 off, 1 on, 2 any n
   const size_t mm = (size_t)m_max;
   c->jw.nb_accum = dlk::jau_accum_blocks_max(p, n);
   // the deterministic pass A writes one slice of U and one energy partial per range of signals

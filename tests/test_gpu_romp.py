@@ -2,10 +2,12 @@
 step recomputed on the tensor cores) against the FP64 oracle at the limits of
 the kernel that runs it.
 
-The plain FP32 form codes with it when 256 < n <= 512, p <= 64, p % 4 == 0
-and s <= 8.  The shapes below reach each edge of that kernel: p from 4 to 64
-(the FP16 residual rows padded with zeros to 64), n from 257 (one atom in the
-second accumulator unit) to 512, s from 1 to 8, m = 1, m = 129 (a second,
+The plain FP32 form codes with it when 256 < n <= 512, p <= 64, p % 4 == 0,
+s <= 8 and the call fills most of one round of tiles; these tests take it for
+every supported call (DL_OMP_RES=2).  The shapes below reach each edge of that
+kernel: p from 4 to 64 (the FP16 residual rows padded with zeros to 64), n
+from 40 and 256 (one accumulator unit per step, the units alternating) and 257
+(one atom in the second unit) to 512, s from 1 to 8, m = 1, m = 129 (a second,
 ragged tile), and m one full round of tiles plus five signals (all SMs and
 both slots busy, then a last round with one tile).  Degenerate inputs: zero
 signals (empty support), exactly 1- and 2-sparse signals (the residual stop
@@ -28,7 +30,13 @@ torch = pytest.importorskip("torch")
 
 ROUND = 152 * 2 * 128  # signals of one round of tiles on a 152-SM GB300
 SHAPES = [(64, 512, 3001, 8), (60, 300, 2049, 5), (4, 257, 130, 1), (32, 384, 129, 8),
-          (64, 511, 1, 3), (44, 480, 1000, 6), (64, 512, ROUND + 5, 2)]
+          (64, 511, 1, 3), (44, 480, 1000, 6), (64, 512, ROUND + 5, 2), (64, 256, 2500, 6),
+          (16, 40, 700, 4)]
+
+
+@pytest.fixture(autouse=True)
+def residual_form_for_every_call(monkeypatch):
+    monkeypatch.setenv("DL_OMP_RES", "2")
 
 
 @pytest.fixture(scope="module")
