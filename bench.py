@@ -353,9 +353,10 @@ def run_ours(args):
     omp_kernel = chosen.get("omp_kernel")
     if omp_kernel == 2:
         # residual-form OMP: the correlations D^T r of every step are its work
-        # (2 n p per signal and step, one product counted; the kernel runs three
-        # FP16 products per correlation for FP32 accuracy), against the FP16 dense
-        # tensor peak (same rate as BF16)
+        # (2 n p per signal and step, one product counted; the FP32 form runs
+        # three FP16 products per correlation for FP32 accuracy, the BF16 form
+        # one BF16 product), against the dense BF16 tensor peak (FP16 runs at
+        # the same rate)
         algo["omp"] = ("tensor", 2.0 * m * s * n * p, float(peaks.get("bf16_tflops", 1891.2)),
                        "TFLOP/s")
     elif best == "fp32":  # one launch: the correlations of all signals and the Gram matrix
@@ -384,11 +385,13 @@ def run_ours(args):
                 "peak_source": ("FP32 multiply-add rate measured on this GPU in this run "
                                 "(dl_fp32_probe, best of FFMA and FFMA2, CUDA events; of measured)"
                                 if r["bound"] == "alu" else
-                                "MEASURED_PEAKS.json bf16_tflops (of measured; FP16 at the BF16 rate)"
+                                ("MEASURED_PEAKS.json bf16_tflops (of measured)" if best == "bf16" else
+                                 "MEASURED_PEAKS.json bf16_tflops (of measured; FP16 at the BF16 rate)")
                                 if omp_kernel == 2 and dominant == "omp" else
                                 "MEASURED_PEAKS.json (of measured; TF32 = bf16/2 nominal ratio)")}
         if omp_kernel == 2 and dominant == "omp":
-            roof["executed_products"] = 3  # Rl Dh + Rh Dl + Rh Dh per correlation
+            # FP32: Rl Dh + Rh Dl + Rh Dh per correlation; BF16: R D
+            roof["executed_products"] = 1 if best == "bf16" else 3
 
     # end to end through the C ABI with host buffers (staging copies inside the timed region)
     e2e = None

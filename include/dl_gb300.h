@@ -351,8 +351,9 @@ int dl_get_config(dl_ctx* ctx, int* cfg4);
  *   0  Batch-OMP, one warp per signal, from stored correlations alpha0
  *   1  the same with the progressive-Cholesky vectors in TMEM
  *   2  residual-form OMP, the correlations D^T r of every step on the tensor
- *      cores (FP16 hi/lo parts, FP32 accumulation), no stored alpha0; taken
- *      for plain FP32 calls with 256 < n <= 512, p <= 64, p % 4 == 0, s <= 8
+ *      cores (FP16 hi/lo parts, or BF16 operands in the DL_BF16 form; FP32
+ *      accumulation), no stored alpha0; taken for FP32 and BF16 calls without
+ *      a proposer with 256 < n <= 512, p <= 64, p % 4 == 0, s <= 8
  *      and at least 3/4 of (SM count x 256) signals; the environment variable
  *      DL_OMP_RES, read by dl_init, turns it off (0) or takes it for every
  *      supported call (2)

@@ -360,17 +360,16 @@ cudaError_t enq_omp_learned(dl_ctx* c, const float* Y, int64_t m, const float* D
 }
 
 // The residual-form OMP (correlations of every step on the tensor cores, no
-// alpha0 pass) serves the plain FP32 form without a proposer for n > 256; at
-// n <= 256 the alpha0 pass is half as costly and the TMEM Batch-OMP was faster
-// (p=64, n=256, s=6, m=2e4: 180 against 160 M signals/s per iteration).
-// The residual-form OMP codes a call when it is supported and, in the automatic
-// mode, when n > 256 and the call has at least three quarters of one round of
-// tiles (both slots of most SMs busy): at n = 256, or with about one tile per
-// SM (p = 64, n = 512, m = 20000: 96 against 90 us for Gram, correlations and
-// the TMEM Batch-OMP), the Batch-OMP forms are as fast or faster.  Mode 2
-// (DL_OMP_RES=2) takes it for every supported call.
+// alpha0 pass) codes a plain FP32 or BF16 call without a proposer when it is
+// supported and, in the automatic mode, when n > 256 and the call has at least
+// three quarters of one round of tiles (both slots of most SMs busy): at
+// n = 256, or with about one tile per SM (p = 64, n = 512, m = 20000: 96
+// against 90 us for Gram, correlations and the TMEM Batch-OMP), the Batch-OMP
+// forms are as fast or faster.  Mode 2 (DL_OMP_RES=2) takes it for every
+// supported call.  The E4M3 form keeps its alpha0 pass.
 bool use_res(dl_ctx* c, const float* Y, const float* D, int s, int64_t m) {
-  if (!c->cfg_omp_res || has_prop(c) || lp_ok(c) || !dlk::omp_res_supported(c->p, c->n, s, Y, D))
+  if (!c->cfg_omp_res || has_prop(c) || c->precision == DL_FP8 ||
+      !dlk::omp_res_supported(c->p, c->n, s, Y, D))
     return false;
   return c->cfg_omp_res == 2 || (c->n > 256 && 4 * m >= 3 * dlk::omp_res_round_signals());
 }
@@ -385,7 +384,7 @@ cudaError_t enq_omp_res(dl_ctx* c, const float* Y, int64_t m, const float* D, in
   if ((e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
   c->last_omp = 2;
   e = dlk::omp_res(Y, m, c->p, D, c->n, c->G, s, c->sidx, c->sval, c->scnt, c->err, c->rs_list,
-                   c->rs_count, (int)c->m_max, c->st);
+                   c->rs_count, (int)c->m_max, c->precision == DL_BF16, c->st);
   if (e != cudaSuccess) return e;
   e = dlk::omp_resolve64(Y, c->p, D, c->G, nullptr, c->lda, c->n, s, c->rs_list, c->rs_count,
                          (int)c->m_max, c->sidx, c->sval, c->scnt, c->st);
@@ -513,9 +512,11 @@ cudaError_t enq_jau(dl_ctx* c, const float* Y, int64_t m, float* D, int s, const
 }
 
 // Whether a call with host buffers overlaps the upload of Y with the first
-// iteration's coding pass: plain FP32 tensor-core path, at least kChunks x 128 signals.
-bool staged_ok(dl_ctx* c, const float* dY, const float* dD, int64_t m) {
-  return !has_prop(c) && !lp_ok(c) && tc_ok(c, dY, dD) && m >= (int64_t)dl_ctx::kChunks * 128;
+// iteration's coding pass: the residual-form OMP (FP32 or BF16) or the plain
+// FP32 tensor-core correlations, at least kChunks x 128 signals.
+bool staged_ok(dl_ctx* c, const float* dY, const float* dD, int64_t m, int s) {
+  if (has_prop(c) || m < (int64_t)dl_ctx::kChunks * 128) return false;
+  return use_res(c, dY, dD, s, m) || (!lp_ok(c) && tc_ok(c, dY, dD));
 }
 
 // Piece q of the staged coding pass covers signals [off[q], off[q+1]).  Each
@@ -577,7 +578,8 @@ cudaError_t enq_omp_res_staged(dl_ctx* c, const float* hostY, const float* dY, i
     if ((e = cudaStreamWaitEvent(c->st, c->ev_chunk[q], 0)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->rs_count, 0, sizeof(int), c->st)) != cudaSuccess) return e;
     e = dlk::omp_res(Yq, mk, c->p, D, c->n, c->G, s, c->sidx + off * s, c->sval + off * s,
-                     c->scnt + off, c->err, c->rs_list, c->rs_count, (int)c->m_max, c->st);
+                     c->scnt + off, c->err, c->rs_list, c->rs_count, (int)c->m_max,
+                     c->precision == DL_BF16, c->st);
     if (e != cudaSuccess) return e;
     e = dlk::omp_resolve64(Yq, c->p, D, c->G, nullptr, c->lda, c->n, s, c->rs_list, c->rs_count,
                            (int)c->m_max, c->sidx + off * s, c->sval + off * s, c->scnt + off,
@@ -1099,7 +1101,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
     dcp = c->hcolptr;
     dri = c->hrowidx;
     dv = c->hval;
-    staged = staged_ok(c, dY, dD, m);
+    staged = staged_ok(c, dY, dD, m, s);
     if ((group_size(c) < c->n || c->rule == DL_RULE_NSGK) && !dlk::jau_vec4(c->p, dY, dD))
       return DL_ENOTIMPL;
     const void* hk[5] = {Y, D, colptr, rowidx, val};

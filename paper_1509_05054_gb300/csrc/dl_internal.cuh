@@ -81,15 +81,17 @@ cudaError_t omp_batch(const float* A0, int64_t lda, const float* G, int n, const
 // The same Batch-OMP with the progressive-Cholesky vectors in tensor memory
 // (k_omp_tm.cu): persistent CTAs of 4q warps (q = 4, 5, 6).  n = 512, 5 <= s <= 8.
 // Residual-form OMP with the correlations of every step on the tensor cores
-// (alpha^(k) = D^T r^(k) from FP16 hi/lo parts of D and r, FP32 accumulation,
-// one persistent CTA per SM, two 128-signal tiles in flight); no alpha0 input.
+// (alpha^(k) = D^T r^(k) from FP16 hi/lo parts of D and r, or with bf16 from
+// BF16 operands, FP32 accumulation; one persistent CTA per SM, two 128-signal
+// tiles in flight); no alpha0 input.  alpha_sel, the Cholesky factor and the
+// residual are FP32 in both forms.
 // p % 4 == 0, p <= 64, n <= 512, s <= 8, Y and D 16-byte aligned.  Signals with
 // a pivot below kPivotMin are listed for omp_resolve64.
 bool omp_res_supported(int p, int n, int s, const float* Y, const float* D);
 int64_t omp_res_round_signals();  // signals of one round of tiles (all SMs, all slots)
 cudaError_t omp_res(const float* Y, int64_t m, int p, const float* D, int n, const float* G, int s,
                     int32_t* idx, float* val, int32_t* cnt, int* err, int* rs_list, int* rs_count,
-                    int rs_cap, cudaStream_t st);
+                    int rs_cap, bool bf16, cudaStream_t st);
 bool omp_tm_supported(int n, int s);
 // A0: FP32 rows, or BF16 rows (a0_bf16) of lda elements.
 cudaError_t omp_batch_tm(int q, const void* A0, bool a0_bf16, int64_t lda, const float* G, int n,

@@ -80,6 +80,8 @@ constexpr int RT_PH = RT_PMAX / RT_HALVES;  // residual elements a thread holds
 // kind::f16: D F32 (bits 4-5 = 1), A and B F16 (format 0), K-major, N = 256, M = 128
 constexpr uint32_t RT_IDESC =
     (1u << 4) | ((uint32_t)(RT_N >> 3) << 17) | ((uint32_t)(RT_M >> 4) << 24);
+// the same with A and B BF16 (the BF16 form: one product of BF16 operands)
+constexpr uint32_t RT_IDESC_BF = RT_IDESC | (1u << 7) | (1u << 10);
 
 enum { RB_TFULL = 0, RB_TEMPTY = 2, RB_COUNT = 4 };
 
@@ -201,16 +203,31 @@ __device__ __forceinline__ float2 hl_sum(uint32_t hw, uint32_t lw) {
   return d;
 }
 
-// Unit g of row j of D from the shared-memory FP16 parts (elements 8g ..
-// 8g+7) as FP32 pairs: D_j 2^eD = hi + lo.
+// Unit g of row j of D from the shared-memory planes (elements 8g .. 8g+7) as
+// FP32 pairs, D_j 2^eD.  FP32 form: the FP16 parts, hi + lo.  BF16 form (BF):
+// the top and bottom 16 bits of each FP32 value, put back together exactly by
+// one byte permute per value (the top plane is D truncated to BF16, the
+// MMA's operand).
+template <bool BF>
 __device__ __forceinline__ void row_unit(const uint8_t* Dh, const uint8_t* Dl, int j, int g,
                                          float2 (&d)[4]) {
   const uint4 a = *reinterpret_cast<const uint4*>(Dh + sw_off(j, g));
   const uint4 b = *reinterpret_cast<const uint4*>(Dl + sw_off(j, g));
-  d[0] = hl_sum(a.x, b.x);
-  d[1] = hl_sum(a.y, b.y);
-  d[2] = hl_sum(a.z, b.z);
-  d[3] = hl_sum(a.w, b.w);
+  if constexpr (BF) {
+    d[0] = make_float2(__uint_as_float(__byte_perm(b.x, a.x, 0x5410)),
+                       __uint_as_float(__byte_perm(b.x, a.x, 0x7632)));
+    d[1] = make_float2(__uint_as_float(__byte_perm(b.y, a.y, 0x5410)),
+                       __uint_as_float(__byte_perm(b.y, a.y, 0x7632)));
+    d[2] = make_float2(__uint_as_float(__byte_perm(b.z, a.z, 0x5410)),
+                       __uint_as_float(__byte_perm(b.z, a.z, 0x7632)));
+    d[3] = make_float2(__uint_as_float(__byte_perm(b.w, a.w, 0x5410)),
+                       __uint_as_float(__byte_perm(b.w, a.w, 0x7632)));
+  } else {
+    d[0] = hl_sum(a.x, b.x);
+    d[1] = hl_sum(a.y, b.y);
+    d[2] = hl_sum(a.z, b.z);
+    d[3] = hl_sum(a.w, b.w);
+  }
 }
 
 // Step STEP of one signal after the argmax chose atom sel and alpha_sel =
@@ -279,13 +296,14 @@ __device__ __forceinline__ bool owner_chol(Owner& o, int sel, float asel, float 
 // This half's part of d_j^T r for atom j, from the shared-memory parts (D =
 // (hi + lo) 2^-eD, exact to about 2^-22 relative; no global-memory latency on
 // the step's chain), in units of 2^-eD.
+template <bool BF>
 __device__ __forceinline__ float owner_dot(const Owner& o, int j, int hf, const uint8_t* Dh,
                                            const uint8_t* Dl) {
   float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
   for (int u = 0; u < RT_PH / 8; ++u) {
     float2 d[4];
-    row_unit(Dh, Dl, j, 2 * u + hf, d);
+    row_unit<BF>(Dh, Dl, j, 2 * u + hf, d);
     a0 = __ffma2_rn(o.r[4 * u], d[0], a0);
     a1 = __ffma2_rn(o.r[4 * u + 1], d[1], a1);
     a0 = __ffma2_rn(o.r[4 * u + 2], d[2], a0);
@@ -305,6 +323,7 @@ __device__ __forceinline__ float owner_norm2(const Owner& o) {
 // r^(k+1) = r^(k) - sum_{j <= step} dg_j d_{I_j} on this half's elements (atoms
 // from the shared-memory parts, scaled back by 2^-eD); returns this half's part
 // of ||r^(k+1)||^2.  One rolled loop over atoms; packed FP32x2 multiply-adds.
+template <bool BF>
 __device__ __forceinline__ float owner_update(Owner& o, int step, int hf, const uint16_t* Is,
                                               const float* dgs, const uint8_t* Dh,
                                               const uint8_t* Dl, float dsc) {
@@ -316,7 +335,7 @@ __device__ __forceinline__ float owner_update(Owner& o, int step, int hf, const 
 #pragma unroll
     for (int u = 0; u < RT_PH / 8; ++u) {
       float2 d[4];
-      row_unit(Dh, Dl, a, 2 * u + hf, d);
+      row_unit<BF>(Dh, Dl, a, 2 * u + hf, d);
 #pragma unroll
       for (int e = 0; e < 4; ++e) o.r[4 * u + e] = __ffma2_rn(nd2, d[e], o.r[4 * u + e]);
     }
@@ -324,11 +343,30 @@ __device__ __forceinline__ float owner_update(Owner& o, int step, int hf, const 
   return owner_norm2(o);
 }
 
-// This half of the signal's residual as FP16 parts, scaled by 2^er with
-// ||r|| 2^er < 2^14 (o.rn: the whole residual's ||r||^2), into row `row` of the
-// slot's two K-major tiles.
+// Two FP32 values as packed BF16 (round to nearest), v0 in the low half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float v0, float v1) {
+  uint32_t u;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(u) : "f"(v1), "f"(v0));
+  return u;
+}
+
+// This half of the signal's residual into row `row` of the slot's K-major
+// tiles.  FP32 form: as FP16 parts in the two tiles, scaled by 2^er with
+// ||r|| 2^er < 2^14 (o.rn: the whole residual's ||r||^2).  BF16 form: rounded
+// to BF16 in the first tile.
+template <bool BF>
 __device__ __forceinline__ void owner_store(const Owner& o, int hf, uint8_t* Ah, uint8_t* Al,
                                             int row) {
+  if constexpr (BF) {
+#pragma unroll
+    for (int u = 0; u < RT_PH / 8; ++u) {
+      uint32_t h[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) h[e] = pack_bf16x2(o.r[4 * u + e].x, o.r[4 * u + e].y);
+      *reinterpret_cast<uint4*>(Ah + sw_off(row, 2 * u + hf)) = make_uint4(h[0], h[1], h[2], h[3]);
+    }
+    return;
+  }
   int E = 0;
   frexpf(sqrtf(o.rn), &E);
   const float sc = o.rn > 0.f ? pow2i(14 - E) : 1.f;
@@ -426,6 +464,7 @@ struct Xch {
   int more;    // lead: the Cholesky step's outcome (1: update and go on)
 };
 
+template <bool BF>
 __global__ void __launch_bounds__(RT_THREADS, 1)
     romp_kernel(const float* __restrict__ Y, int64_t m, int p, const float* __restrict__ D, int n,
                 const float* __restrict__ G, int s, int32_t* __restrict__ oidx,
@@ -489,7 +528,15 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
       }
       uint32_t h[4], l[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) split2(v[2 * e], v[2 * e + 1], h[e], l[e]);
+      for (int e = 0; e < 4; ++e) {
+        if constexpr (BF) {  // top / bottom 16 bits of each FP32 value
+          const uint32_t b0 = __float_as_uint(v[2 * e]), b1 = __float_as_uint(v[2 * e + 1]);
+          h[e] = __byte_perm(b0, b1, 0x7632);
+          l[e] = __byte_perm(b0, b1, 0x5410);
+        } else {
+          split2(v[2 * e], v[2 * e + 1], h[e], l[e]);
+        }
+      }
       *reinterpret_cast<uint4*>(base + RtSmem::dh + sw_off(j, g)) = make_uint4(h[0], h[1], h[2], h[3]);
       *reinterpret_cast<uint4*>(base + RtSmem::dl + sw_off(j, g)) = make_uint4(l[0], l[1], l[2], l[3]);
     }
@@ -565,7 +612,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
         o.rn = 0.f;
       }
       for (int step = 0; step < s; ++step) {
-        if (step == 0 || o.active) owner_store(o, hf, Ah, Al, row);
+        if (step == 0 || o.active) owner_store<BF>(o, hf, Ah, Al, row);
         fence_async_smem();  // the residual rows -> the tensor core's reads
         asm volatile("bar.sync %0, %1;" ::"r"(1 + sl), "r"(32 * 4 * RT_HALVES) : "memory");
         const int u = j * s * RT_NS + step * aj + sl;  // this use's place in the fixed order
@@ -580,17 +627,24 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
             const uint32_t dcol = tmem + (uint32_t)(unit * RT_N);
             const uint64_t boff = (uint64_t)((h * RT_N * RT_ROWB) >> 4);
             const uint64_t bh = dhd + boff, bl = dld + boff;
-            // the two correction products first, then the leading one
+            if constexpr (BF) {  // one product of BF16 operands
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)  // 16 FP16 = 32 bytes of K per MMA
-              mma_f16(dcol, ald + (uint64_t)(2 * kk), bh + (uint64_t)(2 * kk), RT_IDESC,
-                      kk > 0 ? 1u : 0u);
+              for (int kk = 0; kk < 4; ++kk)  // 16 elements = 32 bytes of K per MMA
+                mma_f16(dcol, ahd + (uint64_t)(2 * kk), bh + (uint64_t)(2 * kk), RT_IDESC_BF,
+                        kk > 0 ? 1u : 0u);
+            } else {
+              // the two correction products first, then the leading one
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              mma_f16(dcol, ahd + (uint64_t)(2 * kk), bl + (uint64_t)(2 * kk), RT_IDESC, 1u);
+              for (int kk = 0; kk < 4; ++kk)  // 16 FP16 = 32 bytes of K per MMA
+                mma_f16(dcol, ald + (uint64_t)(2 * kk), bh + (uint64_t)(2 * kk), RT_IDESC,
+                        kk > 0 ? 1u : 0u);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-              mma_f16(dcol, ahd + (uint64_t)(2 * kk), bh + (uint64_t)(2 * kk), RT_IDESC, 1u);
+              for (int kk = 0; kk < 4; ++kk)
+                mma_f16(dcol, ahd + (uint64_t)(2 * kk), bl + (uint64_t)(2 * kk), RT_IDESC, 1u);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                mma_f16(dcol, ahd + (uint64_t)(2 * kk), bh + (uint64_t)(2 * kk), RT_IDESC, 1u);
+            }
             mma_commit(&bars[RB_TFULL + unit]);
           }
         }
@@ -643,7 +697,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
             for (int q = 0; q < RT_SMAX; ++q)
               g[q] = q < step ? __ldg(G + (size_t)Is[q * RT_SIGS] * n + sel) : 0.f;
           }
-          dpart = owner_dot(o, sel, hf, Dh, Dl);
+          dpart = owner_dot<BF>(o, sel, hf, Dh, Dl);
         }
         // X2: half 1's part of alpha_sel to the lead
         if (!lead) xme->dot = dpart;
@@ -671,7 +725,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1)
           o.active = more;
         }
         float npart = 0.f;
-        if (more) npart = owner_update(o, step, hf, Is, dgs, Dh, Dl, dsc);
+        if (more) npart = owner_update<BF>(o, step, hf, Is, dgs, Dh, Dl, dsc);
         if (!good) o.active = false;
         // X3: ||r^(k+1)||^2 from the halves' parts
         xme->nrm = npart;
@@ -702,15 +756,16 @@ bool omp_res_supported(int p, int n, int s, const float* Y, const float* D) {
 
 cudaError_t omp_res(const float* Y, int64_t m, int p, const float* D, int n, const float* G, int s,
                     int32_t* idx, float* val, int32_t* cnt, int* err, int* rs_list, int* rs_count,
-                    int rs_cap, cudaStream_t st) {
+                    int rs_cap, bool bf16, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(romp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  auto kern = bf16 ? romp_kernel<true> : romp_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)RtSmem::dyn);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (m + RT_M - 1) / RT_M;
   const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
-  romp_kernel<<<grid, RT_THREADS, RtSmem::dyn, st>>>(Y, m, p, D, n, G, s, idx, val, cnt, err,
-                                                     rs_list, rs_count, rs_cap);
+  kern<<<grid, RT_THREADS, RtSmem::dyn, st>>>(Y, m, p, D, n, G, s, idx, val, cnt, err, rs_list,
+                                              rs_count, rs_cap);
   return cudaGetLastError();
 }
 

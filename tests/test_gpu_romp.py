@@ -9,7 +9,9 @@ kernel: p from 4 to 64 (the FP16 residual rows padded with zeros to 64), n
 from 40 and 256 (one accumulator unit per step, the units alternating) and 257
 (one atom in the second unit) to 512, s from 1 to 8, m = 1, m = 129 (a second,
 ragged tile), and m one full round of tiles plus five signals (all SMs and
-both slots busy, then a last round with one tile).  Degenerate inputs: zero
+both slots busy, then a last round with one tile).  The BF16 form of the
+kernel (BF16 operands for the correlations, FP32 elsewhere) is checked for
+FP32-accurate coefficients on its own supports and for the coding error.  Degenerate inputs: zero
 signals (empty support), exactly 1- and 2-sparse signals (the residual stop
 rule), and a pair of nearly parallel atoms (Cholesky pivots below 1e-6, the
 hand-off to the FP64 re-solve).  Supports must match the oracle on >= 99.9%
@@ -185,3 +187,63 @@ def test_host_buffer_iteration_splits_at_a_round_of_tiles(dl):
     np.testing.assert_allclose(val_h, val_d, rtol=0, atol=1e-5)
     np.testing.assert_allclose(Dh, Dd, rtol=0, atol=1e-5)
     np.testing.assert_allclose(rm_h, rm_d, rtol=0, atol=1e-6)
+
+
+def test_bf16_residual_form_keeps_fp32_coefficients(dl):
+    """The BF16 form of the residual OMP: correlations from BF16 operands (the
+    argmax may differ from the FP64 oracle's on close calls), but alpha_sel, the
+    Cholesky factor and the residual in FP32 from D put back together exactly:
+    every signal's coefficients are the least-squares solution on its own
+    support to FP32 accuracy, and the coding error is the oracle's to 1%."""
+    Y, D, spec = synth.workload_inputs("patch_n512", m=4000)
+    m, p, n, s = 4000, D.shape[1], D.shape[0], spec["s"]
+    ctx = dl.dl_init(p, n, m, s, dl.DL_BF16, torch.cuda.current_stream())
+    try:
+        colptr = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+        rowidx = torch.zeros(m * s, dtype=torch.int32, device="cuda")
+        val = torch.zeros(m * s, dtype=torch.float32, device="cuda")
+        dl.omp_code(ctx, torch.from_numpy(Y).cuda(), m, torch.from_numpy(D).cuda(), s, colptr,
+                    rowidx, val)
+        dl.dl_sync(ctx)
+        assert dl.dl_last_omp_kernel(ctx) == 2
+    finally:
+        dl.dl_destroy(ctx)
+    idx, v, cnt = csc_to_slots(colptr.cpu().numpy(), rowidx.cpu().numpy(), val.cpu().numpy(), s)
+    Y64, D64 = Y.astype(np.float64), D.astype(np.float64)
+    for i in range(m):
+        I = idx[i, :cnt[i]]
+        assert len(set(I.tolist())) == len(I) and np.all(np.diff(I) > 0)
+        g, *_ = np.linalg.lstsq(D64[I].T, Y64[i], rcond=None)
+        np.testing.assert_allclose(v[i, :cnt[i]], g, rtol=0, atol=1e-4)
+    idx_o, val_o, cnt_o = oracle.omp(Y64, D64, s)
+    same = np.mean(np.all(idx == idx_o, axis=1) & (cnt == cnt_o))
+    r_g = oracle.rmse(Y64, D64, idx, v.astype(np.float64), cnt)
+    r_o = oracle.rmse(Y64, D64, idx_o, val_o, cnt_o)
+    print(f"bf16 residual form: identical supports {100 * same:.2f}%, rmse {100 * (r_g / r_o - 1):+.4f}%")
+    assert 0.9 < same < 0.999  # BF16 correlations, not the FP32 path
+    assert r_g <= 1.01 * r_o
+
+
+def test_bf16_residual_form_reaches_plain_rmse(dl):
+    """Ten Jacobi iterations of the BF16 residual form end within 1% of the
+    FP32 form's relative RMSE from the same start."""
+    Y, D, spec = synth.workload_inputs("patch_n512", m=20000)
+    m, p, n, s, iters = 20000, D.shape[1], D.shape[0], spec["s"], 10
+    out = {}
+    for prec in (dl.DL_FP32, dl.DL_BF16):
+        st = torch.cuda.Stream()
+        ctx = dl.dl_init(p, n, m, s, prec, st)
+        try:
+            Dd = torch.from_numpy(D.copy()).cuda()
+            cp = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+            ri = torch.zeros(m * s, dtype=torch.int32, device="cuda")
+            v = torch.zeros(m * s, device="cuda")
+            rm = np.zeros(2 * iters)
+            dl.dl_iterate(ctx, torch.from_numpy(Y).cuda(), m, Dd, s, iters, cp, ri, v, rm)
+            assert dl.dl_last_omp_kernel(ctx) == 2
+        finally:
+            dl.dl_destroy(ctx)
+        out[prec] = rm.reshape(iters, 2)
+    gap = out[dl.DL_BF16][-1, 1] / out[dl.DL_FP32][-1, 1] - 1
+    print(f"bf16 residual form: final rmse {100 * gap:+.3f}% against the FP32 form")
+    assert abs(gap) <= 0.01
