@@ -16,7 +16,10 @@
 //     up to 512 atoms, one signal per TMEM lane.  The dropped Rl Dl^T term and
 //     the FP16 roundings leave an error of about 2^-21 ||r|| ||d_j|| per
 //     correlation -- the accuracy class of FP32 Batch-OMP.  alpha0 is step 0 of
-//     the same product and never leaves the chip.
+//     the same product and never leaves the chip.  The BF16 form (BF) keeps
+//     the top and bottom 16 bits of each FP32 value of D 2^eD instead: the top
+//     plane (D truncated to BF16) and the residual rounded to BF16 give one
+//     kind::f16 product per step; both planes together give FP32 D exactly.
 //   * Two threads per signal ("halves", the same lane of two warps) read its
 //     TMEM row (tcgen05.ld 32x32b, its lane), each half 128 of every
 //     accumulator unit's 256 columns, and take the argmax of |alpha| with the
@@ -24,7 +27,8 @@
 //     chunks in ascending order; the halves' bests are exchanged through
 //     shared memory).  Each half holds 32 of the residual's 64 elements and
 //     computes its part of alpha_sel = d_sel^T r in FP32 from D's
-//     shared-memory parts (hi + lo, 22 significant bits).  The lead half
+//     shared-memory planes (hi + lo, 22 significant bits; exact FP32 D in the
+//     BF16 form).  The lead half
 //     extends B = L^-1 (the inverse Cholesky factor of G_I, Gram entries from
 //     G) and writes the step's coefficient changes; both halves then update
 //     their elements of r^(k+1) = r^(k) - D_I (gamma^(k+1) - gamma^(k)) in FP32
@@ -293,9 +297,9 @@ __device__ __forceinline__ bool owner_chol(Owner& o, int sel, float asel, float 
   return true;
 }
 
-// This half's part of d_j^T r for atom j, from the shared-memory parts (D =
-// (hi + lo) 2^-eD, exact to about 2^-22 relative; no global-memory latency on
-// the step's chain), in units of 2^-eD.
+// This half's part of d_j^T r for atom j, from the shared-memory planes (D =
+// (hi + lo) 2^-eD, exact to about 2^-22 relative, or exact in the BF16 form;
+// no global-memory latency on the step's chain), in units of 2^-eD.
 template <bool BF>
 __device__ __forceinline__ float owner_dot(const Owner& o, int j, int hf, const uint8_t* Dh,
                                            const uint8_t* Dl) {
