@@ -148,9 +148,11 @@ def test_residual_omp_nonfinite_signal_is_reported(dl):
         dl.dl_destroy(ctx)
 
 
-def test_host_buffer_iteration_splits_at_a_round_of_tiles(dl):
-    """dl_iterate with pinned host buffers stages Y in two pieces (the first one
-    full round of the OMP kernel's tiles) and gives the device path's result:
+@pytest.mark.parametrize("prec", [0, 1])
+def test_host_buffer_iteration_splits_at_a_round_of_tiles(dl, prec):
+    """dl_iterate with pinned host buffers (FP32 and BF16 forms) stages Y in
+    two pieces (the first one full round of the OMP kernel's tiles) and gives
+    the device path's result:
     the coding of each signal depends on nothing but its own data, so the
     supports are identical; the atom update sums in L2 in no fixed order."""
     name, s = "patch_n512", 8
@@ -160,7 +162,7 @@ def test_host_buffer_iteration_splits_at_a_round_of_tiles(dl):
     st = torch.cuda.Stream()
     outs = []
     for host in (False, True):
-        ctx = dl.dl_init(p, n, m, s, dl.DL_FP32, st)
+        ctx = dl.dl_init(p, n, m, s, prec, st)
         try:
             if host:
                 args = [torch.from_numpy(Y).pin_memory(), torch.from_numpy(D.copy()).pin_memory(),
@@ -189,14 +191,25 @@ def test_host_buffer_iteration_splits_at_a_round_of_tiles(dl):
     np.testing.assert_allclose(rm_h, rm_d, rtol=0, atol=1e-6)
 
 
-def test_bf16_residual_form_keeps_fp32_coefficients(dl):
+BF16_SHAPES = [("patch", 64, 512, 4000, 8), ("recovery", 36, 300, 1500, 5),
+               ("recovery", 64, 256, 1200, 6), ("recovery", 16, 40, 600, 4)]
+
+
+@pytest.mark.parametrize("kind,p,n,m,s", BF16_SHAPES)
+def test_bf16_residual_form_keeps_fp32_coefficients(dl, kind, p, n, m, s):
     """The BF16 form of the residual OMP: correlations from BF16 operands (the
     argmax may differ from the FP64 oracle's on close calls), but alpha_sel, the
     Cholesky factor and the residual in FP32 from D put back together exactly:
     every signal's coefficients are the least-squares solution on its own
-    support to FP32 accuracy, and the coding error is the oracle's to 1%."""
-    Y, D, spec = synth.workload_inputs("patch_n512", m=4000)
-    m, p, n, s = 4000, D.shape[1], D.shape[0], spec["s"]
+    support to FP32 accuracy, and the coding error is the oracle's to 1%.
+    Shapes: the patch workload, and recovery problems with p < 64, n = 256 and
+    n = 40 (one accumulator unit per step)."""
+    if kind == "patch":
+        Y, D, _ = synth.workload_inputs("patch_n512", m=m)
+    else:
+        Y, _, _, _ = synth.recovery_problem(p, n, m, s, 30.0, seed=1300 + p + n)
+        D = synth.random_dictionary(p, n, seed=1400 + p + n, dtype=np.float32)
+        Y = Y.astype(np.float32)
     ctx = dl.dl_init(p, n, m, s, dl.DL_BF16, torch.cuda.current_stream())
     try:
         colptr = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
@@ -220,7 +233,9 @@ def test_bf16_residual_form_keeps_fp32_coefficients(dl):
     r_g = oracle.rmse(Y64, D64, idx, v.astype(np.float64), cnt)
     r_o = oracle.rmse(Y64, D64, idx_o, val_o, cnt_o)
     print(f"bf16 residual form: identical supports {100 * same:.2f}%, rmse {100 * (r_g / r_o - 1):+.4f}%")
-    assert 0.9 < same < 0.999  # BF16 correlations, not the FP32 path
+    assert same > 0.9
+    if kind == "patch":
+        assert same < 0.999  # BF16 correlations, not the FP32 path
     assert r_g <= 1.01 * r_o
 
 
