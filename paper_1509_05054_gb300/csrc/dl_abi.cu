@@ -136,7 +136,8 @@ struct dl_ctx {
   int cfg_corr_tc = 1;    // tensor-core correlations when the shape allows
   // side stream: the colptr scan overlaps the first pass of the atom update
   cudaStream_t st2 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+  int scan_kernels = 2;  // side-stream kernels of the last iteration (colptr scan, rowidx)
   // host-buffer calls: the signals arrive in chunks on the side stream
   static constexpr int kChunks = 3;
   cudaEvent_t ev_chunk[kChunks] = {};
@@ -168,6 +169,7 @@ void free_ctx(dl_ctx* c) {
   for (cudaEvent_t e : c->ev_chunk)
     if (e) cudaEventDestroy(e);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_join2) cudaEventDestroy(c->ev_join2);
   if (c->st2) cudaStreamDestroy(c->st2);
   void* ptrs[] = {c->G, c->A0, c->Dhi, c->Dlo, c->Ylp, c->Ysc, c->Dlp, c->Dsc, c->rs_list,
                   c->rs_count, c->sidx, c->sval, c->scnt, c->bsum, c->err, c->iter, c->rmse,
@@ -651,25 +653,48 @@ cudaError_t enq_omp_staged(dl_ctx* c, const float* hostY, const float* dY, int64
 
 // hostY: when given, Y is uploaded into the staging buffer Y by the coding pass
 // itself (enq_omp_staged); staged_kernels then receives that pass's kernel count.
+// The side stream scans the counts into colptr while the atom update starts and
+// then writes the CSC row indices from the coding pass's slots (the supports do
+// not change in the atom update; the row pass writes only the values); with
+// colptr_dl / rowidx_dl (page-locked host buffers) it also downloads both there,
+// under the atom update.
 cudaError_t enq_iteration(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int64_t* colptr,
                           int32_t* rowidx, float* val, const float* hostY = nullptr,
-                          int* staged_kernels = nullptr) {
+                          int* staged_kernels = nullptr, int64_t* colptr_dl = nullptr,
+                          int32_t* rowidx_dl = nullptr) {
   cudaError_t e = hostY ? enq_omp_staged(c, hostY, Y, m, D, s, staged_kernels)
                         : enq_omp(c, Y, m, D, s);
   if (e != cudaSuccess) return e;
-  // colptr scan on the side stream, concurrent with the accumulation and the atom update
   if ((e = cudaEventRecord(c->ev_fork, c->st)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(c->st2, c->ev_fork, 0)) != cudaSuccess) return e;
   e = dlk::counts_to_colptr(c->scnt, m, c->bsum, colptr, c->st2);
   if (e != cudaSuccess) return e;
-  if ((e = cudaEventRecord(c->ev_join, c->st2)) != cudaSuccess) return e;
-  return enq_jau(c, Y, m, D, s, colptr, rowidx, val, c->ev_join);
+  if ((e = cudaEventRecord(c->ev_join, c->st2)) != cudaSuccess) return e;  // the row pass's colptr
+  c->scan_kernels = 2;
+  const bool side_rowidx = rowidx != nullptr && m > 0;
+  if (side_rowidx) {
+    if ((e = dlk::slots_to_csc(c->sidx, nullptr, c->scnt, m, s, colptr, rowidx, nullptr,
+                               c->st2)) != cudaSuccess)
+      return e;
+    c->scan_kernels = 3;
+    if (colptr_dl && (e = cudaMemcpyAsync(colptr_dl, colptr, sizeof(int64_t) * (size_t)(m + 1),
+                                          cudaMemcpyDeviceToHost, c->st2)) != cudaSuccess)
+      return e;
+    if (rowidx_dl && (e = cudaMemcpyAsync(rowidx_dl, rowidx, sizeof(int32_t) * (size_t)m * s,
+                                          cudaMemcpyDeviceToHost, c->st2)) != cudaSuccess)
+      return e;
+    if ((e = cudaEventRecord(c->ev_join2, c->st2)) != cudaSuccess) return e;
+  }
+  e = enq_jau(c, Y, m, D, s, colptr, side_rowidx ? nullptr : rowidx, val, c->ev_join);
+  if (e != cudaSuccess) return e;
+  if (side_rowidx) e = cudaStreamWaitEvent(c->st, c->ev_join2, 0);
+  return e;
 }
 
 // Kernels one DL iteration enqueues (the claim behind dl_kernel_launches).
 // The counts are recorded when the pass is enqueued (eagerly or into a graph).
 int64_t kernels_per_iteration(dl_ctx* c, bool learned) {
-  return c->omp_kernels[learned ? 1 : 0] + kKernelsScan + c->jau_kernels;
+  return c->omp_kernels[learned ? 1 : 0] + c->scan_kernels + c->jau_kernels;
 }
 
 int check_common(dl_ctx* c, int64_t m) {
@@ -699,17 +724,14 @@ cudaError_t enq_host_call(dl_ctx* c, const float* Y, int64_t m, float* D, int s,
       (e = cudaMemsetAsync(c->iter, 0, sizeof(int), c->st)) != cudaSuccess)
     return e;
   int ko = 0;
-  if ((e = enq_iteration(c, c->hY, m, c->hD, s, c->hcolptr, c->hrowidx, c->hval, Y, &ko)) !=
-      cudaSuccess)
+  // colptr and the row indices go down on the side stream under the atom update
+  if ((e = enq_iteration(c, c->hY, m, c->hD, s, c->hcolptr, c->hrowidx, c->hval, Y, &ko, colptr,
+                         rowidx)) != cudaSuccess)
     return e;
-  *kernels = ko + kKernelsScan + c->jau_kernels;
+  *kernels = ko + c->scan_kernels + c->jau_kernels;
   // all s*m entries (the caller's capacity), so no synchronisation is needed to learn nnz
   if ((e = cudaMemcpyAsync(D, c->hD, sizeof(float) * np, cudaMemcpyDeviceToHost, c->st)) !=
           cudaSuccess ||
-      (e = cudaMemcpyAsync(colptr, c->hcolptr, sizeof(int64_t) * (size_t)(m + 1),
-                           cudaMemcpyDeviceToHost, c->st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(rowidx, c->hrowidx, sizeof(int32_t) * ms, cudaMemcpyDeviceToHost,
-                           c->st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(val, c->hval, sizeof(float) * ms, cudaMemcpyDeviceToHost, c->st)) !=
           cudaSuccess)
     return e;
@@ -818,7 +840,8 @@ int dl_init(dl_ctx** out, int p, int n, int64_t m_max, int s_max, int precision,
             dalloc(&c->Dlo, (size_t)n * p) && dalloc(&c->rs_list, mm) && dalloc(&c->rs_count, 1);
   ok = ok && cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) == cudaSuccess &&
        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
+       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess &&
+       cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) == cudaSuccess;
   for (cudaEvent_t& e : c->ev_chunk)
     ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
   if (ok && precision != DL_FP32) {
@@ -1154,7 +1177,7 @@ int dl_iterate(dl_ctx* c, const float* Y, int64_t m, float* D, int s, int iters,
       // first iteration of a host-buffer call: upload overlapped with the coding pass
       int ko = 0;
       DL_CHECK(enq_iteration(c, dY, m, dD, s, dcp, dri, dv, Y, &ko));
-      c->launches += ko + kKernelsScan + c->jau_kernels;
+      c->launches += ko + c->scan_kernels + c->jau_kernels;
       if (c->prof) {
         DL_CHECK(cudaStreamSynchronize(c->st));
         for (int k = 0; k < 8; ++k) {
@@ -1548,7 +1571,7 @@ extern "C" int dl_batch_iterate(dl_batch* b, int iters, double* rmse) {
     b->graph_iters = iters;
   }
   DL_CHECK(cudaGraphLaunch(b->gexec, b->main));
-  for (dl_ctx* c : b->ctxs) c->launches += (int64_t)iters * (c->omp_kernels[0] + kKernelsScan + c->jau_kernels);
+  for (dl_ctx* c : b->ctxs) c->launches += (int64_t)iters * (c->omp_kernels[0] + c->scan_kernels + c->jau_kernels);
   if (rmse) {
     DL_CHECK(cudaStreamSynchronize(b->main));
     for (int k = 0; k < b->count; ++k)

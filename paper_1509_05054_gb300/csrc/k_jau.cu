@@ -932,7 +932,7 @@ __global__ void slots_to_csc_kernel(const int32_t* __restrict__ idx, const float
   const int t = (int)(g - i * s);
   if (t < cnt[i]) {
     rowidx[colptr[i] + t] = idx[g];
-    cval[colptr[i] + t] = val[g];
+    if (cval) cval[colptr[i] + t] = val[g];
   }
 }
 
